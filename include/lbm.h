@@ -1,0 +1,204 @@
+/*
+ * lbm.h — C ABI of the GB300 (sm_103a) differentiable lattice Boltzmann
+ * library: the forward step and the hand-written reverse (adjoint) step of
+ * the AD-LBM inversion of arXiv 2310.00810 (Wang & Kumar), in D2Q9 and D3Q19.
+ *
+ * The method (section 2.1 of the paper):
+ *   Eq. 1-2  rho = sum_i f_i,  rho u = sum_i f_i c_i
+ *   Eq. 3-5  BGK: f_i(x + c_i, t + 1) = f_i - (f_i - f_i^eq(rho, u)) / tau,
+ *            f_i^eq = w_i rho (1 + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u)  (c_s^2 = 1/3)
+ *   Eq. 6    anti-bounce-back pressure planes at x = -1/2 (rho_in) and
+ *            x = nx - 1/2 (rho_out)
+ *   section 2.2 "Bounce Back": halfway bounce-back at grain nodes and at the
+ *            walls y = -1/2, ny - 1/2 (and z = -1/2, nz - 1/2)
+ *   section 2.2 / Eq. 7 / Eq. 15: velocity-mismatch loss at the final step,
+ *            differentiated with respect to the inlet density (a constant
+ *            head or a per-node profile) and tau.
+ * The paper differentiates with Taichi's tape (section 2.2); this library
+ * instead runs an explicit discrete adjoint with sqrt(T) checkpointing.
+ *
+ * Conventions
+ *  - Every call returns an lbm_status.  Calls that take a stream are
+ *    asynchronous on that stream (a cudaStream_t passed as void*; NULL is the
+ *    legacy default stream) unless stated otherwise.  Errors detected on the
+ *    device (a non-finite loss or gradient, a bounded wait that gave up) are
+ *    latched in the plan's status word; lbm_get_status reads it.
+ *  - Ownership: every device buffer is allocated and owned by the caller.
+ *    The plan keeps host-side state only, plus the device pointers it was
+ *    given by lbm_init_geometry (which must stay valid while it is used).
+ *  - Layout: node index n = (z * ny + y) * nx + x (x fastest), N = nx ny nz.
+ *    Populations f[i * N + n], i = 0..Q-1, stored SHIFTED by the rest state
+ *    (f_i - w_i), in the plan's precision (float or double).  Velocity
+ *    fields u[a * N + n] (a = 0..D-1) and densities are double.
+ *  - D2Q9 order: rest, E, N, W, S, NE, NW, SW, SE (the order of the paper's
+ *    Fig. 1 and MRT matrix, Eq. 18).  D3Q19 order: rest, +x, -x, +y, -y, +z,
+ *    -z, (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1),
+ *    (1,0,-1), (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).
+ *  - A plan is not thread-safe; separate plans are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
+    LBM_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement */
+    LBM_ERR_OOM = 3,         /* a caller-provided buffer is too small */
+    LBM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    LBM_ERR_NONFINITE = 5,   /* a loss or gradient came out NaN or Inf */
+    LBM_ERR_TIMEOUT = 6      /* a bounded device-side wait gave up */
+} lbm_status;
+
+enum { LBM_LOSS_VEC = 0, LBM_LOSS_NORM = 1 };          /* |u - u_t|^2  or  (|u| - |u_t|)^2 */
+enum { LBM_NORM_SUM = 0, LBM_NORM_MEAN_FLUID = 1 };    /* Eq. 7 (sum) or Eq. 15 (mean over fluid) */
+enum { LBM_INLET_CONST = 0, LBM_INLET_PROFILE = 1 };   /* one rho_in, or one per inlet node */
+enum { LBM_GEOM_CHANNEL = 0, LBM_GEOM_DISKS = 1, LBM_GEOM_SPHERES = 2, LBM_GEOM_MASK = 3 };
+
+/* Link-word bits (lbm_init_geometry's d_link): bit i (i < Q) set when a
+ * fluid node receives direction i by halfway bounce-back (the link from
+ * x - c_i crosses a wall plane or starts at a solid node); LBM_LINK_SOLID set
+ * (alone) on solid nodes. */
+#define LBM_LINK_SOLID 0x80000000u
+
+typedef struct lbm_desc {
+    int32_t q;           /* 9 (D2Q9) or 19 (D3Q19) */
+    int32_t nx, ny, nz;  /* lattice size; nz = 1 for D2Q9; nx >= 2, ny >= 1 */
+    int32_t precision;   /* bytes per population: 4 (float) or 8 (double) */
+    int32_t n_steps;     /* T >= 1: time steps of lbm_forward / lbm_adjoint */
+    int32_t ckpt_stride; /* k: keep every k-th state (0: ceil(sqrt(T)); 1: every state) */
+    int32_t loss_kind;   /* LBM_LOSS_VEC | LBM_LOSS_NORM */
+    int32_t loss_norm;   /* LBM_NORM_SUM | LBM_NORM_MEAN_FLUID */
+    int32_t inlet_kind;  /* LBM_INLET_CONST | LBM_INLET_PROFILE (ny * nz entries, [z * ny + y]) */
+} lbm_desc;
+
+typedef struct lbm_geom_desc {
+    int32_t kind;            /* LBM_GEOM_* ; DISKS needs q = 9, SPHERES q = 19 */
+    int32_t r_min, r_max;    /* grain radius range in lattice units, 0 <= r_min <= r_max */
+    int32_t hydro_q8;        /* voxelised radius = r * hydro_q8 / 256 (256: factor 1; 230: ~0.9 R) */
+    int32_t inlet_buffer;    /* columns kept free of grains at each end (>= 1) */
+    int32_t fill_isolated;   /* nonzero: pores not connected to x = 0 become solid */
+    int64_t max_rejections;  /* stop after this many trials in a row that add no solid node */
+    uint64_t seed;           /* SplitMix64 seed */
+    double target_porosity;  /* stop once fluid nodes <= (int64)(target * N) */
+} lbm_geom_desc;
+
+typedef struct lbm_plan lbm_plan;
+
+/* Creates a plan for one lattice (host memory only; no device allocation).
+ * Errors: INVALID_ARG for an unsupported q/precision, non-positive sizes,
+ * nz != 1 with q = 9, T < 1 or a negative stride. */
+LBM_API lbm_status lbm_plan_create(const lbm_desc* desc, lbm_plan** out);
+LBM_API lbm_status lbm_plan_destroy(lbm_plan* plan);
+
+/* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
+ * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and segment
+ * buffer, adjoint ping-pong states and FP64 reduction slots. */
+LBM_API lbm_status lbm_workspace_size(const lbm_plan* plan, size_t* bytes);
+
+/* Builds the geometry of section 3.1.1 / 3.3 stand-ins on the device
+ * (seeded grains voxelised with integer arithmetic, then isolated pores
+ * filled, then link words), bit-identical to the recipe:
+ *   SplitMix64 draws, Q8 fixed point, cx = draw_below(256 nx),
+ *   cy = draw_below(256 ny), [cz = draw_below(256 nz)],
+ *   r = 256 r_min + draw_below(256 (r_max - r_min) + 1); a trial is kept if
+ *   it clears the inlet/outlet buffers and (disks) lies 1 lu from every
+ *   placed disk; node solid iff |256 x - c|^2 <= (r hydro_q8 / 256)^2.
+ * kind = LBM_GEOM_MASK takes d_mask as input (nonzero = solid) and only
+ * fills and derives link words.
+ *  d_mask      uint8[N]   out (in for MASK): 0 fluid, 1 solid; 4-byte aligned
+ *                          and allocated to N rounded up to a multiple of 4
+ *  d_link      uint32[N]  out: link words (LBM_LINK_SOLID / bounce-back bits);
+ *                          the plan keeps this pointer for later calls
+ *  d_porosity  double[1]  out (nullable): fluid fraction after the fill
+ *  d_info      int64[4]   out (required): grains placed, solid before fill,
+ *                          nodes filled, fluid nodes
+ * Errors: INVALID_ARG (bad kind for q, radii, buffer), CUDA. */
+LBM_API lbm_status lbm_init_geometry(lbm_plan* plan, const lbm_geom_desc* g, uint8_t* d_mask, uint32_t* d_link,
+                             double* d_porosity, int64_t* d_info, void* stream);
+
+/* Binds an existing link array (from lbm_init_geometry of a plan of the
+ * same lattice size and Q) to this plan, so plans of different precision or
+ * step count can share one geometry.  The pointer must stay valid. */
+LBM_API lbm_status lbm_bind_geometry(lbm_plan* plan, const uint32_t* d_link);
+
+/* T steps from rest (f = w_i, rho = 1: init_field of section 2.2), keeping
+ * the checkpoints the adjoint needs in d_ws.
+ *  d_rho_in  double[1 or ny nz]  inlet density (Eq. 6 rho_w at x = -1/2)
+ *  d_tau     double[1]           relaxation time (> 1/2)
+ *  rho_out   outlet density (Eq. 6 rho_w at x = nx - 1/2)
+ *  d_f       out: f^T, shifted, plan precision, Q N values
+ *  d_ws      workspace of lbm_workspace_size bytes, 256-byte aligned and
+ *            zero-filled before its first use (it holds the status word)
+ * Errors: INVALID_ARG (null pointers, no geometry bound), CUDA. */
+LBM_API lbm_status lbm_forward(lbm_plan* plan, const double* d_rho_in, const double* d_tau, double rho_out, void* d_f,
+                       void* d_ws, void* stream);
+
+/* Advances an arbitrary state by n_steps (>= 1) without checkpoints:
+ * d_f_out = (stream o collide)^n (d_f_in).  In-place (d_f_in == d_f_out) is
+ * allowed.  Uses d_ws for intermediate states. */
+LBM_API lbm_status lbm_step(lbm_plan* plan, const double* d_rho_in, const double* d_tau, double rho_out, const void* d_f_in,
+                    void* d_f_out, int32_t n_steps, void* d_ws, void* stream);
+
+/* Loss of the final state (section 3.1.2: sum of squared velocity
+ * mismatches over the region of interest; Eq. 15 normalisation optional)
+ * and its seed lambda^T = dL/df^T (zero at solid and non-ROI nodes).
+ *  d_f        f^T (shifted, plan precision)
+ *  d_u_target double[D N] target velocity
+ *  d_roi      uint8[N] region of interest (nullable: all fluid nodes)
+ *  d_loss     double[1] out
+ *  d_lambda   out, plan precision, Q N values
+ * A non-finite loss latches LBM_ERR_NONFINITE in the status word. */
+LBM_API lbm_status lbm_loss_grad(lbm_plan* plan, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
+                         double* d_loss, void* d_lambda, void* d_ws, void* stream);
+
+/* Reverse sweep from lambda^T to t = 0 through the checkpoints left in d_ws
+ * by the last lbm_forward with the same parameters: recompute each segment,
+ * then run the adjoint step backwards through it.
+ *  d_lambda       lambda^T (plan precision; not modified)
+ *  d_grad_rho_in  double[1 or ny nz] out: dL/drho_in
+ *  d_grad_tau     double[1] out: dL/dtau
+ * Gradient sums are FP64 in a fixed order (deterministic run to run). */
+LBM_API lbm_status lbm_adjoint(lbm_plan* plan, const double* d_rho_in, const double* d_tau, double rho_out,
+                       const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream);
+
+/* Moments (Eq. 1-2) in FP64: d_rho double[N] (nullable), d_u double[D N].
+ * Solid nodes report rho = 0 and u = 0. */
+LBM_API lbm_status lbm_macroscopic(lbm_plan* plan, const void* d_f, double* d_rho, double* d_u, void* stream);
+
+/* Darcy permeability (Eq. 12) of a steady state: k = nu J / (dp/dx) with
+ * J = (1 / (ny nz)) sum over section x = xs of rho u_x (solids give 0),
+ * nu = (tau - 1/2) / 3 (Eq. 9) and dp/dx = (mean rho_in - rho_out) / (3 nx).
+ *  d_k, d_flux   double[1] out (d_flux nullable). */
+LBM_API lbm_status lbm_darcy(lbm_plan* plan, const void* d_f, const double* d_rho_in, const double* d_tau, double rho_out,
+                     int32_t xs, double* d_k, double* d_flux, void* stream);
+
+/* One Adam step (the optimiser of section 2.2 / 3.4) on a scaled parameter
+ * vector: p = p_offset + p_scale * theta.  Reads dL/dp, updates theta, m, v
+ * in place and writes p.  t is the 1-based step count.  n <= 65536. */
+LBM_API lbm_status lbm_adam_step(int32_t n, double* d_theta, double* d_m, double* d_v, const double* d_grad_p, double* d_p,
+                         double p_offset, double p_scale, int32_t t, double lr, double beta1, double beta2,
+                         double eps, void* stream);
+
+/* Reads (synchronously) and clears the plan's device status word. */
+LBM_API lbm_status lbm_get_status(lbm_plan* plan, lbm_status* status);
+
+/* Static message for a status code. */
+LBM_API const char* lbm_error_string(lbm_status status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,345 @@
+// The C ABI (include/lbm.h): plans, workspace layout, and the orchestration
+// of the forward sweep, the sqrt(T) checkpointed reverse sweep, the loss and
+// the post-processing calls.  Everything that touches lattice data runs in
+// this library's CUDA kernels; the host only sequences launches.
+//
+// Time indexing.  The paper's state f^t (pre-collision) evolves as
+// f^{t+1} = S(C(f^t)) from f^0 = rest.  The kernels store g^t = C(f^t), so
+//   g^0 = rest (collision leaves the rest state unchanged),
+//   g^t = C(S(g^{t-1}))  for t = 1..T-1  (stream-collide launches),
+//   f^T = S(g^{T-1})                      (stream-only launch).
+// The adjoint step for time t needs f^t = S(g^{t-1}) (or the rest state at
+// t = 0).  With stride k and S = ceil(T / k) segments, segment s covers
+// t in [s k, min((s+1) k, T)); its base is g^{s k - 1}, which the forward
+// sweep writes straight into checkpoint slot s (s = 1..S-1) instead of a
+// ping-pong buffer, so checkpointing costs no extra traffic.  The reverse
+// sweep recomputes g^{s k} .. g^{s k + len - 2} into the segment buffer and
+// then runs the adjoint steps of the segment backwards.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+using namespace lbm;
+
+struct lbm_plan {
+    lbm_desc desc;
+    PlanInfo info;
+    int k;      // checkpoint stride
+    int S;      // segments
+    Workspace ws;
+    uint8_t* mask = nullptr;
+    uint32_t* link = nullptr;
+    void* last_ws = nullptr;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+void layout(lbm_plan* p)
+{
+    const size_t st = align256(p->info.state_bytes);
+    Workspace& w = p->ws;
+    size_t o = 0;
+    w.status = o;
+    o += 256;
+    w.grad_acc = o;
+    o += align256(sizeof(double) * (size_t)p->info.n_acc);
+    w.partial = o;
+    o += align256(sizeof(double) * (size_t)p->info.n_blocks);
+    w.partial2 = o;
+    o += align256(sizeof(double) * (size_t)p->info.n_blocks);
+    for (int i = 0; i < 2; ++i) {
+        w.ping[i] = o;
+        o += st;
+    }
+    for (int i = 0; i < 2; ++i) {
+        w.lam[i] = o;
+        o += st;
+    }
+    w.ckpt = o;
+    o += st * (size_t)(p->S - 1);
+    w.seg = o;
+    o += st * (size_t)p->k;
+    w.total = o;
+}
+
+bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 255u) == 0; }
+
+unsigned char* bytes(void* ws) { return static_cast<unsigned char*>(ws); }
+
+Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out)
+{
+    Bc bc;
+    bc.rho_in = rho_in;
+    bc.profile = p->info.n_in > 1 ? 1 : 0;
+    bc.rho_out = rho_out;
+    return bc;
+}
+
+lbm_status check_common(const lbm_plan* p, const void* ws)
+{
+    if (!p) return LBM_ERR_INVALID_ARG;
+    if (!p->link) return LBM_ERR_INVALID_ARG;  // no geometry bound yet
+    if (ws && !aligned256(ws)) return LBM_ERR_INVALID_ARG;
+    return LBM_OK;
+}
+
+#define LBM_TRY(expr)                     \
+    do {                                  \
+        lbm_status st__ = (expr);         \
+        if (st__ != LBM_OK) return st__;  \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
+{
+    if (!d || !out) return LBM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d->q != 9 && d->q != 19) return LBM_ERR_INVALID_ARG;
+    if (d->precision != 4 && d->precision != 8) return LBM_ERR_INVALID_ARG;
+    if (d->nx < 2 || d->ny < 1 || d->nz < 1) return LBM_ERR_INVALID_ARG;
+    if (d->q == 9 && d->nz != 1) return LBM_ERR_INVALID_ARG;
+    if (d->n_steps < 1 || d->ckpt_stride < 0) return LBM_ERR_INVALID_ARG;
+    if (d->loss_kind != LBM_LOSS_VEC && d->loss_kind != LBM_LOSS_NORM) return LBM_ERR_INVALID_ARG;
+    if (d->loss_norm != LBM_NORM_SUM && d->loss_norm != LBM_NORM_MEAN_FLUID) return LBM_ERR_INVALID_ARG;
+    if (d->inlet_kind != LBM_INLET_CONST && d->inlet_kind != LBM_INLET_PROFILE) return LBM_ERR_INVALID_ARG;
+    const long long N = (long long)d->nx * d->ny * d->nz;
+    if (N > (1LL << 31) - 1) return LBM_ERR_INVALID_ARG;  // queue and disk scratch use 32-bit node ids
+    lbm_plan* p = new (std::nothrow) lbm_plan();
+    if (!p) return LBM_ERR_OOM;
+    p->desc = *d;
+    PlanInfo& I = p->info;
+    I.q = d->q;
+    I.d = d->q == 9 ? 2 : 3;
+    I.prec = d->precision;
+    I.geo.nx = d->nx;
+    I.geo.ny = d->ny;
+    I.geo.nz = d->nz;
+    I.geo.N = N;
+    I.geo.link = nullptr;
+    I.grid = dim3((unsigned)((d->nx + kStepThreads - 1) / kStepThreads), (unsigned)d->ny, (unsigned)d->nz);
+    I.n_blocks = (int)(I.grid.x * I.grid.y * I.grid.z);
+    I.n_in = d->inlet_kind == LBM_INLET_PROFILE ? d->ny * d->nz : 1;
+    I.n_acc = d->ny * d->nz;
+    I.state_bytes = (size_t)d->q * (size_t)N * (size_t)d->precision;
+    const int T = d->n_steps;
+    p->k = d->ckpt_stride > 0 ? std::min(d->ckpt_stride, T) : std::max(1, (int)std::ceil(std::sqrt((double)T)));
+    p->S = (T + p->k - 1) / p->k;
+    layout(p);
+    *out = p;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_destroy(lbm_plan* p)
+{
+    delete p;
+    return LBM_OK;
+}
+
+lbm_status lbm_workspace_size(const lbm_plan* p, size_t* bytes_out)
+{
+    if (!p || !bytes_out) return LBM_ERR_INVALID_ARG;
+    *bytes_out = p->ws.total;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_geometry(lbm_plan* p, const lbm_geom_desc* g, uint8_t* d_mask, uint32_t* d_link,
+                             double* d_porosity, int64_t* d_info, void* stream)
+{
+    if (!p || !g || !d_mask || !d_link || !d_info) return LBM_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(d_mask) & 3u) != 0) return LBM_ERR_INVALID_ARG;
+    if (g->kind < LBM_GEOM_CHANNEL || g->kind > LBM_GEOM_MASK) return LBM_ERR_INVALID_ARG;
+    if (g->kind == LBM_GEOM_DISKS && p->info.q != 9) return LBM_ERR_INVALID_ARG;
+    if (g->kind == LBM_GEOM_SPHERES && p->info.q != 19) return LBM_ERR_INVALID_ARG;
+    if (g->kind == LBM_GEOM_DISKS || g->kind == LBM_GEOM_SPHERES) {
+        if (g->r_min < 0 || g->r_max < g->r_min || g->r_max > 4096) return LBM_ERR_INVALID_ARG;
+        if (g->hydro_q8 < 0 || g->hydro_q8 > 256 || g->inlet_buffer < 1) return LBM_ERR_INVALID_ARG;
+        if (g->max_rejections < 1 || !(g->target_porosity >= 0.0 && g->target_porosity <= 1.0))
+            return LBM_ERR_INVALID_ARG;
+        if ((long long)p->info.geo.nx * 256 > (1LL << 30)) return LBM_ERR_INVALID_ARG;
+    }
+    LBM_TRY(geometry_launch(p->info, *g, d_mask, d_link, d_porosity, d_info, static_cast<cudaStream_t>(stream)));
+    p->mask = d_mask;
+    p->link = d_link;
+    p->info.geo.link = d_link;
+    return LBM_OK;
+}
+
+lbm_status lbm_bind_geometry(lbm_plan* p, const uint32_t* d_link)
+{
+    if (!p || !d_link) return LBM_ERR_INVALID_ARG;
+    p->link = const_cast<uint32_t*>(d_link);
+    p->info.geo.link = d_link;
+    return LBM_OK;
+}
+
+lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out, void* d_f,
+                       void* d_ws, void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    if (!d_rho_in || !d_tau || !d_f || !d_ws) return LBM_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = bytes(d_ws);
+    p->last_ws = d_ws;
+    const Bc bc = make_bc(p, d_rho_in, rho_out);
+    const int T = p->desc.n_steps, k = p->k, S = p->S;
+    const size_t st = align256(p->info.state_bytes);
+    auto slot = [&](int t) -> unsigned char* {  // checkpoint slot of g^t, or nullptr
+        const int s1 = t + 1;
+        if (s1 % k == 0 && s1 / k >= 1 && s1 / k <= S - 1) return ws + p->ws.ckpt + st * (size_t)(s1 / k - 1);
+        return nullptr;
+    };
+    unsigned char* ping0 = ws + p->ws.ping[0];
+    unsigned char* ping1 = ws + p->ws.ping[1];
+    // g^0 = rest
+    unsigned char* cur = slot(0);
+    if (!cur) cur = ping0;
+    if (cudaMemsetAsync(cur, 0, p->info.state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
+    for (int t = 1; t <= T - 1; ++t) {
+        unsigned char* dst = slot(t);
+        if (!dst) dst = (cur == ping0) ? ping1 : ping0;
+        LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, s));
+        cur = dst;
+    }
+    return step_launch(p->info, kStreamOnly, cur, d_f, bc, d_tau, s);
+}
+
+lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out, const void* d_f_in,
+                    void* d_f_out, int32_t n_steps, void* d_ws, void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    if (!d_rho_in || !d_tau || !d_f_in || !d_f_out || !d_ws || n_steps < 1) return LBM_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = bytes(d_ws);
+    const Bc bc = make_bc(p, d_rho_in, rho_out);
+    unsigned char* ping0 = ws + p->ws.ping[0];
+    unsigned char* ping1 = ws + p->ws.ping[1];
+    LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, d_tau, s));
+    unsigned char* cur = ping0;
+    for (int t = 1; t < n_steps; ++t) {
+        unsigned char* dst = cur == ping0 ? ping1 : ping0;
+        LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, s));
+        cur = dst;
+    }
+    return step_launch(p->info, kStreamOnly, cur, d_f_out, bc, d_tau, s);
+}
+
+lbm_status lbm_loss_grad(lbm_plan* p, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
+                         double* d_loss, void* d_lambda, void* d_ws, void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    if (!d_f || !d_u_target || !d_loss || !d_lambda || !d_ws) return LBM_ERR_INVALID_ARG;
+    p->last_ws = d_ws;
+    return loss_launch(p->info, d_f, d_u_target, d_roi, p->desc.loss_kind, p->desc.loss_norm, d_loss, d_lambda,
+                       bytes(d_ws), p->ws, static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
+                       const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    if (!d_rho_in || !d_tau || !d_lambda || !d_grad_rho_in || !d_grad_tau || !d_ws) return LBM_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = bytes(d_ws);
+    p->last_ws = d_ws;
+    const Bc bc = make_bc(p, d_rho_in, rho_out);
+    const int T = p->desc.n_steps, k = p->k, S = p->S;
+    const size_t st = align256(p->info.state_bytes);
+    double* grad_acc = reinterpret_cast<double*>(ws + p->ws.grad_acc);
+    double* partial = reinterpret_cast<double*>(ws + p->ws.partial);
+    if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, s) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_blocks, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    const void* lam_cur = d_lambda;
+    int lam_next = 0;
+    for (int sg = S - 1; sg >= 0; --sg) {
+        const int t0 = sg * k, len = std::min(k, T - t0);
+        // segp[j] holds g^{t0 + j - 1}; for sg = 0, j = 0 stands for the rest state f^0
+        auto seg = [&](int j) -> unsigned char* { return ws + p->ws.seg + st * (size_t)j; };
+        const unsigned char* base = sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
+        const unsigned char* prev = base;
+        for (int j = 1; j < len; ++j) {
+            if (sg == 0 && j == 1) {
+                if (cudaMemsetAsync(seg(1), 0, p->info.state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
+            } else {
+                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(j), bc, d_tau, s));
+            }
+            prev = seg(j);
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const unsigned char* src = j == 0 ? base : seg(j);
+            const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
+            void* lam_out = ws + p->ws.lam[lam_next];
+            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, d_tau, grad_acc, partial, s));
+            lam_cur = lam_out;
+            lam_next ^= 1;
+        }
+    }
+    return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
+                                   reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
+}
+
+lbm_status lbm_macroscopic(lbm_plan* p, const void* d_f, double* d_rho, double* d_u, void* stream)
+{
+    LBM_TRY(check_common(p, nullptr));
+    if (!d_f || !d_u) return LBM_ERR_INVALID_ARG;
+    return macroscopic_launch(p->info, d_f, d_rho, d_u, static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_darcy(lbm_plan* p, const void* d_f, const double* d_rho_in, const double* d_tau, double rho_out,
+                     int32_t xs, double* d_k, double* d_flux, void* stream)
+{
+    LBM_TRY(check_common(p, nullptr));
+    if (!d_f || !d_rho_in || !d_tau || !d_k || xs < 0 || xs >= p->info.geo.nx) return LBM_ERR_INVALID_ARG;
+    return darcy_launch(p->info, d_f, d_rho_in, p->info.n_in, d_tau, rho_out, xs, d_k, d_flux,
+                        static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_adam_step(int32_t n, double* d_theta, double* d_m, double* d_v, const double* d_grad_p, double* d_p,
+                         double p_offset, double p_scale, int32_t t, double lr, double beta1, double beta2,
+                         double eps, void* stream)
+{
+    if (n < 1 || n > 65536 || t < 1 || !d_theta || !d_m || !d_v || !d_grad_p || !d_p) return LBM_ERR_INVALID_ARG;
+    return adam_launch(n, d_theta, d_m, d_v, d_grad_p, d_p, p_offset, p_scale, t, lr, beta1, beta2, eps,
+                       static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_get_status(lbm_plan* p, lbm_status* status)
+{
+    if (!p || !status) return LBM_ERR_INVALID_ARG;
+    *status = LBM_OK;
+    if (!p->last_ws) return LBM_OK;
+    uint32_t word = 0;
+    uint32_t* dev = reinterpret_cast<uint32_t*>(bytes(p->last_ws) + p->ws.status);
+    if (cudaMemcpy(&word, dev, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemset(dev, 0, sizeof(word)) != cudaSuccess) return LBM_ERR_CUDA;
+    for (int b = 1; b < 32; ++b)
+        if (word & (1u << b)) {
+            *status = static_cast<lbm_status>(b);
+            break;
+        }
+    return LBM_OK;
+}
+
+const char* lbm_error_string(lbm_status st)
+{
+    switch (st) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case LBM_ERR_OOM: return "buffer too small";
+    case LBM_ERR_CUDA: return "CUDA runtime error";
+    case LBM_ERR_NONFINITE: return "non-finite loss or gradient";
+    case LBM_ERR_TIMEOUT: return "device-side wait timed out";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,303 @@
+// Loss at the final step and its seed, gradient finalisation, macroscopic
+// fields, Darcy permeability and the Adam update (arXiv 2310.00810:
+// compute_loss of section 2.2, Eq. 7, Eq. 15, Eq. 12, Eq. 9, section 3.4).
+//
+// All sums over nodes are FP64: per-block partials (warp shuffles, then
+// shared memory) followed by one fixed-order pass, so results are
+// deterministic run to run.
+#include "device.cuh"
+
+namespace lbm {
+
+// Fixed-order sum of a[0..n) by one block of kReduceThreads threads.
+__device__ double block_reduce_array(const double* __restrict__ a, long long n)
+{
+    double v = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) v += a[i];
+    return block_sum(v, threadIdx.x, blockDim.x);
+}
+
+// -------------------------------------------------------------- loss
+
+__global__ void __launch_bounds__(kStepThreads) k_count_roi(Geo g, const uint8_t* __restrict__ roi,
+                                                            double* __restrict__ partial)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const long long n = ((long long)z * g.ny + y) * g.nx + x;
+    double c = 0.0;
+    if (x < g.nx && !(g.link[n] & kLinkSolid) && (!roi || roi[n])) c = 1.0;
+    const double bs = block_sum(c, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = bs;
+}
+
+// weight = 1 (sum) or 1 / count (mean over ROI fluid nodes)
+__global__ void k_loss_weight(const double* __restrict__ partial, int nb, int mean, double* __restrict__ scalars)
+{
+    const double c = block_reduce_array(partial, nb);
+    if (threadIdx.x == 0) {
+        scalars[0] = c;
+        scalars[1] = mean ? (c > 0.0 ? 1.0 / c : 0.0) : 1.0;
+    }
+}
+
+// Per node: u from shifted f^T; loss term; lambda^T_k = sum_a dL/du_a (c_ka - u_a) / rho.
+template <int Q, typename T, int KIND>
+__global__ void __launch_bounds__(kStepThreads)
+    k_loss(const T* __restrict__ f, const double* __restrict__ ut, const uint8_t* __restrict__ roi, Geo g,
+           const double* __restrict__ weight, T* __restrict__ lam, double* __restrict__ partial)
+{
+    using L = Lattice<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    const long long N = g.N;
+    const long long n = ((long long)z * g.ny + y) * g.nx + x;
+    double term = 0.0;
+    if (x < g.nx) {
+        const uint32_t lw = g.link[n];
+        T out[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) out[i] = T(0);
+        if (!(lw & kLinkSolid) && (!roi || roi[n])) {
+            T v[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) v[i] = f[(long long)i * N + n];
+            T drho, rho, u[3];
+            moments<Q, T>(v, drho, rho, u);
+            const double wgt = *weight;
+            double du[3] = {0.0, 0.0, 0.0};
+            if (KIND == LBM_LOSS_VEC) {
+#pragma unroll
+                for (int a = 0; a < L::D; ++a) {
+                    const double e = (double)u[a] - ut[(long long)a * N + n];
+                    term += wgt * e * e;
+                    du[a] = 2.0 * wgt * e;
+                }
+            } else {
+                double uu = 0.0, tt = 0.0;
+#pragma unroll
+                for (int a = 0; a < L::D; ++a) {
+                    uu += (double)u[a] * (double)u[a];
+                    const double t = ut[(long long)a * N + n];
+                    tt += t * t;
+                }
+                const double un = sqrt(uu);
+                const double e = un - sqrt(tt);
+                term += wgt * e * e;
+                if (uu != 0.0)
+#pragma unroll
+                    for (int a = 0; a < L::D; ++a) du[a] = 2.0 * wgt * e * (double)u[a] / un;
+            }
+            const T inv = T(1) / rho;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                T s = 0;
+#pragma unroll
+                for (int a = 0; a < L::D; ++a) s += T(du[a]) * (T(L::c(k, a)) - u[a]);
+                out[k] = s * inv;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) lam[(long long)k * N + n] = out[k];
+    }
+    const double bs = block_sum(term, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = bs;
+}
+
+__global__ void k_loss_final(const double* __restrict__ partial, int nb, double* __restrict__ d_loss,
+                             uint32_t* __restrict__ status)
+{
+    const double L = block_reduce_array(partial, nb);
+    if (threadIdx.x == 0) {
+        *d_loss = L;
+        if (!isfinite(L)) atomicOr(status, 1u << LBM_ERR_NONFINITE);
+    }
+}
+
+template <int Q, typename T>
+static void loss_impl(const PlanInfo& p, const void* f, const double* ut, const uint8_t* roi, int kind, int norm,
+                      double* d_loss, void* lambda, unsigned char* ws, const Workspace& w, cudaStream_t s)
+{
+    double* partial = reinterpret_cast<double*>(ws + w.partial2);
+    double* scalars = reinterpret_cast<double*>(ws + w.status + kScalarCount);
+    uint32_t* status = reinterpret_cast<uint32_t*>(ws + w.status);
+    k_count_roi<<<p.grid, kStepThreads, 0, s>>>(p.geo, roi, partial);
+    k_loss_weight<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, norm == LBM_NORM_MEAN_FLUID, scalars);
+    const T* fp = static_cast<const T*>(f);
+    T* lp = static_cast<T*>(lambda);
+    if (kind == LBM_LOSS_VEC)
+        k_loss<Q, T, LBM_LOSS_VEC><<<p.grid, kStepThreads, 0, s>>>(fp, ut, roi, p.geo, scalars + 1, lp, partial);
+    else
+        k_loss<Q, T, LBM_LOSS_NORM><<<p.grid, kStepThreads, 0, s>>>(fp, ut, roi, p.geo, scalars + 1, lp, partial);
+    k_loss_final<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, d_loss, status);
+}
+
+lbm_status loss_launch(const PlanInfo& p, const void* f, const double* u_target, const uint8_t* roi, int kind,
+                       int norm, double* d_loss, void* lambda, unsigned char* ws, const Workspace& w,
+                       cudaStream_t s)
+{
+    if (p.q == 9 && p.prec == 4) loss_impl<9, float>(p, f, u_target, roi, kind, norm, d_loss, lambda, ws, w, s);
+    else if (p.q == 9 && p.prec == 8) loss_impl<9, double>(p, f, u_target, roi, kind, norm, d_loss, lambda, ws, w, s);
+    else if (p.q == 19 && p.prec == 4) loss_impl<19, float>(p, f, u_target, roi, kind, norm, d_loss, lambda, ws, w, s);
+    else if (p.q == 19 && p.prec == 8)
+        loss_impl<19, double>(p, f, u_target, roi, kind, norm, d_loss, lambda, ws, w, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+// ----------------------------------------------------- gradient finalise
+
+// dL/dtau = -(sum of dL/domega partials) / tau^2 ; dL/drho_in from the
+// per-inlet-node accumulators (summed for a constant head).
+__global__ void k_finish_gradients(const double* __restrict__ grad_acc, int n_acc, int profile,
+                                   const double* __restrict__ partial, int nb, const double* __restrict__ tau,
+                                   double* __restrict__ g_rho_in, double* __restrict__ g_tau,
+                                   uint32_t* __restrict__ status)
+{
+    const double gw = block_reduce_array(partial, nb);
+    double gsum = 0.0;
+    if (!profile) gsum = block_reduce_array(grad_acc, n_acc);
+    bool bad = false;
+    if (profile)
+        for (int i = threadIdx.x; i < n_acc; i += blockDim.x) {
+            g_rho_in[i] = grad_acc[i];
+            bad |= !isfinite(grad_acc[i]);
+        }
+    if (threadIdx.x == 0) {
+        const double t = *tau;
+        *g_tau = -gw / (t * t);
+        if (!profile) g_rho_in[0] = gsum;
+        bad |= !isfinite(gw) || !isfinite(gsum);
+    }
+    if (bad) atomicOr(status, 1u << LBM_ERR_NONFINITE);
+}
+
+lbm_status finish_gradients_launch(const PlanInfo& p, const double* grad_acc, const double* partial,
+                                   const double* tau, double* d_grad_rho_in, double* d_grad_tau, uint32_t* status,
+                                   cudaStream_t s)
+{
+    k_finish_gradients<<<1, kReduceThreads, 0, s>>>(grad_acc, p.n_acc, p.n_in > 1 ? 1 : 0, partial, p.n_blocks, tau,
+                                                    d_grad_rho_in, d_grad_tau, status);
+    return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------- macroscopic
+
+template <int Q, typename T>
+__global__ void __launch_bounds__(kStepThreads)
+    k_macroscopic(const T* __restrict__ f, Geo g, double* __restrict__ rho_out, double* __restrict__ u_out)
+{
+    using L = Lattice<Q>;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long N = g.N, n = ((long long)z * g.ny + y) * g.nx + x;
+    double r = 0.0, u[3] = {0.0, 0.0, 0.0};
+    if (!(g.link[n] & kLinkSolid)) {
+        double s = 0.0, j[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const double v = (double)f[(long long)i * N + n];
+            s += v;
+#pragma unroll
+            for (int a = 0; a < L::D; ++a) j[a] += L::c(i, a) * v;
+        }
+        r = 1.0 + s;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) u[a] = j[a] / r;
+    }
+    if (rho_out) rho_out[n] = r;
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) u_out[(long long)a * N + n] = u[a];
+}
+
+lbm_status macroscopic_launch(const PlanInfo& p, const void* f, double* rho, double* u, cudaStream_t s)
+{
+    if (p.q == 9 && p.prec == 4)
+        k_macroscopic<9, float><<<p.grid, kStepThreads, 0, s>>>(static_cast<const float*>(f), p.geo, rho, u);
+    else if (p.q == 9 && p.prec == 8)
+        k_macroscopic<9, double><<<p.grid, kStepThreads, 0, s>>>(static_cast<const double*>(f), p.geo, rho, u);
+    else if (p.q == 19 && p.prec == 4)
+        k_macroscopic<19, float><<<p.grid, kStepThreads, 0, s>>>(static_cast<const float*>(f), p.geo, rho, u);
+    else if (p.q == 19 && p.prec == 8)
+        k_macroscopic<19, double><<<p.grid, kStepThreads, 0, s>>>(static_cast<const double*>(f), p.geo, rho, u);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------------------------- Darcy
+
+// k = nu J / (dp/dx), J = section mean of rho u_x, nu = (tau - 1/2)/3 (Eq. 9),
+// dp/dx = (mean rho_in - rho_out) / (3 nx)  (Eq. 12).
+template <int Q, typename T>
+__global__ void k_darcy(const T* __restrict__ f, Geo g, const double* __restrict__ rho_in, int n_in,
+                        const double* __restrict__ tau, double rho_out, int xs, double* __restrict__ k,
+                        double* __restrict__ flux)
+{
+    using L = Lattice<Q>;
+    const long long N = g.N;
+    const long long cells = (long long)g.ny * g.nz;
+    double J = 0.0;
+    for (long long c = threadIdx.x; c < cells; c += blockDim.x) {
+        const long long n = c * g.nx + xs;  // c = z * ny + y
+        if (g.link[n] & kLinkSolid) continue;
+        double jx = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            if (L::c(i, 0) != 0) jx += L::c(i, 0) * (double)f[(long long)i * N + n];
+        J += jx;  // rho u_x = sum_i c_ix f_i (the rest shift has zero momentum)
+    }
+    J = block_sum(J, threadIdx.x, blockDim.x);
+    const double rin = block_reduce_array(rho_in, n_in);
+    if (threadIdx.x == 0) {
+        J /= (double)cells;
+        const double nu = (*tau - 0.5) / 3.0;
+        const double dpdx = (rin / n_in - rho_out) / (3.0 * g.nx);
+        *k = nu * J / dpdx;
+        if (flux) *flux = J;
+    }
+}
+
+lbm_status darcy_launch(const PlanInfo& p, const void* f, const double* rho_in, int n_in, const double* tau,
+                        double rho_out, int xs, double* k, double* flux, cudaStream_t s)
+{
+    if (p.q == 9 && p.prec == 4)
+        k_darcy<9, float><<<1, kReduceThreads, 0, s>>>(static_cast<const float*>(f), p.geo, rho_in, n_in, tau,
+                                                        rho_out, xs, k, flux);
+    else if (p.q == 9 && p.prec == 8)
+        k_darcy<9, double><<<1, kReduceThreads, 0, s>>>(static_cast<const double*>(f), p.geo, rho_in, n_in, tau,
+                                                         rho_out, xs, k, flux);
+    else if (p.q == 19 && p.prec == 4)
+        k_darcy<19, float><<<1, kReduceThreads, 0, s>>>(static_cast<const float*>(f), p.geo, rho_in, n_in, tau,
+                                                         rho_out, xs, k, flux);
+    else if (p.q == 19 && p.prec == 8)
+        k_darcy<19, double><<<1, kReduceThreads, 0, s>>>(static_cast<const double*>(f), p.geo, rho_in, n_in, tau,
+                                                          rho_out, xs, k, flux);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+// -------------------------------------------------------------- Adam
+
+__global__ void k_adam(int n, double* __restrict__ theta, double* __restrict__ m, double* __restrict__ v,
+                       const double* __restrict__ grad_p, double* __restrict__ p, double off, double scale, double bc1,
+                       double bc2, double lr, double b1, double b2, double eps)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double g = grad_p[i] * scale;  // dL/dtheta = dL/dp * dp/dtheta
+    const double mi = b1 * m[i] + (1.0 - b1) * g;
+    const double vi = b2 * v[i] + (1.0 - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    const double th = theta[i] - lr * (mi / bc1) / (sqrt(vi / bc2) + eps);
+    theta[i] = th;
+    p[i] = off + scale * th;
+}
+
+lbm_status adam_launch(int n, double* theta, double* m, double* v, const double* grad_p, double* p, double off,
+                       double scale, int t, double lr, double b1, double b2, double eps, cudaStream_t s)
+{
+    const double bc1 = 1.0 - pow(b1, (double)t), bc2 = 1.0 - pow(b2, (double)t);
+    k_adam<<<(n + 255) / 256, 256, 0, s>>>(n, theta, m, v, grad_p, p, off, scale, bc1, bc2, lr, b1, b2, eps);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lbm

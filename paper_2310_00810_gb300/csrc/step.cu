@@ -1,0 +1,75 @@
+// Forward lattice update: fused pull-streaming, halfway bounce-back,
+// anti-bounce-back pressure planes and BGK collision (arXiv 2310.00810,
+// section 2.1, Eq. 1-6, and the "Bounce Back" stage of section 2.2).
+//
+// The library keeps the POST-collision state g^t = f*^t in memory, so one
+// launch in stream-collide mode computes g^{t+1} = C(S(g^t)): each node
+// pulls what streams into it (from x - c_i), applies the boundary rules on
+// its own links, then collides in registers and stores locally.  The paper's
+// cycle f^{t+1} = S(C(f^t)) is recovered as
+//     f^T = S o (C o S)^{T-1} o C (f^0),
+// i.e. one collide-only launch (or the rest state, which collision leaves
+// unchanged), T - 1 stream-collide launches and one stream-only launch.
+// Populations are stored shifted by the rest state (f - w_i), which keeps
+// FP32 from cancelling 1 - 1e-4 size differences.
+//
+// Link rules for what fluid node x receives in direction i (the link from
+// x - c_i):
+//   bounce-back bit i set in the link word   ->  g_opp(i)(x)
+//   x - c_i beyond the plane x = -1/2 / nx - 1/2 (and not a wall link)
+//        -> -g_opp(i)(x) + 2 w_i (rho_w (1 + 4.5 (c_i.u_w)^2 - 1.5 u_w.u_w) - 1)   (Eq. 6,
+//           shifted; u_w is the node's own velocity at time t, from its
+//           post-collision populations, which collision does not change)
+//   otherwise                                  ->  g_i(x - c_i)
+#include "device.cuh"
+
+namespace lbm {
+
+template <int Q, typename T, int MODE>
+__global__ void __launch_bounds__(kStepThreads) k_step(const T* __restrict__ src, T* __restrict__ dst, Geo g, Bc bc,
+                                                        const double* __restrict__ tau)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
+    if (x >= g.nx) return;
+    const long long n = ((long long)z * g.ny + y) * g.nx + x;
+    const uint32_t lw = g.link[n];
+    if (lw & kLinkSolid) return;
+    T v[Q];
+    if (MODE == kCollideOnly) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = src[(long long)i * g.N + n];
+    } else {
+        pull<Q, T>(v, src, n, x, y, z, lw, g, bc);
+    }
+    if (MODE != kStreamOnly) collide<Q, T>(v, T(1.0 / *tau));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[(long long)i * g.N + n] = v[i];
+}
+
+template <int Q, typename T>
+static void launch(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
+                   cudaStream_t s)
+{
+    const T* a = static_cast<const T*>(src);
+    T* b = static_cast<T*>(dst);
+    dim3 block(kStepThreads);
+    if (mode == kStreamCollide)
+        k_step<Q, T, kStreamCollide><<<p.grid, block, 0, s>>>(a, b, p.geo, bc, tau);
+    else if (mode == kCollideOnly)
+        k_step<Q, T, kCollideOnly><<<p.grid, block, 0, s>>>(a, b, p.geo, bc, tau);
+    else
+        k_step<Q, T, kStreamOnly><<<p.grid, block, 0, s>>>(a, b, p.geo, bc, tau);
+}
+
+lbm_status step_launch(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
+                       cudaStream_t s)
+{
+    if (p.q == 9 && p.prec == 4) launch<9, float>(p, mode, src, dst, bc, tau, s);
+    else if (p.q == 9 && p.prec == 8) launch<9, double>(p, mode, src, dst, bc, tau, s);
+    else if (p.q == 19 && p.prec == 4) launch<19, float>(p, mode, src, dst, bc, tau, s);
+    else if (p.q == 19 && p.prec == 8) launch<19, double>(p, mode, src, dst, bc, tau, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lbm

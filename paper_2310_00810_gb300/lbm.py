@@ -1,0 +1,316 @@
+"""Thin ctypes binding of the C ABI in ``include/lbm.h`` (``liblbm.so``).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch tensors become device pointers, the current torch
+CUDA stream becomes the ``cudaStream_t``.  All lattice work runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library has not
+been built (``python -m paper_2310_00810_gb300.build``) loading fails loudly.
+
+``Solver`` bundles one plan with the device buffers it needs (allocated by
+torch) for the common single-instance use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT = range(7)
+LBM_LOSS_VEC, LBM_LOSS_NORM = 0, 1
+LBM_NORM_SUM, LBM_NORM_MEAN_FLUID = 0, 1
+LBM_INLET_CONST, LBM_INLET_PROFILE = 0, 1
+LBM_GEOM_CHANNEL, LBM_GEOM_DISKS, LBM_GEOM_SPHERES, LBM_GEOM_MASK = 0, 1, 2, 3
+LBM_LINK_SOLID = 0x80000000
+
+ENTRY_POINTS = (
+    "lbm_plan_create", "lbm_plan_destroy", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
+    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
+    "lbm_get_status", "lbm_error_string",
+)
+
+
+class lbm_desc(C.Structure):
+    _fields_ = [("q", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("precision", C.c_int32), ("n_steps", C.c_int32), ("ckpt_stride", C.c_int32),
+                ("loss_kind", C.c_int32), ("loss_norm", C.c_int32), ("inlet_kind", C.c_int32)]
+
+
+class lbm_geom_desc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("r_min", C.c_int32), ("r_max", C.c_int32), ("hydro_q8", C.c_int32),
+                ("inlet_buffer", C.c_int32), ("fill_isolated", C.c_int32), ("max_rejections", C.c_int64),
+                ("seed", C.c_uint64), ("target_porosity", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {lbm_error_string(status)} (status {status})")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblbm.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = library_path()
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with `python -m paper_2310_00810_gb300.build`")
+            lib = C.CDLL(path)
+            vp, i32, f64 = C.c_void_p, C.c_int32, C.c_double
+            sig = {
+                "lbm_plan_create": [C.POINTER(lbm_desc), C.POINTER(vp)],
+                "lbm_plan_destroy": [vp],
+                "lbm_workspace_size": [vp, C.POINTER(C.c_size_t)],
+                "lbm_init_geometry": [vp, C.POINTER(lbm_geom_desc), vp, vp, vp, vp, vp],
+                "lbm_bind_geometry": [vp, vp],
+                "lbm_forward": [vp, vp, vp, f64, vp, vp, vp],
+                "lbm_step": [vp, vp, vp, f64, vp, vp, i32, vp, vp],
+                "lbm_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
+                "lbm_adjoint": [vp, vp, vp, f64, vp, vp, vp, vp, vp],
+                "lbm_macroscopic": [vp, vp, vp, vp, vp],
+                "lbm_darcy": [vp, vp, vp, vp, f64, i32, vp, vp, vp],
+                "lbm_adam_step": [i32, vp, vp, vp, vp, vp, f64, f64, i32, f64, f64, f64, f64, vp],
+                "lbm_get_status": [vp, C.POINTER(C.c_int)],
+                "lbm_error_string": [C.c_int],
+            }
+            for name, args in sig.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = C.c_char_p if name == "lbm_error_string" else C.c_int
+            _lib = lib
+        return _lib
+
+
+def _ptr(t: torch.Tensor | None, dtype: torch.dtype | None = None, numel: int | None = None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"tensor has {t.numel()} elements, needs {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(st: int, where: str) -> None:
+    if st != LBM_OK:
+        raise LBMError(st, where)
+
+
+def lbm_error_string(status: int) -> str:
+    return load().lbm_error_string(int(status)).decode()
+
+
+class Plan:
+    """Owns an ``lbm_plan*``; attributes mirror ``lbm_desc``."""
+
+    def __init__(self, q, nx, ny, nz=1, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
+                 loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST):
+        self.desc = lbm_desc(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+        h = C.c_void_p()
+        _check(load().lbm_plan_create(C.byref(self.desc), C.byref(h)), "lbm_plan_create")
+        self.handle = h
+        self.q, self.nx, self.ny, self.nz = q, nx, ny, nz
+        self.precision, self.n_steps = precision, n_steps
+        self.inlet_kind = inlet_kind
+        self.d = 2 if q == 9 else 3
+        self.N = nx * ny * nz
+        self.n_in = ny * nz if inlet_kind == LBM_INLET_PROFILE else 1
+        self.dtype = torch.float32 if precision == 4 else torch.float64
+
+    @property
+    def shape(self):
+        """Node-field shape: (ny, nx) for D2Q9, (nz, ny, nx) for D3Q19."""
+        return (self.ny, self.nx) if self.q == 9 else (self.nz, self.ny, self.nx)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.lbm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lbm_plan_create(q, nx, ny, nz=1, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
+                    loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST) -> Plan:
+    return Plan(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+
+
+def lbm_plan_destroy(plan: Plan) -> None:
+    plan.close()
+
+
+def lbm_workspace_size(plan: Plan) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_workspace_size(plan.handle, C.byref(n)), "lbm_workspace_size")
+    return n.value
+
+
+def lbm_init_geometry(plan: Plan, mask, link, info, porosity=None, kind=LBM_GEOM_CHANNEL, seed=0, r_min=6,
+                      r_max=12, target_porosity=1.0, hydro_q8=256, inlet_buffer=8, fill_isolated=True,
+                      max_rejections=1_000_000, stream=None) -> None:
+    g = lbm_geom_desc(kind, r_min, r_max, hydro_q8, inlet_buffer, 1 if fill_isolated else 0, max_rejections,
+                      seed, float(target_porosity))
+    _check(load().lbm_init_geometry(plan.handle, C.byref(g), _ptr(mask, torch.uint8, plan.N),
+                                    _ptr(link, torch.int32, plan.N), _ptr(porosity, torch.float64, 1),
+                                    _ptr(info, torch.int64, 4), _stream(stream)), "lbm_init_geometry")
+    plan._link = link  # keep the bound geometry alive with the plan
+    plan._mask = mask
+
+
+def lbm_bind_geometry(plan: Plan, link) -> None:
+    _check(load().lbm_bind_geometry(plan.handle, _ptr(link, torch.int32, plan.N)), "lbm_bind_geometry")
+    plan._link = link
+
+
+def lbm_forward(plan: Plan, rho_in, tau, rho_out: float, f, ws, stream=None) -> None:
+    _check(load().lbm_forward(plan.handle, _ptr(rho_in, torch.float64, plan.n_in), _ptr(tau, torch.float64, 1),
+                              float(rho_out), _ptr(f, plan.dtype, plan.q * plan.N), _ptr(ws, torch.uint8),
+                              _stream(stream)), "lbm_forward")
+
+
+def lbm_step(plan: Plan, rho_in, tau, rho_out: float, f_in, f_out, n_steps: int, ws, stream=None) -> None:
+    _check(load().lbm_step(plan.handle, _ptr(rho_in, torch.float64, plan.n_in), _ptr(tau, torch.float64, 1),
+                           float(rho_out), _ptr(f_in, plan.dtype, plan.q * plan.N),
+                           _ptr(f_out, plan.dtype, plan.q * plan.N), int(n_steps), _ptr(ws, torch.uint8),
+                           _stream(stream)), "lbm_step")
+
+
+def lbm_loss_grad(plan: Plan, f, u_target, roi, loss, lam, ws, stream=None) -> None:
+    _check(load().lbm_loss_grad(plan.handle, _ptr(f, plan.dtype, plan.q * plan.N),
+                                _ptr(u_target, torch.float64, plan.d * plan.N), _ptr(roi, torch.uint8, plan.N),
+                                _ptr(loss, torch.float64, 1), _ptr(lam, plan.dtype, plan.q * plan.N),
+                                _ptr(ws, torch.uint8), _stream(stream)), "lbm_loss_grad")
+
+
+def lbm_adjoint(plan: Plan, rho_in, tau, rho_out: float, lam, grad_rho_in, grad_tau, ws, stream=None) -> None:
+    _check(load().lbm_adjoint(plan.handle, _ptr(rho_in, torch.float64, plan.n_in), _ptr(tau, torch.float64, 1),
+                              float(rho_out), _ptr(lam, plan.dtype, plan.q * plan.N),
+                              _ptr(grad_rho_in, torch.float64, plan.n_in), _ptr(grad_tau, torch.float64, 1),
+                              _ptr(ws, torch.uint8), _stream(stream)), "lbm_adjoint")
+
+
+def lbm_macroscopic(plan: Plan, f, rho, u, stream=None) -> None:
+    _check(load().lbm_macroscopic(plan.handle, _ptr(f, plan.dtype, plan.q * plan.N), _ptr(rho, torch.float64, plan.N),
+                                  _ptr(u, torch.float64, plan.d * plan.N), _stream(stream)), "lbm_macroscopic")
+
+
+def lbm_darcy(plan: Plan, f, rho_in, tau, rho_out: float, xs: int, k, flux=None, stream=None) -> None:
+    _check(load().lbm_darcy(plan.handle, _ptr(f, plan.dtype, plan.q * plan.N), _ptr(rho_in, torch.float64, plan.n_in),
+                            _ptr(tau, torch.float64, 1), float(rho_out), int(xs), _ptr(k, torch.float64, 1),
+                            _ptr(flux, torch.float64, 1), _stream(stream)), "lbm_darcy")
+
+
+def lbm_adam_step(theta, m, v, grad_p, p, p_offset: float, p_scale: float, t: int, lr: float, beta1=0.9,
+                  beta2=0.999, eps=1e-8, stream=None) -> None:
+    n = theta.numel()
+    _check(load().lbm_adam_step(n, _ptr(theta, torch.float64), _ptr(m, torch.float64, n), _ptr(v, torch.float64, n),
+                                _ptr(grad_p, torch.float64, n), _ptr(p, torch.float64, n), float(p_offset),
+                                float(p_scale), int(t), float(lr), float(beta1), float(beta2), float(eps),
+                                _stream(stream)), "lbm_adam_step")
+
+
+def lbm_get_status(plan: Plan) -> int:
+    st = C.c_int()
+    _check(load().lbm_get_status(plan.handle, C.byref(st)), "lbm_get_status")
+    return st.value
+
+
+class Solver:
+    """One plan with its geometry and workspace held in torch device memory.
+
+    ``geometry``: dict of ``lbm_init_geometry`` keyword arguments (kind, seed,
+    r_min, r_max, target_porosity, ...), or a uint8 mask tensor (kind MASK)."""
+
+    def __init__(self, q, nx, ny, nz=1, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
+                 loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST, geometry=None, device="cuda", link=None,
+                 mask=None):
+        self.device = torch.device(device)
+        self.plan = Plan(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+        p = self.plan
+        self.ws = torch.zeros(lbm_workspace_size(p), dtype=torch.uint8, device=self.device)
+        if link is not None:
+            self.link, self.mask = link, mask
+            lbm_bind_geometry(p, link)
+            self.info = None
+            self.porosity = None
+        else:
+            self.mask = torch.zeros(((p.N + 3) // 4) * 4, dtype=torch.uint8, device=self.device)
+            self.link = torch.zeros(p.N, dtype=torch.int32, device=self.device)
+            self.info = torch.zeros(4, dtype=torch.int64, device=self.device)
+            self.porosity = torch.zeros(1, dtype=torch.float64, device=self.device)
+            if isinstance(geometry, torch.Tensor):
+                self.mask[: p.N].copy_(geometry.reshape(-1).to(torch.uint8))
+                lbm_init_geometry(p, self.mask, self.link, self.info, self.porosity, kind=LBM_GEOM_MASK,
+                                  fill_isolated=False)
+            else:
+                lbm_init_geometry(p, self.mask, self.link, self.info, self.porosity, **(geometry or {}))
+
+    @property
+    def mask_field(self) -> torch.Tensor:
+        return self.mask[: self.plan.N].reshape(self.plan.shape)
+
+    def new_state(self) -> torch.Tensor:
+        return torch.empty((self.plan.q, *self.plan.shape), dtype=self.plan.dtype, device=self.device)
+
+    def forward(self, rho_in, tau, rho_out, f=None):
+        f = self.new_state() if f is None else f
+        lbm_forward(self.plan, rho_in, tau, rho_out, f, self.ws)
+        return f
+
+    def step(self, rho_in, tau, rho_out, f_in, n_steps, f_out=None):
+        f_out = torch.empty_like(f_in) if f_out is None else f_out
+        lbm_step(self.plan, rho_in, tau, rho_out, f_in, f_out, n_steps, self.ws)
+        return f_out
+
+    def loss_grad(self, f, u_target, roi=None):
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        lam = self.new_state()
+        lbm_loss_grad(self.plan, f, u_target, roi, loss, lam, self.ws)
+        return loss, lam
+
+    def adjoint(self, rho_in, tau, rho_out, lam):
+        g_in = torch.zeros(self.plan.n_in, dtype=torch.float64, device=self.device)
+        g_tau = torch.zeros(1, dtype=torch.float64, device=self.device)
+        lbm_adjoint(self.plan, rho_in, tau, rho_out, lam, g_in, g_tau, self.ws)
+        return g_in, g_tau
+
+    def macroscopic(self, f):
+        rho = torch.empty(self.plan.shape, dtype=torch.float64, device=self.device)
+        u = torch.empty((self.plan.d, *self.plan.shape), dtype=torch.float64, device=self.device)
+        lbm_macroscopic(self.plan, f, rho, u)
+        return rho, u
+
+    def darcy(self, f, rho_in, tau, rho_out, xs=None):
+        k = torch.zeros(1, dtype=torch.float64, device=self.device)
+        flux = torch.zeros(1, dtype=torch.float64, device=self.device)
+        lbm_darcy(self.plan, f, rho_in, tau, rho_out, self.plan.nx // 2 if xs is None else xs, k, flux)
+        return k, flux
+
+    def status(self) -> int:
+        return lbm_get_status(self.plan)

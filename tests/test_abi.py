@@ -1,0 +1,74 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every
+entry point include/lbm.h declares; host-only calls validate arguments.
+No kernel is launched here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2310_00810_gb300 import build as B
+from paper_2310_00810_gb300 import lbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return lbm.load()
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"^\s*(?:LBM_API\s+)?(?:lbm_status|const char\s*\*)\s+(lbm_\w+)\s*\(", text, re.M))
+    return names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert "lbm_forward" in declared and "lbm_adjoint" in declared
+    assert declared == set(lbm.ENTRY_POINTS), "binding and header disagree"
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_nothing_else_is_exported(lib):
+    out = os.popen(f"nm -D --defined-only {B.LIB}").read()
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert {n for n in exported if n.startswith("lbm_")} == set(lbm.ENTRY_POINTS)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(q=7), dict(precision=2), dict(nx=1), dict(ny=0), dict(nz=2), dict(n_steps=0), dict(ckpt_stride=-1),
+    dict(loss_kind=5), dict(inlet_kind=3),
+])
+def test_plan_create_rejects_bad_descriptors(lib, bad):
+    args = dict(q=9, nx=64, ny=32, nz=1, precision=4, n_steps=10, ckpt_stride=0, loss_kind=0, loss_norm=0,
+                inlet_kind=0)
+    args.update(bad)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.Plan(**args)
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_workspace_size_counts_checkpoints(lib):
+    st = 9 * 64 * 32 * 4
+    p1 = lbm.Plan(9, 64, 32, 1, 4, n_steps=100, ckpt_stride=1)
+    p10 = lbm.Plan(9, 64, 32, 1, 4, n_steps=100, ckpt_stride=10)
+    p0 = lbm.Plan(9, 64, 32, 1, 4, n_steps=100)  # sqrt(T) = 10
+    s1, s10, s0 = (lbm.lbm_workspace_size(p) for p in (p1, p10, p0))
+    assert s10 == s0
+    # stride 1 keeps T - 1 checkpoints + 1 segment state; stride 10 keeps 9 + 10
+    assert s1 - s10 == (99 + 1 - 9 - 10) * st
+    assert s1 > 100 * st
+
+
+def test_calls_without_geometry_are_rejected(lib):
+    p = lbm.Plan(9, 64, 32, 1, 4, n_steps=4)
+    st = lib.lbm_forward(p.handle, None, None, 1.0, None, None, None)
+    assert st == lbm.LBM_ERR_INVALID_ARG
+    assert lbm.lbm_error_string(lbm.LBM_ERR_NONFINITE) == "non-finite loss or gradient"
