@@ -1,0 +1,418 @@
+"""Benchmark of the AD-LBM hot path: forward + adjoint gradient evaluations.
+
+One step = one gradient evaluation of the 512x256 D2Q9 FP32 disk packing
+(porosity 0.6, 20000 time steps, 256-entry inlet density profile): the
+forward sweep with sqrt(T) checkpoints, the loss and its seed, the
+checkpointed reverse sweep (segment recompute + adjoint steps) and one Adam
+update of the profile, all on the device.  The metric is fwd+adjoint MLUPS:
+lattice nodes x time steps per second (each time step's forward and adjoint
+update counted once), summed over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the CPU oracle (plain FP64 C) is timed on the same
+workload and metric, each step a bounded sample of time steps.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "disks512x256"
+METRIC = "fwd+adjoint MLUPS (D2Q9 FP32 512x256 disks, 20000 steps, checkpointed adjoint)"
+UNIT = "MLUPS"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-hbm-roofline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=250)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--time-steps", type=int, default=None,
+                    help="override T (profiling runs only; the reported workload is T = 20000)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        rows = [r for r in csv.reader(open(self.path)) if len(r) >= 9]
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------- the workload
+
+def make_problem(device, rank, time_steps=None):
+    import dataclasses
+
+    import torch
+
+    from paper_2310_00810_gb300 import lbm
+    from paper_2310_00810_gb300 import workloads as W
+
+    wl = W.WORKLOADS[WORKLOAD]
+    if time_steps:
+        wl = dataclasses.replace(wl, steps=time_steps)
+    s = lbm.Solver(wl.q, wl.nx, wl.ny, precision=wl.precision, n_steps=wl.steps, inlet_kind=lbm.LBM_INLET_PROFILE,
+                   geometry=dict(kind=lbm.LBM_GEOM_DISKS, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max,
+                                 target_porosity=wl.porosity), device=device)
+    delta_true = W.inlet_profile(wl.ny, seed=2000 + rank)
+    dv = lambda a: torch.as_tensor(np.asarray(a, np.float64), device=device)
+    tau = dv([wl.tau])
+    f = s.forward(dv(wl.rho_out + delta_true), tau, wl.rho_out)
+    _, u_target = s.macroscopic(f)
+    prob = dict(solver=s, wl=wl, tau=tau, u_target=u_target.contiguous(), delta_true=delta_true,
+                theta=torch.zeros(wl.ny, dtype=torch.float64, device=device),
+                m=torch.zeros(wl.ny, dtype=torch.float64, device=device),
+                v=torch.zeros(wl.ny, dtype=torch.float64, device=device),
+                rho_in=torch.full((wl.ny,), wl.rho_out, dtype=torch.float64, device=device),
+                f=s.new_state(), lam=s.new_state(),
+                loss=torch.zeros(1, dtype=torch.float64, device=device),
+                g_in=torch.zeros(wl.ny, dtype=torch.float64, device=device),
+                g_tau=torch.zeros(1, dtype=torch.float64, device=device), t=0)
+    return prob
+
+
+def issue_step(P, ev=None):
+    """Enqueue one gradient evaluation + Adam update on the solver's stream."""
+    from paper_2310_00810_gb300 import lbm
+
+    s, wl = P["solver"], P["wl"]
+    p = s.plan
+    if ev is not None:
+        ev[0].record(s.stream)
+    lbm.lbm_forward(p, P["rho_in"], P["tau"], wl.rho_out, P["f"], s.ws, s.stream)
+    if ev is not None:
+        ev[1].record(s.stream)
+    lbm.lbm_loss_grad(p, P["f"], P["u_target"], None, P["loss"], P["lam"], s.ws, s.stream)
+    lbm.lbm_adjoint(p, P["rho_in"], P["tau"], wl.rho_out, P["lam"], P["g_in"], P["g_tau"], s.ws, s.stream)
+    P["t"] += 1
+    lbm.lbm_adam_step(P["theta"], P["m"], P["v"], P["g_in"], P["rho_in"], wl.rho_out, 1e-3, P["t"], 0.02,
+                      stream=s.stream)
+    if ev is not None:
+        ev[2].record(s.stream)
+
+
+def launches_per_step(wl, k):
+    """Kernels of this library launched by one gradient evaluation."""
+    T = wl.steps
+    S = (T + k - 1) // k
+    fwd = T  # T-1 stream-collide + 1 stream-only
+    loss = 4  # count, weight, loss, final
+    recompute = 0
+    for sg in range(S):
+        ln = min(k, T - sg * k)
+        recompute += max(0, ln - 1) - (1 if sg == 0 and ln >= 2 else 0)
+    adj = T + 1  # T adjoint steps + gradient finalise
+    return fwd + loss + recompute + adj + 1  # + Adam
+
+
+def fluid_nodes(P):
+    return int(P["solver"].info[3].item())
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2310_00810_gb300 import build
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    P = make_problem(device, rank, args.time_steps)
+    s, wl = P["solver"], P["wl"]
+    N = wl.nodes
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(device)
+
+    for _ in range(max(3, args.warmup)):
+        issue_step(P)
+    barrier()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        with torch.cuda.stream(s.stream):
+            flush.fill_(float(i))  # evict the previous step's lines from the 129 MB L2
+        issue_step(P, evs[i])
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    step_ms = [evs[i][0].elapsed_time(evs[i][2]) for i in range(args.steps)]
+    fwd_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    ms_per_step = total_ms / args.steps
+    value = world * N * wl.steps * args.steps / (total_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel: the fused stream-collide step, timed live
+    # through the forward phase of every timed step (T launches per phase)
+    nf = fluid_nodes(P)
+    bytes_per_launch = 2 * wl.q * 4 * nf + 4 * N  # populations of fluid nodes + link words
+    fwd_launch_s = statistics.mean(fwd_ms) * 1e-3 / wl.steps
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = bytes_per_launch / fwd_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_step<9,float,stream-collide>", "achieved": round(achieved, 1),
+                "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
+                "peak_source": "measured" if peaks else "fallback",
+                "traffic": None, "bytes_per_launch": bytes_per_launch,
+                "note": "512x256 state (9.4 MB read+write per step) is L2-resident; see roofline_hbm"}
+
+    e2e = None if args.no_e2e else run_e2e(P, args, device, barrier, world)
+    hbm = None if args.no_hbm_roofline else roofline_large(device, hbm_peak)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample_steps)
+
+    rel_err = float(np.linalg.norm((P["rho_in"].cpu().numpy() - wl.rho_out) - P["delta_true"]) /
+                    np.linalg.norm(P["delta_true"]))
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: D2Q9 BGK FP32 512x256, seeded disks r 6-12 porosity "
+                                   f"{nf / N:.4f} (target 0.6), T={wl.steps}, tau 0.8, 256-entry inlet profile "
+                                   f"(4 sine modes, amplitude 1e-3), sqrt(T) checkpoints, Adam lr 0.02",
+                       "nodes": N, "fluid_nodes": nf, "time_steps": wl.steps,
+                       "l2": "512 MB buffer written between timed steps (L2 flush); per-step state is L2-resident",
+                       "parallelism": f"replicas x{world} (independent inversions, no collective)"},
+            "e2e": e2e, "gpu_launches": launches_per_step(wl, s.plan_k if hasattr(s, "plan_k") else
+                                                          max(1, math.ceil(math.sqrt(wl.steps)))) * args.steps,
+            "roofline": roofline, "roofline_hbm": hbm, "cpu_baseline": cpu, "clocks": clocks,
+            "wall_s_timed_region": round(wall, 3),
+            "inversion_progress": {"adam_steps": P["t"], "rel_err_delta": rel_err},
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(P, args, device, barrier, world):
+    """Same metric through the public API with host buffers: every step copies
+    the inputs (inlet profile, tau, target velocity) from pinned host memory
+    and reads the loss and gradient back."""
+    import torch
+
+    from paper_2310_00810_gb300 import lbm
+
+    s, wl = P["solver"], P["wl"]
+    h_rho = P["rho_in"].cpu().pin_memory()
+    h_tau = P["tau"].cpu().pin_memory()
+    h_ut = P["u_target"].cpu().pin_memory()
+    h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    h_g = torch.empty(wl.ny, dtype=torch.float64).pin_memory()
+    d_rho, d_tau, d_ut = torch.empty_like(P["rho_in"]), torch.empty_like(P["tau"]), torch.empty_like(P["u_target"])
+    K = max(1, min(args.steps, 3))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(K):
+        with torch.cuda.stream(s.stream):
+            d_rho.copy_(h_rho, non_blocking=True)
+            d_tau.copy_(h_tau, non_blocking=True)
+            d_ut.copy_(h_ut, non_blocking=True)
+        lbm.lbm_forward(s.plan, d_rho, d_tau, wl.rho_out, P["f"], s.ws, s.stream)
+        lbm.lbm_loss_grad(s.plan, P["f"], d_ut, None, P["loss"], P["lam"], s.ws, s.stream)
+        lbm.lbm_adjoint(s.plan, d_rho, d_tau, wl.rho_out, P["lam"], P["g_in"], P["g_tau"], s.ws, s.stream)
+        with torch.cuda.stream(s.stream):
+            h_loss.copy_(P["loss"], non_blocking=True)
+            h_g.copy_(P["g_in"], non_blocking=True)
+    e1.record(s.stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    bi = (h_rho.numel() + h_tau.numel() + h_ut.numel()) * 8
+    bo = (h_loss.numel() + h_g.numel()) * 8
+    val = world * wl.nodes * wl.steps * K / (ms * 1e-3) / 1e6
+    return {"value": round(val, 1), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+            "steps": K, "ms_per_step": round(ms / K, 3)}
+
+
+def roofline_large(device, hbm_peak):
+    """HBM roofline of the stream-collide step on a lattice larger than L2:
+    D2Q9 FP32 8192x4096 disk packing (two 1.2 GB population buffers)."""
+    import torch
+
+    from paper_2310_00810_gb300 import lbm
+    from paper_2310_00810_gb300 import workloads as W
+
+    wl = W.WORKLOADS["disks8192x4096"]
+    s = lbm.Solver(wl.q, wl.nx, wl.ny, precision=4, n_steps=2, geometry=dict(
+        kind=lbm.LBM_GEOM_DISKS, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max, target_porosity=wl.porosity),
+        device=device)
+    nf = int(s.info[3].item())
+    N = wl.nodes
+    rho_in = torch.tensor([1.001], dtype=torch.float64, device=device)
+    tau = torch.tensor([wl.tau], dtype=torch.float64, device=device)
+    a = torch.zeros((9, wl.ny, wl.nx), dtype=torch.float32, device=device)
+    b = torch.zeros_like(a)
+    n_launch = 20
+    # n steps = 1 collide-only + (n-1) stream-collide + 1 stream-only launches
+    lbm.lbm_step(s.plan, rho_in, tau, 1.0, a, b, 4, s.ws, s.stream)
+    torch.cuda.synchronize(device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    lbm.lbm_step(s.plan, rho_in, tau, 1.0, a, b, n_launch, s.ws, s.stream)
+    e1.record(s.stream)
+    torch.cuda.synchronize(device)
+    per = e0.elapsed_time(e1) * 1e-3 / (n_launch + 1)
+    byts = 2 * 9 * 4 * nf + 4 * N
+    ach = byts / per / 1e9
+    out = {"bound": "hbm", "kernel": "k_step<9,float> on disks8192x4096", "achieved": round(ach, 1),
+           "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
+           "bytes_per_launch": byts, "fluid_nodes": nf, "nodes": N,
+           "glups_fluid": round(nf / per / 1e9, 2)}
+    del a, b, s
+    torch.cuda.empty_cache()
+    return out
+
+
+def cpu_baseline(sample_steps):
+    """The FP64 C oracle, as it stands, on a bounded sample of the workload:
+    the full gradient (forward + checkpointed reverse sweep) over the first
+    `sample_steps` time steps of the same 512x256 problem."""
+    from oracle import oracle as O
+    from paper_2310_00810_gb300 import workloads as W
+
+    wl = W.WORKLOADS[WORKLOAD]
+    m, _ = O.geometry(9, wl.nx, wl.ny, kind=O.GEOM_DISKS, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max,
+                      porosity=wl.porosity)
+    rin = wl.rho_out + W.inlet_profile(wl.ny, seed=2000)
+    ut = np.zeros((2, wl.ny, wl.nx))
+    t0 = time.perf_counter()
+    O.gradient(9, m, rin, wl.rho_out, wl.tau, sample_steps, ut, ckpt_stride=max(1, int(math.sqrt(sample_steps))))
+    dt = time.perf_counter() - t0
+    return {"value": round(wl.nodes * sample_steps / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{WORKLOAD} gradient over the first {sample_steps} of 20000 time steps "
+                      f"({dt:.1f} s, single-threaded FP64 C)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+
+    O.build()
+    K, Wm = args.steps, max(0, args.warmup)
+    sample = max(4, min(args.cpu_sample_steps, 30))
+    for _ in range(min(Wm, 1)):
+        cpu_baseline(4)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(K):
+        vals.append(cpu_baseline(sample))
+    wall = time.perf_counter() - t0
+    from paper_2310_00810_gb300 import workloads as W
+
+    wl = W.WORKLOADS[WORKLOAD]
+    value = K * wl.nodes * sample / wall / 1e6
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+           "steps": K, "warmup": Wm, "ms_per_step": round(wall / K * 1e3, 1), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{WORKLOAD} (oracle sample: {sample} of 20000 time steps per step)"},
+           "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"gradient over the first {sample} time steps of {WORKLOAD}, per step"},
+           "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

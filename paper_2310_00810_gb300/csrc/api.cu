@@ -15,14 +15,45 @@
 // ping-pong buffer, so checkpointing costs no extra traffic.  The reverse
 // sweep recomputes g^{s k} .. g^{s k + len - 2} into the segment buffer and
 // then runs the adjoint steps of the segment backwards.
+//
+// Launch sequences.  A forward or reverse sweep is T to 3T kernel launches;
+// on a stream other than the legacy default stream each distinct sequence
+// (same operation, pointers and scalars) is captured once into a CUDA graph
+// and replayed with one cudaGraphLaunch.  When the caller's stream is itself
+// being captured, the launches go straight into the caller's graph.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
 using namespace lbm;
+
+namespace {
+
+struct GraphKey {
+    int op = 0;
+    const void* ptr[8] = {};
+    double scalar = 0.0;
+    long long n = 0;
+    bool operator==(const GraphKey& o) const
+    {
+        return op == o.op && scalar == o.scalar && n == o.n && std::memcmp(ptr, o.ptr, sizeof(ptr)) == 0;
+    }
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+};
+
+constexpr size_t kMaxGraphs = 8;
+
+}  // namespace
 
 struct lbm_plan {
     lbm_desc desc;
@@ -33,6 +64,13 @@ struct lbm_plan {
     uint8_t* mask = nullptr;
     uint32_t* link = nullptr;
     void* last_ws = nullptr;
+    bool use_graphs = true;
+    std::vector<GraphEntry> graphs;  // most recently used last
+    ~lbm_plan()
+    {
+        for (auto& g : graphs)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+    }
 };
 
 namespace {
@@ -94,6 +132,42 @@ lbm_status check_common(const lbm_plan* p, const void* ws)
         if (st__ != LBM_OK) return st__;  \
     } while (0)
 
+// Issues `issue(s)` through a cached CUDA graph when that is possible.
+lbm_status run_sequence(lbm_plan* p, const GraphKey& key, cudaStream_t s,
+                        const std::function<lbm_status(cudaStream_t)>& issue)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (!p->use_graphs || s == nullptr || s == cudaStreamLegacy || s == cudaStreamPerThread) return issue(s);
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cs != cudaStreamCaptureStatusNone) return issue(s);
+    for (size_t i = 0; i < p->graphs.size(); ++i)
+        if (p->graphs[i].key == key) {
+            GraphEntry e = p->graphs[i];
+            p->graphs.erase(p->graphs.begin() + (long)i);
+            p->graphs.push_back(e);
+            return cuda_status(cudaGraphLaunch(e.exec, s));
+        }
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return LBM_ERR_CUDA;
+    lbm_status st = issue(s);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (st != LBM_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return st != LBM_OK ? st : LBM_ERR_CUDA;
+    }
+    GraphEntry ent;
+    ent.key = key;
+    e = cudaGraphInstantiate(&ent.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return LBM_ERR_CUDA;
+    if (p->graphs.size() >= kMaxGraphs) {
+        cudaGraphExecDestroy(p->graphs.front().exec);
+        p->graphs.erase(p->graphs.begin());
+    }
+    p->graphs.push_back(ent);
+    return cuda_status(cudaGraphLaunch(ent.exec, s));
+}
+
 }  // namespace
 
 extern "C" {
@@ -133,6 +207,8 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     p->k = d->ckpt_stride > 0 ? std::min(d->ckpt_stride, T) : std::max(1, (int)std::ceil(std::sqrt((double)T)));
     p->S = (T + p->k - 1) / p->k;
     layout(p);
+    const char* env = std::getenv("LBM_NO_GRAPHS");
+    p->use_graphs = !(env && env[0] == '1');
     *out = p;
     return LBM_OK;
 }
@@ -198,17 +274,28 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     };
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
-    // g^0 = rest
-    unsigned char* cur = slot(0);
-    if (!cur) cur = ping0;
-    if (cudaMemsetAsync(cur, 0, p->info.state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
-    for (int t = 1; t <= T - 1; ++t) {
-        unsigned char* dst = slot(t);
-        if (!dst) dst = (cur == ping0) ? ping1 : ping0;
-        LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, s));
-        cur = dst;
-    }
-    return step_launch(p->info, kStreamOnly, cur, d_f, bc, d_tau, s);
+    auto issue = [&](cudaStream_t st_) -> lbm_status {
+        // g^0 = rest
+        unsigned char* cur = slot(0);
+        if (!cur) cur = ping0;
+        if (cudaMemsetAsync(cur, 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
+        for (int t = 1; t <= T - 1; ++t) {
+            unsigned char* dst = slot(t);
+            if (!dst) dst = (cur == ping0) ? ping1 : ping0;
+            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, st_));
+            cur = dst;
+        }
+        return step_launch(p->info, kStreamOnly, cur, d_f, bc, d_tau, st_);
+    };
+    GraphKey key;
+    key.op = 1;
+    key.ptr[0] = d_rho_in;
+    key.ptr[1] = d_tau;
+    key.ptr[2] = d_f;
+    key.ptr[3] = d_ws;
+    key.ptr[4] = p->link;
+    key.scalar = rho_out;
+    return run_sequence(p, key, s, issue);
 }
 
 lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out, const void* d_f_in,
@@ -221,14 +308,28 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
     const Bc bc = make_bc(p, d_rho_in, rho_out);
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
-    LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, d_tau, s));
-    unsigned char* cur = ping0;
-    for (int t = 1; t < n_steps; ++t) {
-        unsigned char* dst = cur == ping0 ? ping1 : ping0;
-        LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, s));
-        cur = dst;
-    }
-    return step_launch(p->info, kStreamOnly, cur, d_f_out, bc, d_tau, s);
+    auto issue = [&](cudaStream_t st_) -> lbm_status {
+        LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, d_tau, st_));
+        unsigned char* cur = ping0;
+        for (int t = 1; t < n_steps; ++t) {
+            unsigned char* dst = cur == ping0 ? ping1 : ping0;
+            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, st_));
+            cur = dst;
+        }
+        return step_launch(p->info, kStreamOnly, cur, d_f_out, bc, d_tau, st_);
+    };
+    if (n_steps < 8) return issue(s);
+    GraphKey key;
+    key.op = 2;
+    key.ptr[0] = d_rho_in;
+    key.ptr[1] = d_tau;
+    key.ptr[2] = d_f_in;
+    key.ptr[3] = d_f_out;
+    key.ptr[4] = d_ws;
+    key.ptr[5] = p->link;
+    key.scalar = rho_out;
+    key.n = n_steps;
+    return run_sequence(p, key, s, issue);
 }
 
 lbm_status lbm_loss_grad(lbm_plan* p, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
@@ -254,36 +355,50 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     const size_t st = align256(p->info.state_bytes);
     double* grad_acc = reinterpret_cast<double*>(ws + p->ws.grad_acc);
     double* partial = reinterpret_cast<double*>(ws + p->ws.partial);
-    if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, s) != cudaSuccess) return LBM_ERR_CUDA;
-    if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_blocks, s) != cudaSuccess)
-        return LBM_ERR_CUDA;
-    const void* lam_cur = d_lambda;
-    int lam_next = 0;
-    for (int sg = S - 1; sg >= 0; --sg) {
-        const int t0 = sg * k, len = std::min(k, T - t0);
-        // segp[j] holds g^{t0 + j - 1}; for sg = 0, j = 0 stands for the rest state f^0
-        auto seg = [&](int j) -> unsigned char* { return ws + p->ws.seg + st * (size_t)j; };
-        const unsigned char* base = sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
-        const unsigned char* prev = base;
-        for (int j = 1; j < len; ++j) {
-            if (sg == 0 && j == 1) {
-                if (cudaMemsetAsync(seg(1), 0, p->info.state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
-            } else {
-                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(j), bc, d_tau, s));
+    auto issue = [&](cudaStream_t st_) -> lbm_status {
+        if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, st_) != cudaSuccess)
+            return LBM_ERR_CUDA;
+        if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_blocks, st_) != cudaSuccess)
+            return LBM_ERR_CUDA;
+        const void* lam_cur = d_lambda;
+        int lam_next = 0;
+        for (int sg = S - 1; sg >= 0; --sg) {
+            const int t0 = sg * k, len = std::min(k, T - t0);
+            // seg(j) holds g^{t0 + j - 1}; for sg = 0, j = 0 stands for the rest state f^0
+            auto seg = [&](int j) -> unsigned char* { return ws + p->ws.seg + st * (size_t)j; };
+            const unsigned char* base = sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
+            const unsigned char* prev = base;
+            for (int j = 1; j < len; ++j) {
+                if (sg == 0 && j == 1) {
+                    if (cudaMemsetAsync(seg(1), 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
+                } else {
+                    LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(j), bc, d_tau, st_));
+                }
+                prev = seg(j);
             }
-            prev = seg(j);
+            for (int j = len - 1; j >= 0; --j) {
+                const unsigned char* src = j == 0 ? base : seg(j);
+                const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
+                void* lam_out = ws + p->ws.lam[lam_next];
+                LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, d_tau, grad_acc, partial, st_));
+                lam_cur = lam_out;
+                lam_next ^= 1;
+            }
         }
-        for (int j = len - 1; j >= 0; --j) {
-            const unsigned char* src = j == 0 ? base : seg(j);
-            const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
-            void* lam_out = ws + p->ws.lam[lam_next];
-            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, d_tau, grad_acc, partial, s));
-            lam_cur = lam_out;
-            lam_next ^= 1;
-        }
-    }
-    return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
-                                   reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
+        return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
+                                       reinterpret_cast<uint32_t*>(ws + p->ws.status), st_);
+    };
+    GraphKey key;
+    key.op = 3;
+    key.ptr[0] = d_rho_in;
+    key.ptr[1] = d_tau;
+    key.ptr[2] = d_lambda;
+    key.ptr[3] = d_grad_rho_in;
+    key.ptr[4] = d_grad_tau;
+    key.ptr[5] = d_ws;
+    key.ptr[6] = p->link;
+    key.scalar = rho_out;
+    return run_sequence(p, key, s, issue);
 }
 
 lbm_status lbm_macroscopic(lbm_plan* p, const void* d_f, double* d_rho, double* d_u, void* stream)

@@ -252,6 +252,8 @@ class Solver:
                  mask=None):
         self.device = torch.device(device)
         self.plan = Plan(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+        # the library replays its T-step sweeps as CUDA graphs on a non-default stream
+        self.stream = torch.cuda.Stream(device=self.device)
         p = self.plan
         self.ws = torch.zeros(lbm_workspace_size(p), dtype=torch.uint8, device=self.device)
         if link is not None:
@@ -271,6 +273,15 @@ class Solver:
             else:
                 lbm_init_geometry(p, self.mask, self.link, self.info, self.porosity, **(geometry or {}))
 
+    def run(self, fn):
+        """Runs fn() on the solver's stream, ordered after and before the caller's stream."""
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        with torch.cuda.stream(self.stream):
+            out = fn()
+        cur.wait_stream(self.stream)
+        return out
+
     @property
     def mask_field(self) -> torch.Tensor:
         return self.mask[: self.plan.N].reshape(self.plan.shape)
@@ -280,36 +291,37 @@ class Solver:
 
     def forward(self, rho_in, tau, rho_out, f=None):
         f = self.new_state() if f is None else f
-        lbm_forward(self.plan, rho_in, tau, rho_out, f, self.ws)
+        self.run(lambda: lbm_forward(self.plan, rho_in, tau, rho_out, f, self.ws))
         return f
 
     def step(self, rho_in, tau, rho_out, f_in, n_steps, f_out=None):
         f_out = torch.empty_like(f_in) if f_out is None else f_out
-        lbm_step(self.plan, rho_in, tau, rho_out, f_in, f_out, n_steps, self.ws)
+        self.run(lambda: lbm_step(self.plan, rho_in, tau, rho_out, f_in, f_out, n_steps, self.ws))
         return f_out
 
-    def loss_grad(self, f, u_target, roi=None):
-        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
-        lam = self.new_state()
-        lbm_loss_grad(self.plan, f, u_target, roi, loss, lam, self.ws)
+    def loss_grad(self, f, u_target, roi=None, loss=None, lam=None):
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device) if loss is None else loss
+        lam = self.new_state() if lam is None else lam
+        self.run(lambda: lbm_loss_grad(self.plan, f, u_target, roi, loss, lam, self.ws))
         return loss, lam
 
-    def adjoint(self, rho_in, tau, rho_out, lam):
-        g_in = torch.zeros(self.plan.n_in, dtype=torch.float64, device=self.device)
-        g_tau = torch.zeros(1, dtype=torch.float64, device=self.device)
-        lbm_adjoint(self.plan, rho_in, tau, rho_out, lam, g_in, g_tau, self.ws)
+    def adjoint(self, rho_in, tau, rho_out, lam, g_in=None, g_tau=None):
+        g_in = torch.zeros(self.plan.n_in, dtype=torch.float64, device=self.device) if g_in is None else g_in
+        g_tau = torch.zeros(1, dtype=torch.float64, device=self.device) if g_tau is None else g_tau
+        self.run(lambda: lbm_adjoint(self.plan, rho_in, tau, rho_out, lam, g_in, g_tau, self.ws))
         return g_in, g_tau
 
     def macroscopic(self, f):
         rho = torch.empty(self.plan.shape, dtype=torch.float64, device=self.device)
         u = torch.empty((self.plan.d, *self.plan.shape), dtype=torch.float64, device=self.device)
-        lbm_macroscopic(self.plan, f, rho, u)
+        self.run(lambda: lbm_macroscopic(self.plan, f, rho, u))
         return rho, u
 
     def darcy(self, f, rho_in, tau, rho_out, xs=None):
         k = torch.zeros(1, dtype=torch.float64, device=self.device)
         flux = torch.zeros(1, dtype=torch.float64, device=self.device)
-        lbm_darcy(self.plan, f, rho_in, tau, rho_out, self.plan.nx // 2 if xs is None else xs, k, flux)
+        self.run(lambda: lbm_darcy(self.plan, f, rho_in, tau, rho_out, self.plan.nx // 2 if xs is None else xs, k,
+                                   flux))
         return k, flux
 
     def status(self) -> int:
