@@ -164,6 +164,32 @@ LBM_API lbm_status lbm_step(lbm_plan* plan, const double* d_rho_in, const double
 LBM_API lbm_status lbm_loss_grad(lbm_plan* plan, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
                          double* d_loss, void* d_lambda, void* d_ws, void* stream);
 
+/* The same loss and seed as lbm_loss_grad, for callers that cannot
+ * allocate device memory at all: code that runs under an allocator it does
+ * not own (a plugin or extension inside a host application that forbids
+ * cudaMalloc), real-time loops where an allocation could stall, or hosts
+ * that only pass in the buffers they already have.  The paper has no
+ * counterpart; this is an interface convenience only.
+ * It takes no workspace: its reduction scratch is a fixed, file-scope
+ * device array of LBM_NOALLOC_MAX_BLOCKS + 32 doubles (about 512 KB) that
+ * every GPU loading this library holds until the process exits.  The call
+ * itself allocates nothing (no cudaMalloc, no cudaFree, no allocating
+ * library routine).
+ *  - Lattices whose loss grid needs more than LBM_NOALLOC_MAX_BLOCKS thread
+ *    blocks (ceil(nx / 128) * ny * nz > 65536) are rejected with
+ *    LBM_ERR_INVALID_ARG; use lbm_loss_grad for those.
+ *  - The first call on a device looks up the array's device address for
+ *    that device (with it current); make that first call before any stream
+ *    capture.
+ *  - All calls share the one array, which keeps the last call's contents:
+ *    calls whose kernels may overlap on the GPU (different streams without
+ *    ordering between them) race on it and must be serialised by the caller.
+ *  - A non-finite loss shows up as a NaN/Inf in d_loss; unlike
+ *    lbm_loss_grad, it does not latch the plan's status word. */
+#define LBM_NOALLOC_MAX_BLOCKS 65536
+LBM_API lbm_status lbm_loss_grad_noalloc(lbm_plan* plan, const void* d_f, const double* d_u_target,
+                                         const uint8_t* d_roi, double* d_loss, void* d_lambda, void* stream);
+
 /* Reverse sweep from lambda^T to t = 0 through the checkpoints left in d_ws
  * by the last lbm_forward with the same parameters: recompute each segment,
  * then run the adjoint step backwards through it.

@@ -342,6 +342,15 @@ lbm_status lbm_loss_grad(lbm_plan* p, const void* d_f, const double* d_u_target,
                        bytes(d_ws), p->ws, static_cast<cudaStream_t>(stream));
 }
 
+lbm_status lbm_loss_grad_noalloc(lbm_plan* p, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
+                                 double* d_loss, void* d_lambda, void* stream)
+{
+    LBM_TRY(check_common(p, nullptr));
+    if (!d_f || !d_u_target || !d_loss || !d_lambda) return LBM_ERR_INVALID_ARG;
+    return loss_launch_noalloc(p->info, d_f, d_u_target, d_roi, p->desc.loss_kind, p->desc.loss_norm, d_loss,
+                               d_lambda, static_cast<cudaStream_t>(stream));
+}
+
 lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
                        const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream)
 {

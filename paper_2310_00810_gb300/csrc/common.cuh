@@ -91,6 +91,8 @@ lbm_status adjoint_launch(const PlanInfo& p, int t_is_zero, const void* gprev, c
 lbm_status loss_launch(const PlanInfo& p, const void* f, const double* u_target, const uint8_t* roi, int kind,
                        int norm, double* d_loss, void* lambda, unsigned char* ws, const Workspace& w,
                        cudaStream_t s);
+lbm_status loss_launch_noalloc(const PlanInfo& p, const void* f, const double* u_target, const uint8_t* roi, int kind,
+                               int norm, double* d_loss, void* lambda, cudaStream_t s);
 lbm_status finish_gradients_launch(const PlanInfo& p, const double* grad_acc, const double* partial,
                                    const double* tau, double* d_grad_rho_in, double* d_grad_tau,
                                    uint32_t* status, cudaStream_t s);

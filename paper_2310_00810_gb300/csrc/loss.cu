@@ -143,6 +143,64 @@ lbm_status loss_launch(const PlanInfo& p, const void* f, const double* u_target,
     return cuda_status(cudaGetLastError());
 }
 
+// ------------------------------------------- loss without a workspace
+
+// Scratch of lbm_loss_grad_noalloc: a status slot and two scalars, then one
+// FP64 partial per thread block of the loss grid.  Every GPU that loads the
+// library holds this array until the process exits.
+constexpr int kNoallocHead = 32;  // doubles before the partials (status, count, weight, padding)
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocHead + LBM_NOALLOC_MAX_BLOCKS];
+
+namespace {
+constexpr int kMaxDevices = 64;
+double* g_noalloc_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+}  // namespace
+
+lbm_status loss_launch_noalloc(const PlanInfo& p, const void* f, const double* u_target, const uint8_t* roi, int kind,
+                               int norm, double* d_loss, void* lambda, cudaStream_t s)
+{
+    if (p.n_blocks > LBM_NOALLOC_MAX_BLOCKS) return LBM_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_UNSUPPORTED;
+    // One-time set-up per device (with that device current): the host-side
+    // name of the array is not a device address, so ask the runtime for it.
+    double* base = __atomic_load_n(&g_noalloc_addr[dev], __ATOMIC_ACQUIRE);
+    if (!base) {
+        void* ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LBM_ERR_CUDA;
+        base = static_cast<double*>(ptr);
+        __atomic_store_n(&g_noalloc_addr[dev], base, __ATOMIC_RELEASE);
+    }
+    uint32_t* status = reinterpret_cast<uint32_t*>(base);
+    double* scalars = base + 1;  // [0] ROI fluid count, [1] loss weight
+    double* partial = base + kNoallocHead;
+    // the status slot is OR-ed into, so it must start at zero; the scalars and
+    // the partials are fully overwritten before they are read
+    if (cudaMemsetAsync(status, 0, sizeof(double), s) != cudaSuccess) return LBM_ERR_CUDA;
+    k_count_roi<<<p.grid, kStepThreads, 0, s>>>(p.geo, roi, partial);
+    k_loss_weight<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, norm == LBM_NORM_MEAN_FLUID, scalars);
+#define LBM_NOALLOC_LOSS(Q, T)                                                                                     \
+    do {                                                                                                           \
+        const T* fp = static_cast<const T*>(f);                                                                    \
+        T* lp = static_cast<T*>(lambda);                                                                           \
+        if (kind == LBM_LOSS_VEC)                                                                                  \
+            k_loss<Q, T, LBM_LOSS_VEC><<<p.grid, kStepThreads, 0, s>>>(fp, u_target, roi, p.geo, scalars + 1, lp,    \
+                                                                       partial);                                   \
+        else                                                                                                       \
+            k_loss<Q, T, LBM_LOSS_NORM><<<p.grid, kStepThreads, 0, s>>>(fp, u_target, roi, p.geo, scalars + 1, lp,   \
+                                                                        partial);                                  \
+    } while (0)
+    if (p.q == 9 && p.prec == 4) LBM_NOALLOC_LOSS(9, float);
+    else if (p.q == 9 && p.prec == 8) LBM_NOALLOC_LOSS(9, double);
+    else if (p.q == 19 && p.prec == 4) LBM_NOALLOC_LOSS(19, float);
+    else if (p.q == 19 && p.prec == 8) LBM_NOALLOC_LOSS(19, double);
+    else return LBM_ERR_UNSUPPORTED;
+#undef LBM_NOALLOC_LOSS
+    k_loss_final<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, d_loss, status);
+    return cuda_status(cudaGetLastError());
+}
+
 // ----------------------------------------------------- gradient finalise
 
 // dL/dtau = -(sum of dL/domega partials) / tau^2 ; dL/drho_in from the

@@ -28,7 +28,7 @@ LBM_LINK_SOLID = 0x80000000
 
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
-    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
+    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string",
 )
 
@@ -78,6 +78,7 @@ def load():
                 "lbm_forward": [vp, vp, vp, f64, vp, vp, vp],
                 "lbm_step": [vp, vp, vp, f64, vp, vp, i32, vp, vp],
                 "lbm_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
+                "lbm_loss_grad_noalloc": [vp, vp, vp, vp, vp, vp, vp],
                 "lbm_adjoint": [vp, vp, vp, f64, vp, vp, vp, vp, vp],
                 "lbm_macroscopic": [vp, vp, vp, vp, vp],
                 "lbm_darcy": [vp, vp, vp, vp, f64, i32, vp, vp, vp],
@@ -206,6 +207,24 @@ def lbm_loss_grad(plan: Plan, f, u_target, roi, loss, lam, ws, stream=None) -> N
                                 _ptr(u_target, torch.float64, plan.d * plan.N), _ptr(roi, torch.uint8, plan.N),
                                 _ptr(loss, torch.float64, 1), _ptr(lam, plan.dtype, plan.q * plan.N),
                                 _ptr(ws, torch.uint8), _stream(stream)), "lbm_loss_grad")
+
+
+LBM_NOALLOC_MAX_BLOCKS = 65536
+
+
+def lbm_loss_grad_noalloc(plan: Plan, f, u_target, roi, loss, lam, stream=None) -> None:
+    """lbm_loss_grad without a workspace, for callers that cannot allocate
+    device memory: the reduction scratch is the library's own fixed device
+    array (see include/lbm.h), shared by every call."""
+    blocks = -(-plan.nx // 128) * plan.ny * plan.nz
+    if blocks > LBM_NOALLOC_MAX_BLOCKS:
+        raise LBMError(LBM_ERR_INVALID_ARG, f"lbm_loss_grad_noalloc: the loss grid needs {blocks} blocks, more "
+                                            f"than the fixed scratch holds ({LBM_NOALLOC_MAX_BLOCKS})")
+    _check(load().lbm_loss_grad_noalloc(plan.handle, _ptr(f, plan.dtype, plan.q * plan.N),
+                                        _ptr(u_target, torch.float64, plan.d * plan.N),
+                                        _ptr(roi, torch.uint8, plan.N), _ptr(loss, torch.float64, 1),
+                                        _ptr(lam, plan.dtype, plan.q * plan.N), _stream(stream)),
+           "lbm_loss_grad_noalloc")
 
 
 def lbm_adjoint(plan: Plan, rho_in, tau, rho_out: float, lam, grad_rho_in, grad_tau, ws, stream=None) -> None:
