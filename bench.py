@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--time-steps", type=int, default=None,
                     help="override T (profiling runs only; the reported workload is T = 20000)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "kernels"],
+                    help="kernels: time the stream-collide and adjoint kernels alone on --lattice")
+    ap.add_argument("--lattice", default="disks8192x4096", help="workload name for --mode kernels")
+    ap.add_argument("--launches", type=int, default=20)
     return ap.parse_args()
 
 
@@ -356,6 +360,61 @@ def roofline_large(device, hbm_peak):
     return out
 
 
+def kernel_rooflines(device, hbm_peak, name, n_launch):
+    """Stream-collide and adjoint kernels alone on workload `name` (a lattice
+    larger than L2 for the HBM roofline): CUDA events around n_launch
+    back-to-back launches of each.  Algorithmic bytes count fluid nodes:
+    2 Q s per stream-collide update, 3 Q s per adjoint update, plus the
+    4-byte link word of every node."""
+    import torch
+
+    from paper_2310_00810_gb300 import lbm
+    from paper_2310_00810_gb300 import workloads as W
+
+    wl = W.WORKLOADS[name]
+    s = lbm.Solver(wl.q, wl.nx, wl.ny, wl.nz, precision=wl.precision, n_steps=n_launch, ckpt_stride=n_launch,
+                   geometry=dict(kind=wl.geom_kind, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max,
+                                 target_porosity=wl.porosity), device=device)
+    nf, N, q, sz = int(s.info[3].item()), wl.nodes, wl.q, wl.precision
+    rho_in = torch.tensor([1.001], dtype=torch.float64, device=device)
+    tau = torch.tensor([wl.tau], dtype=torch.float64, device=device)
+    a = s.new_state().zero_()
+    b = s.new_state().zero_()
+    out = {}
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    # stream-collide: lbm_step(n) = 1 collide-only + (n-1) stream-collide + 1 stream-only launches
+    lbm.lbm_step(s.plan, rho_in, tau, 1.0, a, b, 4, s.ws, s.stream)
+    e[0].record(s.stream)
+    lbm.lbm_step(s.plan, rho_in, tau, 1.0, a, b, n_launch, s.ws, s.stream)
+    e[1].record(s.stream)
+    # adjoint: a forward sweep, the loss seed, then the reverse sweep (stride = T: one segment,
+    # n_launch - 2 recompute launches and n_launch adjoint launches)
+    u_t = torch.zeros((s.plan.d, *s.plan.shape), dtype=torch.float64, device=device)
+    lbm.lbm_forward(s.plan, rho_in, tau, 1.0, a, s.ws, s.stream)
+    loss = torch.zeros(1, dtype=torch.float64, device=device)
+    lbm.lbm_loss_grad(s.plan, a, u_t, None, loss, b, s.ws, s.stream)
+    g_in = torch.zeros(1, dtype=torch.float64, device=device)
+    g_tau = torch.zeros(1, dtype=torch.float64, device=device)
+    lbm.lbm_adjoint(s.plan, rho_in, tau, 1.0, b, g_in, g_tau, s.ws, s.stream)  # warm (graph capture)
+    e[2].record(s.stream)
+    lbm.lbm_adjoint(s.plan, rho_in, tau, 1.0, b, g_in, g_tau, s.ws, s.stream)
+    e[3].record(s.stream)
+    torch.cuda.synchronize(device)
+    t_sc = e[0].elapsed_time(e[1]) * 1e-3 / (n_launch + 1)
+    t_rev = e[2].elapsed_time(e[3]) * 1e-3
+    t_adj = (t_rev - (n_launch - 2) * t_sc) / n_launch
+    for kern, t, per in (("stream-collide", t_sc, 2 * q * sz), ("adjoint", t_adj, 3 * q * sz)):
+        byts = per * nf + 4 * N
+        ach = byts / t / 1e9
+        out[kern] = {"bound": "hbm", "kernel": f"{kern} on {name}", "achieved": round(ach, 1), "peak": hbm_peak,
+                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None, "bytes_per_launch": byts,
+                     "us_per_launch": round(t * 1e6, 2), "fluid_nodes": nf, "nodes": N,
+                     "glups_fluid": round(nf / t / 1e9, 2)}
+    del a, b, s
+    torch.cuda.empty_cache()
+    return out
+
+
 def cpu_baseline(sample_steps):
     """The FP64 C oracle, as it stands, on a bounded sample of the workload:
     the full gradient (forward + checkpointed reverse sweep) over the first
@@ -406,10 +465,26 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_kernels(args):
+    import torch
+
+    from paper_2310_00810_gb300 import build
+
+    build.build()
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = json.load(open(peaks))["hbm_gbs"] if os.path.exists(peaks) else 6800.0
+    print(json.dumps({"mode": "kernels", "lattice": args.lattice,
+                      "kernels": kernel_rooflines(device, hbm_peak, args.lattice, args.launches)}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "kernels":
+        run_kernels(args)
     else:
         run_native(args)
 

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kStepThreads)
     k_adjoint(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Geo g, Bc bc,
               const double* __restrict__ tau, double* __restrict__ grad_acc, double* __restrict__ partial)
 {
+    pdl_enter();
     using L = Lattice<Q>;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     const long long N = g.N, plane = (long long)g.nx * g.ny;
@@ -122,14 +123,18 @@ static void launch(const PlanInfo& p, int t0, const void* gprev, const void* lam
     const T* li = static_cast<const T*>(lam_in);
     T* lo = static_cast<T*>(lam_out);
     if (t0)
-        k_adjoint<Q, T, true><<<p.grid, kStepThreads, 0, s>>>(gp, li, lo, p.geo, bc, tau, grad_acc, partial);
+        launch_k(p.pdl, k_adjoint<Q, T, true>, dim3(p.grid), dim3(kStepThreads), 0, s, gp, li, lo, p.geo, bc, tau, grad_acc, partial);
     else
-        k_adjoint<Q, T, false><<<p.grid, kStepThreads, 0, s>>>(gp, li, lo, p.geo, bc, tau, grad_acc, partial);
+        launch_k(p.pdl, k_adjoint<Q, T, false>, dim3(p.grid), dim3(kStepThreads), 0, s, gp, li, lo, p.geo, bc, tau, grad_acc, partial);
 }
 
 lbm_status adjoint_launch(const PlanInfo& p, int t_is_zero, const void* gprev, const void* lam_in, void* lam_out,
                           const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
+    if (adjoint_launch_tma(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s))
+        return cuda_status(cudaGetLastError());
+    if (adjoint_launch_vec(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s))
+        return cuda_status(cudaGetLastError());
     if (p.q == 9 && p.prec == 4) launch<9, float>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
     else if (p.q == 9 && p.prec == 8)
         launch<9, double>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);

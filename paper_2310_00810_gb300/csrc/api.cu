@@ -87,7 +87,7 @@ void layout(lbm_plan* p)
     w.grad_acc = o;
     o += align256(sizeof(double) * (size_t)p->info.n_acc);
     w.partial = o;
-    o += align256(sizeof(double) * (size_t)p->info.n_blocks);
+    o += align256(sizeof(double) * (size_t)p->info.n_partial);
     w.partial2 = o;
     o += align256(sizeof(double) * (size_t)p->info.n_blocks);
     for (int i = 0; i < 2; ++i) {
@@ -109,13 +109,34 @@ bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 25
 
 unsigned char* bytes(void* ws) { return static_cast<unsigned char*>(ws); }
 
-Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out)
+Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
 {
     Bc bc;
     bc.rho_in = rho_in;
     bc.profile = p->info.n_in > 1 ? 1 : 0;
     bc.rho_out = rho_out;
+    bc.status = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + p->ws.status);
     return bc;
+}
+
+PersistArgs persist_args(const lbm_plan* p, void* d_ws)
+{
+    unsigned char* ws = static_cast<unsigned char*>(d_ws);
+    PersistArgs a;
+    a.ping[0] = ws + p->ws.ping[0];
+    a.ping[1] = ws + p->ws.ping[1];
+    a.ckpt = ws + p->ws.ckpt;
+    a.seg = ws + p->ws.seg;
+    a.lam[0] = ws + p->ws.lam[0];
+    a.lam[1] = ws + p->ws.lam[1];
+    a.lam_in = nullptr;
+    a.out = nullptr;
+    a.state_stride = align256(p->info.state_bytes);
+    a.T = p->desc.n_steps;
+    a.k = p->k;
+    a.S = p->S;
+    a.bar = reinterpret_cast<PersistBar*>(ws + p->ws.status + kBarOffset);
+    return a;
 }
 
 lbm_status check_common(const lbm_plan* p, const void* ws)
@@ -202,6 +223,9 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     I.n_blocks = (int)(I.grid.x * I.grid.y * I.grid.z);
     I.n_in = d->inlet_kind == LBM_INLET_PROFILE ? d->ny * d->nz : 1;
     I.n_acc = d->ny * d->nz;
+    I.geo.link = nullptr;
+    I.geo.skip_sectors = d->nx % 8 == 0 ? 1 : 0;
+    I.n_partial = std::max(std::max(I.n_blocks, vec_blocks_max(I)), 1024);
     I.state_bytes = (size_t)d->q * (size_t)N * (size_t)d->precision;
     const int T = d->n_steps;
     p->k = d->ckpt_stride > 0 ? std::min(d->ckpt_stride, T) : std::max(1, (int)std::ceil(std::sqrt((double)T)));
@@ -209,6 +233,27 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     layout(p);
     const char* env = std::getenv("LBM_NO_GRAPHS");
     p->use_graphs = !(env && env[0] == '1');
+    // LBM_KERNEL=scalar forces the one-node-per-thread kernels; LBM_VEC=n caps the nodes per thread
+    const char* kern = std::getenv("LBM_KERNEL");
+    const char* vec = std::getenv("LBM_VEC");
+    I.max_vec = (kern && std::strcmp(kern, "scalar") == 0) ? 0 : (vec ? std::atoi(vec) : 4);
+    // LBM_TMA=0 turns the TMA-staged kernels off; LBM_TMA_MIN_TILES sets the size from which they are used
+    const char* tma = std::getenv("LBM_TMA");
+    const char* tmin = std::getenv("LBM_TMA_MIN_TILES");
+    I.use_tma = I.max_vec >= 2 && !(tma && tma[0] == '0');
+    I.tma_min_tiles = tmin ? std::atoi(tmin) : 1;
+    const char* sv = std::getenv("LBM_STEP_VARIANT");
+    I.step_variant = sv ? std::atoi(sv) : 0;
+    const char* tv = std::getenv("LBM_TMA_VARIANT");
+    I.tma_variant = tv ? std::atoi(tv) : 1;
+    // LBM_PERSIST=1 turns on the one-launch sweeps (off by default: on this part a grid barrier costs more than
+    // a graph kernel boundary); LBM_PERSIST_MAX_MB sets the largest state they take
+    const char* pd = std::getenv("LBM_PDL");
+    I.pdl = !(pd && pd[0] == '0');
+    const char* pe = std::getenv("LBM_PERSIST");
+    const char* pm = std::getenv("LBM_PERSIST_MAX_MB");
+    I.use_persist = I.max_vec >= 2 && pe && pe[0] == '1';
+    I.persist_max_bytes = (size_t)(pm ? std::atof(pm) : 24.0) * (1u << 20);
     *out = p;
     return LBM_OK;
 }
@@ -264,7 +309,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
     p->last_ws = d_ws;
-    const Bc bc = make_bc(p, d_rho_in, rho_out);
+    const Bc bc = make_bc(p, d_rho_in, rho_out, d_ws);
     const int T = p->desc.n_steps, k = p->k, S = p->S;
     const size_t st = align256(p->info.state_bytes);
     auto slot = [&](int t) -> unsigned char* {  // checkpoint slot of g^t, or nullptr
@@ -274,6 +319,15 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     };
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
+    if (persist_ok(p->info)) {
+        // one cooperative launch for the whole sweep; g^0 = rest where the sweep expects it
+        PersistArgs a = persist_args(p, d_ws);
+        a.out = d_f;
+        unsigned char* g0 = slot(0) ? slot(0) : ping0;
+        if (cudaMemsetAsync(g0, 0, p->info.state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
+        if (T == 1) return step_launch(p->info, kStreamOnly, g0, d_f, bc, d_tau, s);
+        return forward_persist(p->info, a, bc, d_tau, s);
+    }
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         // g^0 = rest
         unsigned char* cur = slot(0);
@@ -305,7 +359,7 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
     if (!d_rho_in || !d_tau || !d_f_in || !d_f_out || !d_ws || n_steps < 1) return LBM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
-    const Bc bc = make_bc(p, d_rho_in, rho_out);
+    const Bc bc = make_bc(p, d_rho_in, rho_out, d_ws);
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
     auto issue = [&](cudaStream_t st_) -> lbm_status {
@@ -359,15 +413,27 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
     p->last_ws = d_ws;
-    const Bc bc = make_bc(p, d_rho_in, rho_out);
+    const Bc bc = make_bc(p, d_rho_in, rho_out, d_ws);
     const int T = p->desc.n_steps, k = p->k, S = p->S;
     const size_t st = align256(p->info.state_bytes);
     double* grad_acc = reinterpret_cast<double*>(ws + p->ws.grad_acc);
     double* partial = reinterpret_cast<double*>(ws + p->ws.partial);
+    if (persist_ok(p->info)) {
+        // one cooperative launch for all segments: recompute, then adjoint steps backwards
+        if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, s) != cudaSuccess)
+            return LBM_ERR_CUDA;
+        if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_partial, s) != cudaSuccess)
+            return LBM_ERR_CUDA;
+        PersistArgs a = persist_args(p, d_ws);
+        a.lam_in = d_lambda;
+        LBM_TRY(reverse_persist(p->info, a, bc, d_tau, grad_acc, partial, s));
+        return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
+                                       reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
+    }
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, st_) != cudaSuccess)
             return LBM_ERR_CUDA;
-        if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_blocks, st_) != cudaSuccess)
+        if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_partial, st_) != cudaSuccess)
             return LBM_ERR_CUDA;
         const void* lam_cur = d_lambda;
         int lam_next = 0;

@@ -12,7 +12,8 @@
 
 namespace lbm {
 
-constexpr int kStepThreads = 128;   // threads per block along x for the step kernels
+constexpr int kStepThreads = 128;   // threads per block along x for the scalar step kernels
+constexpr int kVecRows = 4;         // rows per block (one warp per row) for the vectorised kernels
 constexpr int kReduceThreads = 1024;
 
 enum StepMode : int { kStreamCollide = 0, kCollideOnly = 1, kStreamOnly = 2 };
@@ -34,12 +35,14 @@ struct Geo {
     int nx, ny, nz;
     long long N;
     const uint32_t* link;
+    int skip_sectors;  // 1: kernels may skip stores of 32-byte sectors holding only solid nodes (nx % 8 == 0)
 };
 
 struct Bc {
     const double* rho_in;  // device: 1 or ny*nz entries
     int profile;           // 1: rho_in[z*ny + y], 0: rho_in[0]
     double rho_out;
+    uint32_t* status;      // device status word (bounded waits latch LBM_ERR_TIMEOUT here)
 };
 
 // Everything a launch needs to know about the lattice and its precision.
@@ -50,8 +53,39 @@ struct PlanInfo {
     int n_blocks;     // grid.x * grid.y * grid.z
     int n_in;         // inlet entries (1 or ny*nz)
     int n_acc;        // per-inlet-node accumulators (always ny*nz)
+    int n_partial;    // per-block FP64 partial slots (covers every step-kernel grid)
+    int max_vec;      // widest nodes-per-thread of the step/adjoint kernels (0/1: scalar kernels only)
+    int use_tma;      // 1: TMA-staged FP32 step/adjoint kernels where alignment allows
+    int step_variant; // register stream-collide kernel: 0 link-dependent loads, 1 all loads up front
+    int tma_variant;  // D2Q9 TMA stream-collide: 0 per-direction shifted boxes, 1 halo boxes + TMA link words
+    int pdl;          // 1: launch the sweep kernels with programmatic dependent launch
+    int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes
+    size_t persist_max_bytes;
+    int tma_min_tiles;  // smallest tile count for which the TMA kernels are used
     size_t state_bytes;
 };
+
+// Grid barrier words of the persistent sweeps (in the status section).
+struct PersistBar {
+    unsigned count;
+    unsigned gen;
+    int abort;
+    int pad;
+};
+
+// Buffers and schedule of a persistent sweep (see persist.cu).
+struct PersistArgs {
+    unsigned char* ping[2];  // forward ping-pong states
+    unsigned char* ckpt;     // checkpoint slot s (1..S-1) at (s - 1) * state_stride
+    unsigned char* seg;      // segment state j at j * state_stride
+    unsigned char* lam[2];   // adjoint ping-pong states
+    const void* lam_in;      // lambda^T (reverse sweep input)
+    void* out;               // f^T (forward sweep output)
+    size_t state_stride;
+    int T, k, S;
+    PersistBar* bar;
+};
+constexpr size_t kBarOffset = 64;  // byte offset of the PersistBar in the status section
 
 // Slots of the FP64 scalars inside the status section.
 constexpr size_t kScalarCount = 8;    // double: ROI fluid-node count
@@ -82,10 +116,48 @@ __device__ __forceinline__ double block_sum(double v, int tid, int nthreads)
     return v;
 }
 
+// ------------------------------------------- programmatic dependent launch
+
+// The sweep kernels are launched with programmatic stream serialization: the
+// next kernel of the stream may be scheduled while this one is still running,
+// and each kernel first waits (griddepcontrol.wait) until its predecessor has
+// completed and its writes are visible.  Launched without the attribute,
+// both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <class K, class... Args>
+inline void launch_k(bool pdl, K kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // ------------------------------------------------------------ launchers
 
 lbm_status step_launch(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
                        cudaStream_t s);
+bool step_launch_vec(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
+                     cudaStream_t s);
+bool adjoint_launch_vec(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
+                        const double* tau, double* grad_acc, double* partial, cudaStream_t s);
+int vec_blocks_max(const PlanInfo& p);
+bool step_launch_tma(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
+                     cudaStream_t s);
+bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
+                        const double* tau, double* grad_acc, double* partial, cudaStream_t s);
 lbm_status adjoint_launch(const PlanInfo& p, int t_is_zero, const void* gprev, const void* lam_in, void* lam_out,
                           const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s);
 lbm_status loss_launch(const PlanInfo& p, const void* f, const double* u_target, const uint8_t* roi, int kind,
@@ -103,6 +175,11 @@ lbm_status adam_launch(int n, double* theta, double* m, double* v, const double*
                        double scale, int t, double lr, double b1, double b2, double eps, cudaStream_t s);
 lbm_status geometry_launch(const PlanInfo& p, const lbm_geom_desc& g, uint8_t* mask, uint32_t* link,
                            double* porosity, int64_t* info, cudaStream_t s);
+
+bool persist_ok(const PlanInfo& p);
+lbm_status forward_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau, cudaStream_t s);
+lbm_status reverse_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau,
+                           double* grad_acc, double* partial, cudaStream_t s);
 
 inline lbm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA; }
 

@@ -232,7 +232,7 @@ lbm_status finish_gradients_launch(const PlanInfo& p, const double* grad_acc, co
                                    const double* tau, double* d_grad_rho_in, double* d_grad_tau, uint32_t* status,
                                    cudaStream_t s)
 {
-    k_finish_gradients<<<1, kReduceThreads, 0, s>>>(grad_acc, p.n_acc, p.n_in > 1 ? 1 : 0, partial, p.n_blocks, tau,
+    k_finish_gradients<<<1, kReduceThreads, 0, s>>>(grad_acc, p.n_acc, p.n_in > 1 ? 1 : 0, partial, p.n_partial, tau,
                                                     d_grad_rho_in, d_grad_tau, status);
     return cuda_status(cudaGetLastError());
 }

@@ -29,6 +29,7 @@ template <int Q, typename T, int MODE>
 __global__ void __launch_bounds__(kStepThreads) k_step(const T* __restrict__ src, T* __restrict__ dst, Geo g, Bc bc,
                                                         const double* __restrict__ tau)
 {
+    pdl_enter();
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, z = blockIdx.z;
     if (x >= g.nx) return;
     const long long n = ((long long)z * g.ny + y) * g.nx + x;
@@ -54,16 +55,18 @@ static void launch(const PlanInfo& p, int mode, const void* src, void* dst, cons
     T* b = static_cast<T*>(dst);
     dim3 block(kStepThreads);
     if (mode == kStreamCollide)
-        k_step<Q, T, kStreamCollide><<<p.grid, block, 0, s>>>(a, b, p.geo, bc, tau);
+        launch_k(p.pdl, k_step<Q, T, kStreamCollide>, dim3(p.grid), dim3(block), 0, s, a, b, p.geo, bc, tau);
     else if (mode == kCollideOnly)
-        k_step<Q, T, kCollideOnly><<<p.grid, block, 0, s>>>(a, b, p.geo, bc, tau);
+        launch_k(p.pdl, k_step<Q, T, kCollideOnly>, dim3(p.grid), dim3(block), 0, s, a, b, p.geo, bc, tau);
     else
-        k_step<Q, T, kStreamOnly><<<p.grid, block, 0, s>>>(a, b, p.geo, bc, tau);
+        launch_k(p.pdl, k_step<Q, T, kStreamOnly>, dim3(p.grid), dim3(block), 0, s, a, b, p.geo, bc, tau);
 }
 
 lbm_status step_launch(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
                        cudaStream_t s)
 {
+    if (step_launch_tma(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
+    if (step_launch_vec(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (p.q == 9 && p.prec == 4) launch<9, float>(p, mode, src, dst, bc, tau, s);
     else if (p.q == 9 && p.prec == 8) launch<9, double>(p, mode, src, dst, bc, tau, s);
     else if (p.q == 19 && p.prec == 4) launch<19, float>(p, mode, src, dst, bc, tau, s);

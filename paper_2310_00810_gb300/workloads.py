@@ -91,6 +91,9 @@ WORKLOADS = {
                                  "const"),
     # Lattices larger than L2, for the HBM roofline of the step kernels.
     "disks8192x4096": Workload("disks8192x4096", 9, 8192, 4096, 1, 4, 20, 0.8, 1, 7000, 6, 12, 0.6, "profile"),
+    "disks4096x2048": Workload("disks4096x2048", 9, 4096, 2048, 1, 4, 20, 0.8, 1, 7001, 6, 12, 0.6, "profile"),
+    "spheres256x128x128": Workload("spheres256x128x128", 19, 256, 128, 128, 4, 10, 0.8, 2, 8001, 6, 6, 0.45,
+                                   "const"),
     "spheres512x256x256": Workload("spheres512x256x256", 19, 512, 256, 256, 4, 10, 0.8, 2, 8000, 6, 6, 0.45,
                                    "const"),
 }
