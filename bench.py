@@ -241,14 +241,18 @@ def run_native(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = bytes_per_launch / fwd_launch_s / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_step<9,float,stream-collide>", "achieved": round(achieved, 1),
+    roofline = {"bound": "hbm", "kernel": "stream-collide step (k_step_tma_halo<0> on this lattice)",
+                "achieved": round(achieved, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                 "peak_source": "measured" if peaks else "fallback",
                 "traffic": None, "bytes_per_launch": bytes_per_launch,
                 "note": "512x256 state (9.4 MB read+write per step) is L2-resident; see roofline_hbm"}
 
     e2e = None if args.no_e2e else run_e2e(P, args, device, barrier, world)
-    hbm = None if args.no_hbm_roofline else roofline_large(device, hbm_peak)
+    hbm = None if args.no_hbm_roofline else kernel_rooflines(device, hbm_peak, "disks8192x4096", 20)
+    if hbm:
+        for kern, tr in HBM_TRAFFIC.items():
+            hbm[kern]["traffic"] = tr
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -318,6 +322,12 @@ def run_e2e(P, args, device, barrier, world):
     val = world * wl.nodes * wl.steps * K / (ms * 1e-3) / 1e6
     return {"value": round(val, 1), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
             "steps": K, "ms_per_step": round(ms / K, 3)}
+
+
+# DRAM bytes (read + write) per launch of the two kernels on disks8192x4096, from ncu captures of
+# disks4096x2048 (profiles/k_step_tma_halo_disks4096x2048.md, profiles/k_adjoint_tma_halo_disks4096x2048.md)
+# scaled by the 4x larger node count (traffic grows in proportion to the nodes).
+HBM_TRAFFIC = {"stream-collide": 4 * (343.118080e6 + 201.248512e6), "adjoint": 4 * (642.651648e6 + 217.033472e6)}
 
 
 def roofline_large(device, hbm_peak):
