@@ -54,6 +54,8 @@ def parse():
                     help="kernels: time the stream-collide and adjoint kernels alone on --lattice")
     ap.add_argument("--lattice", default="disks8192x4096", help="workload name for --mode kernels")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--no-invert", action="store_true", help="skip the time-to-1e-3 inversion leg")
+    ap.add_argument("--invert-time-limit", type=float, default=180.0)
     return ap.parse_args()
 
 
@@ -254,6 +256,8 @@ def run_native(args):
         for kern, tr in HBM_TRAFFIC.items():
             hbm[kern]["traffic"] = tr
 
+    inversion = None if args.no_invert else time_to_target(P, args.invert_time_limit)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_steps)
@@ -276,11 +280,26 @@ def run_native(args):
             "roofline": roofline, "roofline_hbm": hbm, "cpu_baseline": cpu, "clocks": clocks,
             "wall_s_timed_region": round(wall, 3),
             "inversion_progress": {"adam_steps": P["t"], "rel_err_delta": rel_err},
+            "time_to_1e-3": inversion,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def time_to_target(P, time_limit):
+    """Wall time for the single-instance inversion of the 256-entry inlet
+    profile from delta = 0 to 1e-3 relative error (L-BFGS on the device
+    gradients; each evaluation is one forward + checkpointed adjoint sweep)."""
+    from paper_2310_00810_gb300 import invert as I
+
+    s, wl = P["solver"], P["wl"]
+    inv = I.Inversion(s, P["u_target"], wl.rho_out, tau0=wl.tau)
+    res = inv.run_lbfgs(max_evals=2000, tol=1e-3, truth_delta=P["delta_true"], time_limit=time_limit)
+    return {"seconds": round(res.seconds, 2), "converged": bool(res.converged), "iterations": res.iterations,
+            "gradient_evaluations": inv.evaluations, "rel_err_delta": res.rel_err_inlet, "method": "L-BFGS",
+            "start": "delta = 0 (no initial guess)", "time_limit_s": time_limit}
 
 
 def run_e2e(P, args, device, barrier, world):
