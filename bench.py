@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--lattice", default="disks8192x4096", help="workload name for --mode kernels")
     ap.add_argument("--launches", type=int, default=20)
     ap.add_argument("--no-invert", action="store_true", help="skip the time-to-1e-3 inversion leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
+    ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--invert-time-limit", type=float, default=180.0)
     return ap.parse_args()
 
@@ -257,6 +259,7 @@ def run_native(args):
             hbm[kern]["traffic"] = tr
 
     inversion = None if args.no_invert else time_to_target(P, args.invert_time_limit)
+    batched = None if args.no_batch else batch_leg(device, args.batch_instances, rank)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -281,6 +284,7 @@ def run_native(args):
             "wall_s_timed_region": round(wall, 3),
             "inversion_progress": {"adam_steps": P["t"], "rel_err_delta": rel_err},
             "time_to_1e-3": inversion,
+            "batched": batched,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -300,6 +304,77 @@ def time_to_target(P, time_limit):
     return {"seconds": round(res.seconds, 2), "converged": bool(res.converged), "iterations": res.iterations,
             "gradient_evaluations": inv.evaluations, "rel_err_delta": res.rel_err_inlet, "method": "L-BFGS",
             "start": "delta = 0 (no initial guess)", "time_limit_s": time_limit}
+
+
+def batch_leg(device, count, rank, steps=2):
+    """The batched inversions: `count` independent D2Q9 FP32 lattices with
+    nx = 32 U{4..32}, ny = nx / 2, seeded disks (porosity U[0.5, 0.7]),
+    T = 5000, one gradient evaluation (forward + loss + checkpointed adjoint)
+    of every instance per batch step, all instances in shared kernels."""
+    import torch
+
+    from paper_2310_00810_gb300 import lbm
+    from paper_2310_00810_gb300 import workloads as W
+
+    T = 5000
+    spec = W.batch_sizes(count, seed=4000 + 100 * rank)
+    sizes = [(nx, ny, 1) for nx, ny, _, _ in spec]
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=sd, r_min=6, r_max=12, target_porosity=por)
+             for nx, ny, por, sd in spec]
+    b = lbm.Batch(9, sizes, precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms,
+                  device=device)
+    rho_in = b.new_inlet()
+    for i, (nx, ny, _, sd) in enumerate(spec):
+        b.view_inlet(rho_in, i).copy_(torch.as_tensor(1.0 + W.inlet_profile(ny, seed=2000 + sd), device=device))
+    tau = torch.full((b.n,), 0.8, dtype=torch.float64, device=device)
+    f_true = b.forward(rho_in, tau, 1.0)
+    torch.cuda.synchronize(device)
+    ut = batch_macroscopic(b, f_true, device)  # observed fields; the evaluation starts from delta = 0
+    rho0 = torch.ones_like(rho_in)
+    f = b.new_state()
+    lam = b.new_state()
+    loss = torch.zeros(b.n, dtype=torch.float64, device=device)
+    g_in = b.new_inlet()
+    g_tau = torch.zeros(b.n, dtype=torch.float64, device=device)
+
+    def one():
+        b.forward(rho0, tau, 1.0, f)
+        b.loss_grad(f, ut, None, loss, lam)
+        b.adjoint(rho0, tau, 1.0, lam, g_in, g_tau)
+
+    one()
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    for _ in range(steps):
+        one()
+    e1.record(b.stream)
+    torch.cuda.synchronize(device)
+    sec = e0.elapsed_time(e1) * 1e-3 / steps
+    nodes = sum(nx * ny for nx, ny, _ in sizes)
+    return {"instances": b.n, "nodes": nodes, "time_steps": T, "seconds_per_gradient_eval": round(sec, 4),
+            "aggregate_mlups": round(nodes * T / sec / 1e6, 1),
+            "gradient_evals_per_s_per_instance": round(1.0 / sec, 3),
+            "gradient_evals_per_s_total": round(b.n / sec, 2),
+            "sizes": f"nx in [{min(s[0] for s in sizes)}, {max(s[0] for s in sizes)}], ny = nx / 2"}
+
+
+def batch_macroscopic(b, f, device):
+    """Velocity fields of every instance of a batch (per-instance lbm_macroscopic on a bound plan)."""
+    import torch
+
+    from paper_2310_00810_gb300 import lbm
+
+    ut = b.new_velocity()
+    for i in range(b.n):
+        nx, ny, nz = b.sizes[i]
+        p = lbm.Plan(b.q, nx, ny, nz, b.precision, 1)
+        o = int(b.node_off[i])
+        lbm.lbm_bind_geometry(p, b.link[o:o + nx * ny * nz])
+        u = torch.empty((b.d, ny, nx), dtype=torch.float64, device=device)
+        lbm.lbm_macroscopic(p, b.view_state(f, i).contiguous(), None, u)
+        b.view_velocity(ut, i).copy_(u)
+    return ut
 
 
 def run_e2e(P, args, device, barrier, world):

@@ -218,6 +218,54 @@ LBM_API lbm_status lbm_adam_step(int32_t n, double* d_theta, double* d_m, double
                          double p_offset, double p_scale, int32_t t, double lr, double beta1, double beta2,
                          double eps, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent lattices (instances) of different sizes advanced together:
+ * every time step is one kernel over the row segments of all instances, so
+ * a batch of small lattices keeps the whole GPU busy.  All instances share Q,
+ * precision, T, the checkpoint stride, the loss kind and normalisation and
+ * the inlet kind of the common descriptor (its nx, ny, nz are ignored).
+ * Packed layouts (element offsets from lbm_batch_layout, each 256-byte
+ * aligned): populations of instance i at state_off[i] ([Q][N_i], shifted,
+ * plan precision); node fields (mask, link words) at node_off[i]; velocity
+ * fields at vel_off[i] ([D][N_i], double); inlet densities and their
+ * gradients at inlet_off[i] (1 or ny_i nz_i entries); tau, loss, dL/dtau,
+ * porosity one double per instance (info: four int64 per instance). */
+typedef struct lbm_batch lbm_batch;
+
+/* n >= 1 instances with sizes nx[i], ny[i], nz[i] (nz = 1 for D2Q9); every
+ * nx[i] must be a multiple of 4 (D2Q9 FP32) or 2 (otherwise).
+ * Errors: INVALID_ARG as lbm_plan_create, per instance. */
+LBM_API lbm_status lbm_batch_create(const lbm_desc* common, int32_t n, const int32_t* nx, const int32_t* ny,
+                                    const int32_t* nz, lbm_batch** out);
+LBM_API lbm_status lbm_batch_destroy(lbm_batch* batch);
+
+/* Host arrays of n + 1 element offsets (the last entry is the total) and the
+ * workspace bytes.  Any pointer may be NULL. */
+LBM_API lbm_status lbm_batch_layout(const lbm_batch* batch, int64_t* state_off, int64_t* node_off, int64_t* vel_off,
+                                    int64_t* inlet_off, size_t* ws_bytes);
+
+/* lbm_init_geometry for every instance (g: n descriptors), then the batch's
+ * work-unit tables are written into d_ws (which must then stay with the
+ * batch).  d_mask, d_link, d_porosity, d_info packed as above. */
+LBM_API lbm_status lbm_batch_init_geometry(lbm_batch* batch, const lbm_geom_desc* g, uint8_t* d_mask,
+                                           uint32_t* d_link, double* d_porosity, int64_t* d_info, void* d_ws,
+                                           void* stream);
+
+/* T steps from rest for every instance (lbm_forward, batched); d_tau: n. */
+LBM_API lbm_status lbm_batch_forward(lbm_batch* batch, const double* d_rho_in, const double* d_tau, double rho_out,
+                                     void* d_f, void* d_ws, void* stream);
+
+/* Per-instance loss (d_loss: n) and seed lambda^T (packed like d_f). */
+LBM_API lbm_status lbm_batch_loss_grad(lbm_batch* batch, const void* d_f, const double* d_u_target,
+                                       const uint8_t* d_roi, double* d_loss, void* d_lambda, void* d_ws,
+                                       void* stream);
+
+/* Reverse sweep for every instance (lbm_adjoint, batched): dL/drho_in packed
+ * by inlet_off, dL/dtau one per instance. */
+LBM_API lbm_status lbm_batch_adjoint(lbm_batch* batch, const double* d_rho_in, const double* d_tau, double rho_out,
+                                     const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws,
+                                     void* stream);
+
 /* Reads (synchronously) and clears the plan's device status word. */
 LBM_API lbm_status lbm_get_status(lbm_plan* plan, lbm_status* status);
 

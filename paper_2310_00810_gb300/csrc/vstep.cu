@@ -15,97 +15,6 @@
 
 namespace lbm {
 
-// Loads the VEC values of row `rowp` that the lane's nodes x0 .. x0+VEC-1
-// receive from columns x0 - SX .. x0 + VEC - 1 - SX (SX in {-1, 0, 1}).
-// `live` is false for lanes past the end of the row (they still shuffle).
-// Which of a lane's loads some fluid node needs.  `fl` has bit j set when
-// the lane's node j is fluid; nodes of other lanes are seen through shuffles.
-// A lane whose nodes are all solid, and whose edge element no neighbouring
-// fluid node takes, skips its loads and its stores (solid nodes carry no
-// populations), which removes most of the traffic of grain interiors.
-template <int VEC>
-struct Need {
-    bool sx0, sxp, sxm;   // need the own vector for shift 0, +1 (from x - 1), -1 (from x + 1)
-    bool edge_p, edge_m;  // lane 0 / lane 31 need the element beyond the warp's segment
-};
-
-template <int VEC>
-__device__ __forceinline__ Need<VEC> lane_needs(unsigned fl, int lane)
-{
-    const unsigned first = fl & 1u, last = (fl >> (VEC - 1)) & 1u;
-    const unsigned next_first = __shfl_down_sync(0xffffffffu, first, 1);
-    const unsigned prev_last = __shfl_up_sync(0xffffffffu, last, 1);
-    Need<VEC> n;
-    n.sx0 = fl != 0u;
-    n.sxp = (fl & ~1u) != 0u || (lane < 31 && next_first);
-    n.sxm = (fl & ~(1u << (VEC - 1))) != 0u || (lane > 0 && prev_last);
-    n.edge_p = lane == 0 && first;
-    n.edge_m = lane == 31 && last;
-    return n;
-}
-
-template <typename T, int VEC, int SX>
-__device__ __forceinline__ void load_shifted(T (&o)[VEC], const T* __restrict__ rowp, int x0, int x0w, int nx,
-                                             int lane, const Need<VEC>& need)
-{
-    T V[VEC];
-    const bool ld = SX == 0 ? need.sx0 : (SX == 1 ? need.sxp : need.sxm);
-    if (ld) {
-        Vec<T, VEC>::load(rowp + x0, V);
-    } else {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) V[j] = T(0);
-    }
-    if (SX == 0) {
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) o[j] = V[j];
-    } else if (SX == 1) {  // from x - 1
-        T prev = __shfl_up_sync(0xffffffffu, V[VEC - 1], 1);
-        if (lane == 0) prev = (x0w > 0 && need.edge_p) ? rowp[x0w - 1] : T(0);
-        o[0] = prev;
-#pragma unroll
-        for (int j = 1; j < VEC; ++j) o[j] = V[j - 1];
-    } else {  // from x + 1
-        T next = __shfl_down_sync(0xffffffffu, V[0], 1);
-        if (lane == 31) next = (x0w + 32 * VEC < nx && need.edge_m) ? rowp[x0w + 32 * VEC] : T(0);
-#pragma unroll
-        for (int j = 0; j < VEC - 1; ++j) o[j] = V[j + 1];
-        o[VEC - 1] = next;
-    }
-}
-
-// load_shifted with the shift chosen at run time (folded after unrolling).
-template <typename T, int VEC>
-__device__ __forceinline__ void load_shift(T (&o)[VEC], int sx, const T* __restrict__ rowp, int x0, int x0w, int nx,
-                                           int lane, const Need<VEC>& need)
-{
-    if (sx == 0) load_shifted<T, VEC, 0>(o, rowp, x0, x0w, nx, lane, need);
-    else if (sx == 1) load_shifted<T, VEC, 1>(o, rowp, x0, x0w, nx, lane, need);
-    else load_shifted<T, VEC, -1>(o, rowp, x0, x0w, nx, lane, need);
-}
-
-// What each of the lane's VEC nodes receives (the pull of step.cu, Eq. 3 and 6).
-template <int Q, typename T, int VEC>
-__device__ __forceinline__ void pull_vec(T (&v)[Q][VEC], const T* __restrict__ src, long long n0, int x0, int x0w,
-                                         int y, int z, const uint32_t (&lw)[VEC], const Geo& g, const Bc& bc,
-                                         int lane, bool live, const Need<VEC>& need)
-{
-    using L = Lattice<Q>;
-    const long long N = g.N;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const int sy = y - L::c(i, 1), sz = z - L::c(i, 2);
-        if (sy >= 0 && sy < g.ny && sz >= 0 && sz < g.nz) {
-            const T* rowp = src + (long long)i * N + ((long long)sz * g.ny + sy) * g.nx;
-            load_shift<T, VEC>(v[i], L::c(i, 0), rowp, x0, x0w, g.nx, lane, need);
-        } else {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) v[i][j] = T(0);
-        }
-    }
-    if (live) pull_fixup<Q, T, VEC>(v, src, n0, x0, y, z, lw, g, bc);
-}
-
 // Minimum resident blocks per SM (register budget) for each instantiation,
 // chosen from ptxas -v so that none of the hot variants spills.
 template <int Q, typename T, int VEC>

@@ -29,7 +29,8 @@ LBM_LINK_SOLID = 0x80000000
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
-    "lbm_get_status", "lbm_error_string",
+    "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
+    "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
 )
 
 
@@ -84,6 +85,13 @@ def load():
                 "lbm_darcy": [vp, vp, vp, vp, f64, i32, vp, vp, vp],
                 "lbm_adam_step": [i32, vp, vp, vp, vp, vp, f64, f64, i32, f64, f64, f64, f64, vp],
                 "lbm_get_status": [vp, C.POINTER(C.c_int)],
+                "lbm_batch_create": [C.POINTER(lbm_desc), i32, vp, vp, vp, C.POINTER(vp)],
+                "lbm_batch_destroy": [vp],
+                "lbm_batch_layout": [vp, vp, vp, vp, vp, C.POINTER(C.c_size_t)],
+                "lbm_batch_init_geometry": [vp, vp, vp, vp, vp, vp, vp, vp],
+                "lbm_batch_forward": [vp, vp, vp, f64, vp, vp, vp],
+                "lbm_batch_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
+                "lbm_batch_adjoint": [vp, vp, vp, f64, vp, vp, vp, vp, vp],
                 "lbm_error_string": [C.c_int],
             }
             for name, args in sig.items():
@@ -345,3 +353,133 @@ class Solver:
 
     def status(self) -> int:
         return lbm_get_status(self.plan)
+
+
+# ----------------------------------------------------------------- batches
+
+class Batch:
+    """Many independent lattices of different sizes advanced together
+    (lbm_batch_*).  ``sizes``: list of (nx, ny, nz); ``geometries``: one
+    lbm_init_geometry keyword dict per instance.  Packed device buffers are
+    allocated with torch; ``view_*`` give per-instance views into them."""
+
+    def __init__(self, q, sizes, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
+                 loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST, geometries=None, device="cuda"):
+        import numpy as np
+
+        self.device = torch.device(device)
+        self.q, self.d, self.n = q, 2 if q == 9 else 3, len(sizes)
+        self.sizes = [tuple(int(v) for v in sz) for sz in sizes]
+        self.precision, self.n_steps, self.inlet_kind = precision, n_steps, inlet_kind
+        self.dtype = torch.float32 if precision == 4 else torch.float64
+        desc = lbm_desc(q, 0, 0, 0, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+        nx = (C.c_int32 * self.n)(*[sz[0] for sz in self.sizes])
+        ny = (C.c_int32 * self.n)(*[sz[1] for sz in self.sizes])
+        nz = (C.c_int32 * self.n)(*[sz[2] for sz in self.sizes])
+        h = C.c_void_p()
+        _check(load().lbm_batch_create(C.byref(desc), self.n, nx, ny, nz, C.byref(h)), "lbm_batch_create")
+        self.handle = h
+        offs = [np.zeros(self.n + 1, np.int64) for _ in range(4)]
+        wsb = C.c_size_t()
+        _check(load().lbm_batch_layout(h, *[o.ctypes.data_as(C.c_void_p) for o in offs], C.byref(wsb)),
+               "lbm_batch_layout")
+        self.state_off, self.node_off, self.vel_off, self.inlet_off = offs
+        self.ws = torch.zeros(wsb.value, dtype=torch.uint8, device=self.device)
+        nodes = int(self.node_off[-1])
+        self.mask = torch.zeros(((nodes + 3) // 4) * 4, dtype=torch.uint8, device=self.device)
+        self.link = torch.zeros(nodes, dtype=torch.int32, device=self.device)
+        self.porosity = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+        self.info = torch.zeros(4 * self.n, dtype=torch.int64, device=self.device)
+        geoms = (lbm_geom_desc * self.n)()
+        for i, g in enumerate(geometries or [{}] * self.n):
+            a = dict(kind=LBM_GEOM_CHANNEL, seed=0, r_min=6, r_max=12, target_porosity=1.0, hydro_q8=256,
+                     inlet_buffer=8, fill_isolated=True, max_rejections=1_000_000)
+            a.update(g)
+            geoms[i] = lbm_geom_desc(a["kind"], a["r_min"], a["r_max"], a["hydro_q8"], a["inlet_buffer"],
+                                     1 if a["fill_isolated"] else 0, a["max_rejections"], a["seed"],
+                                     float(a["target_porosity"]))
+        self.stream = torch.cuda.Stream(device=self.device)
+        _check(load().lbm_batch_init_geometry(h, geoms, _ptr(self.mask), _ptr(self.link), _ptr(self.porosity),
+                                              _ptr(self.info), _ptr(self.ws), _stream(None)),
+               "lbm_batch_init_geometry")
+
+    def _run(self, fn):
+        cur = torch.cuda.current_stream(self.device)
+        self.stream.wait_stream(cur)
+        with torch.cuda.stream(self.stream):
+            fn()
+        cur.wait_stream(self.stream)
+
+    # sizes of the packed buffers
+    def new_state(self):
+        return torch.empty(int(self.state_off[-1]), dtype=self.dtype, device=self.device)
+
+    def new_velocity(self):
+        return torch.zeros(int(self.vel_off[-1]), dtype=torch.float64, device=self.device)
+
+    def new_inlet(self):
+        return torch.zeros(int(self.inlet_off[-1]), dtype=torch.float64, device=self.device)
+
+    def shape(self, i):
+        nx, ny, nz = self.sizes[i]
+        return (ny, nx) if self.q == 9 else (nz, ny, nx)
+
+    def nodes(self, i):
+        nx, ny, nz = self.sizes[i]
+        return nx * ny * nz
+
+    def view_state(self, t, i):
+        o = int(self.state_off[i])
+        return t[o:o + self.q * self.nodes(i)].view(self.q, *self.shape(i))
+
+    def view_mask(self, i):
+        o = int(self.node_off[i])
+        return self.mask[o:o + self.nodes(i)].view(*self.shape(i))
+
+    def view_velocity(self, t, i):
+        o = int(self.vel_off[i])
+        return t[o:o + self.d * self.nodes(i)].view(self.d, *self.shape(i))
+
+    def view_inlet(self, t, i):
+        o = int(self.inlet_off[i])
+        n = self.sizes[i][1] * self.sizes[i][2] if self.inlet_kind == LBM_INLET_PROFILE else 1
+        return t[o:o + n]
+
+    def forward(self, rho_in, tau, rho_out, f=None):
+        f = self.new_state() if f is None else f
+        self._run(lambda: _check(load().lbm_batch_forward(self.handle, _ptr(rho_in, torch.float64),
+                                                          _ptr(tau, torch.float64, self.n), float(rho_out),
+                                                          _ptr(f, self.dtype), _ptr(self.ws),
+                                                          _stream(self.stream)), "lbm_batch_forward"))
+        return f
+
+    def loss_grad(self, f, u_target, roi=None, loss=None, lam=None):
+        loss = torch.zeros(self.n, dtype=torch.float64, device=self.device) if loss is None else loss
+        lam = self.new_state() if lam is None else lam
+        self._run(lambda: _check(load().lbm_batch_loss_grad(self.handle, _ptr(f, self.dtype),
+                                                            _ptr(u_target, torch.float64), _ptr(roi, torch.uint8),
+                                                            _ptr(loss, torch.float64, self.n),
+                                                            _ptr(lam, self.dtype), _ptr(self.ws),
+                                                            _stream(self.stream)), "lbm_batch_loss_grad"))
+        return loss, lam
+
+    def adjoint(self, rho_in, tau, rho_out, lam, g_in=None, g_tau=None):
+        g_in = self.new_inlet() if g_in is None else g_in
+        g_tau = torch.zeros(self.n, dtype=torch.float64, device=self.device) if g_tau is None else g_tau
+        self._run(lambda: _check(load().lbm_batch_adjoint(self.handle, _ptr(rho_in, torch.float64),
+                                                          _ptr(tau, torch.float64, self.n), float(rho_out),
+                                                          _ptr(lam, self.dtype), _ptr(g_in, torch.float64),
+                                                          _ptr(g_tau, torch.float64, self.n), _ptr(self.ws),
+                                                          _stream(self.stream)), "lbm_batch_adjoint"))
+        return g_in, g_tau
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

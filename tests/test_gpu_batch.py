@@ -1,0 +1,97 @@
+"""Batched lattices: every instance of a batch matches a single-instance run
+of the same lattice (populations bit for bit with the same kernel family,
+losses and gradients to FP64 summation-order rounding)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2310_00810_gb300 import lbm
+from paper_2310_00810_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_00810_gb300 import build
+
+    build.build()
+    lbm.load()
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+CASES = {
+    "d2q9_f32": (9, 4, [(128, 64, 1), (96, 40, 1), (160, 48, 1), (64, 32, 1), (224, 80, 1)]),
+    "d2q9_f64": (9, 8, [(96, 40, 1), (130, 34, 1), (64, 32, 1)]),
+    "d3q19_f32": (19, 4, [(40, 16, 12), (32, 12, 12), (48, 10, 14)]),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("profile", [False, True])
+def test_batch_matches_single_instances(case, profile, monkeypatch):
+    monkeypatch.setenv("LBM_TMA", "0")  # single-instance runs on the same register kernels
+    q, prec, sizes = CASES[case]
+    T = 40 if q == 9 else 16
+    inlet = lbm.LBM_INLET_PROFILE if profile else lbm.LBM_INLET_CONST
+    geoms = []
+    for i, (nx, ny, nz) in enumerate(sizes):
+        if q == 9:
+            geoms.append(dict(kind=lbm.LBM_GEOM_DISKS, seed=60 + i, r_min=3, r_max=6, target_porosity=0.7,
+                              inlet_buffer=4))
+        else:
+            geoms.append(dict(kind=lbm.LBM_GEOM_SPHERES, seed=60 + i, r_min=2, r_max=2, target_porosity=0.75,
+                              inlet_buffer=4))
+    b = lbm.Batch(q, sizes, precision=prec, n_steps=T, inlet_kind=inlet, geometries=geoms)
+    rho_in = b.new_inlet()
+    ut = b.new_velocity()
+    taus = []
+    for i, (nx, ny, nz) in enumerate(sizes):
+        n_in = ny * nz if profile else 1
+        b.view_inlet(rho_in, i).copy_(dev(1.0 + (W.inlet_profile(n_in, seed=70 + i) if profile else np.array([1e-3 * (1 + i)]))))
+        b.view_velocity(ut, i).copy_(dev(W.perturbation((b.d,) + b.shape(i), seed=80 + i, scale=1e-3)))
+        taus.append(0.75 + 0.05 * i)
+    tau = dev(taus)
+    f = b.forward(rho_in, tau, 1.0)
+    loss, lam = b.loss_grad(f, ut)
+    g_in, g_tau = b.adjoint(rho_in, tau, 1.0, lam)
+    torch.cuda.synchronize()
+    for i, (nx, ny, nz) in enumerate(sizes):
+        s = lbm.Solver(q, nx, ny, nz, precision=prec, n_steps=T, inlet_kind=inlet, geometry=geoms[i])
+        assert torch.equal(s.mask_field, b.view_mask(i))
+        fi = s.forward(b.view_inlet(rho_in, i).contiguous(), tau[i:i + 1].contiguous(), 1.0)
+        fl = ~s.mask_field.bool()
+        assert torch.equal(fi[:, fl], b.view_state(f, i)[:, fl])
+        Li, lami = s.loss_grad(fi, b.view_velocity(ut, i).contiguous())
+        gi, gti = s.adjoint(b.view_inlet(rho_in, i).contiguous(), tau[i:i + 1].contiguous(), 1.0, lami)
+        assert abs(Li.item() - loss[i].item()) <= 1e-12 * abs(Li.item())
+        np.testing.assert_allclose(b.view_inlet(g_in, i).cpu().numpy(), gi.cpu().numpy(), rtol=1e-9, atol=0)
+        assert abs(gti.item() - g_tau[i].item()) <= 1e-9 * abs(gti.item())
+
+
+def test_batch_gradient_matches_oracle():
+    """One batch instance against the FP64 oracle directly."""
+    sizes = [(96, 40, 1), (64, 24, 1)]
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=90 + i, r_min=3, r_max=5, target_porosity=0.72, inlet_buffer=4)
+             for i in range(2)]
+    b = lbm.Batch(9, sizes, precision=8, n_steps=30, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms)
+    rho_in = b.new_inlet()
+    ut = b.new_velocity()
+    for i in range(2):
+        b.view_inlet(rho_in, i).copy_(dev(1.0 + W.inlet_profile(sizes[i][1], seed=91 + i)))
+        b.view_velocity(ut, i).copy_(dev(W.perturbation((2,) + b.shape(i), seed=92 + i, scale=1e-3)))
+    tau = dev([0.8, 0.9])
+    f = b.forward(rho_in, tau, 1.0)
+    loss, lam = b.loss_grad(f, ut)
+    g_in, g_tau = b.adjoint(rho_in, tau, 1.0, lam)
+    for i in range(2):
+        m = b.view_mask(i).cpu().numpy()
+        Lw, gw, gtw = O.gradient(9, m, b.view_inlet(rho_in, i).cpu().numpy(), 1.0, [0.8, 0.9][i], 30,
+                                 b.view_velocity(ut, i).cpu().numpy(), ckpt_stride=6)
+        assert abs(loss[i].item() - Lw) <= 1e-10 * Lw
+        np.testing.assert_allclose(b.view_inlet(g_in, i).cpu().numpy(), gw, rtol=1e-9, atol=0)
+        assert abs(g_tau[i].item() - gtw) <= 1e-9 * abs(gtw)
