@@ -61,6 +61,30 @@ def parse():
     return ap.parse_args()
 
 
+def replica_seeds(rank: int) -> dict:
+    """Seeds of rank `rank`'s independent replica (replicas differ in their
+    inlet profiles and batched geometries; the lattice of the timed workload
+    is the same on every rank)."""
+    return {"profile": 2000 + rank, "batch": 4000 + 100 * rank}
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -130,7 +154,7 @@ def make_problem(device, rank, time_steps=None):
     s = lbm.Solver(wl.q, wl.nx, wl.ny, precision=wl.precision, n_steps=wl.steps, inlet_kind=lbm.LBM_INLET_PROFILE,
                    geometry=dict(kind=lbm.LBM_GEOM_DISKS, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max,
                                  target_porosity=wl.porosity), device=device)
-    delta_true = W.inlet_profile(wl.ny, seed=2000 + rank)
+    delta_true = W.inlet_profile(wl.ny, seed=replica_seeds(rank)["profile"])
     dv = lambda a: torch.as_tensor(np.asarray(a, np.float64), device=device)
     tau = dv([wl.tau])
     f = s.forward(dv(wl.rho_out + delta_true), tau, wl.rho_out)
@@ -202,6 +226,9 @@ def run_native(args):
         dist.barrier()
     P = make_problem(device, rank, args.time_steps)
     s, wl = P["solver"], P["wl"]
+    from paper_2310_00810_gb300 import autotune
+
+    tuned = autotune.tune(s)  # kernel family / tile shape for this lattice (cached per GPU and shape)
     N = wl.nodes
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
@@ -228,13 +255,9 @@ def run_native(args):
     clocks = clk.stop()
     step_ms = [evs[i][0].elapsed_time(evs[i][2]) for i in range(args.steps)]
     fwd_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+    total_ms = max_over_ranks(sum(step_ms), device)
     ms_per_step = total_ms / args.steps
-    value = world * N * wl.steps * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_throughput(N * wl.steps * args.steps, world, total_ms * 1e-3) / 1e6
 
     # roofline of the dominant kernel: the fused stream-collide step, timed live
     # through the forward phase of every timed step (T launches per phase)
@@ -245,7 +268,7 @@ def run_native(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = bytes_per_launch / fwd_launch_s / 1e9
-    roofline = {"bound": "hbm", "kernel": "stream-collide step (k_step_tma_halo<0> on this lattice)",
+    roofline = {"bound": "hbm", "kernel": f"stream-collide step ({tuned['choice']})",
                 "achieved": round(achieved, 1),
                 "peak": hbm_peak, "unit": "GB/s", "frac": round(achieved / hbm_peak, 4),
                 "peak_source": "measured" if peaks else "fallback",
@@ -277,7 +300,8 @@ def run_native(args):
                                    f"(4 sine modes, amplitude 1e-3), sqrt(T) checkpoints, Adam lr 0.02",
                        "nodes": N, "fluid_nodes": nf, "time_steps": wl.steps,
                        "l2": "512 MB buffer written between timed steps (L2 flush); per-step state is L2-resident",
-                       "parallelism": f"replicas x{world} (independent inversions, no collective)"},
+                       "parallelism": f"replicas x{world} (independent inversions, no collective)",
+                       "kernels": tuned["choice"], "autotune_us_per_time_step": tuned.get("us_per_time_step")},
             "e2e": e2e, "gpu_launches": launches_per_step(wl, s.plan_k if hasattr(s, "plan_k") else
                                                           max(1, math.ceil(math.sqrt(wl.steps)))) * args.steps,
             "roofline": roofline, "roofline_hbm": hbm, "cpu_baseline": cpu, "clocks": clocks,
@@ -317,7 +341,7 @@ def batch_leg(device, count, rank, steps=2):
     from paper_2310_00810_gb300 import workloads as W
 
     T = 5000
-    spec = W.batch_sizes(count, seed=4000 + 100 * rank)
+    spec = W.batch_sizes(count, seed=replica_seeds(rank)["batch"])
     sizes = [(nx, ny, 1) for nx, ny, _, _ in spec]
     geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=sd, r_min=6, r_max=12, target_porosity=por)
              for nx, ny, por, sd in spec]

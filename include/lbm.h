@@ -103,6 +103,27 @@ typedef struct lbm_plan lbm_plan;
 LBM_API lbm_status lbm_plan_create(const lbm_desc* desc, lbm_plan** out);
 LBM_API lbm_status lbm_plan_destroy(lbm_plan* plan);
 
+/* Kernel families for the step and adjoint kernels (performance only: all
+ * give the same results to rounding).  AUTO picks TMA-staged kernels where
+ * alignment allows (FP32, nx % 4 == 0), else vectorised register kernels,
+ * else one node per thread. */
+enum { LBM_FAMILY_AUTO = 0, LBM_FAMILY_SCALAR = 1, LBM_FAMILY_VEC = 2, LBM_FAMILY_TMA = 3 };
+
+typedef struct lbm_kernel_choice {
+    int32_t step_family;     /* LBM_FAMILY_* for the stream-collide kernels */
+    int32_t adjoint_family;  /* LBM_FAMILY_* for the adjoint kernels */
+    int32_t vec;             /* nodes per thread of the register kernels: 2 or 4 */
+    int32_t tma_rows;        /* tile height of the D2Q9 TMA kernels: 4 or 8 */
+    int32_t pdl;             /* 1: programmatic dependent launch between sweep kernels */
+    int32_t persist;         /* 1: one cooperative launch per sweep (lattices up to 24 MB of state) */
+} lbm_kernel_choice;
+
+/* Sets / reads the plan's kernel choice (an autotuner's knob).  Cached CUDA
+ * graphs of the plan are dropped on a change.  Errors: INVALID_ARG for an
+ * out-of-range field. */
+LBM_API lbm_status lbm_plan_set_kernels(lbm_plan* plan, const lbm_kernel_choice* choice);
+LBM_API lbm_status lbm_plan_get_kernels(const lbm_plan* plan, lbm_kernel_choice* choice);
+
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
  * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and segment
  * buffer, adjoint ping-pong states and FP64 reduction slots. */

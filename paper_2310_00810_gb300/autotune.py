@@ -1,0 +1,161 @@
+"""Autotuner for the kernel choice of a plan.
+
+For a given lattice (size, Q, precision, geometry) it times, on the device,
+the candidate kernel families of the stream-collide and adjoint steps — TMA
+staging with 8- or 4-row tiles, register kernels with 4 or 2 nodes per
+thread, one node per thread — then programmatic dependent launch on/off and
+the one-launch persistent sweeps, and keeps the fastest.  Only the speed
+differs between candidates; every family computes the same step.  Results are
+cached in JSON keyed by GPU name, Q, precision and lattice size.
+
+Timing uses a short tuning plan bound to the solver's geometry (T_tune time
+steps), with CUDA events around graph-replayed launch sequences.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+import torch
+
+from . import lbm
+
+_lock = threading.Lock()
+DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
+
+
+def _key(p: lbm.Plan) -> str:
+    name = torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+    return f"{name}|q{p.q}|p{p.precision}|{p.nx}x{p.ny}x{p.nz}|{p.inlet_kind}"
+
+
+def _load(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(path, key, value):
+    with _lock:
+        db = _load(path)
+        db[key] = value
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as fh:
+            json.dump(db, fh, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+
+def step_candidates(p: lbm.Plan):
+    """(name, step_family, vec, tma_rows) the plan's shape allows."""
+    out = []
+    if p.precision == 4 and p.nx % 4 == 0:
+        out.append(("tma8", lbm.LBM_FAMILY_TMA, 4, 8))
+        if p.q == 9:
+            out.append(("tma4", lbm.LBM_FAMILY_TMA, 4, 4))
+    if p.nx % 4 == 0 and p.precision == 4:
+        out.append(("vec4", lbm.LBM_FAMILY_VEC, 4, 8))
+    if p.nx % 2 == 0:
+        out.append(("vec2", lbm.LBM_FAMILY_VEC, 2, 8))
+    out.append(("scalar", lbm.LBM_FAMILY_SCALAR, 2, 8))
+    return out
+
+
+def _time(fn, repeats, stream):
+    fn()  # warm: graph capture, first-touch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(repeats):
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    return best
+
+
+def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | None = DEFAULT_CACHE,
+         use_cache: bool = True, apply: bool = True) -> dict:
+    """Choose and (by default) apply the fastest kernel configuration for the
+    solver's plan.  Returns {"choice": {...}, "timings_us": {...}}."""
+    p = solver.plan
+    key = _key(p)
+    if use_cache and cache:
+        hit = _load(cache).get(key)
+        if hit:
+            if apply:
+                lbm.lbm_plan_set_kernels(p, **hit["choice"])
+            return dict(hit, cached=True)
+    dev = solver.device
+    tp = lbm.Solver(p.q, p.nx, p.ny, p.nz, precision=p.precision, n_steps=t_tune, ckpt_stride=8,
+                    inlet_kind=p.inlet_kind, link=solver.link, mask=solver.mask, device=dev)
+    tq = tp.plan
+    rho_in = torch.full((tq.n_in,), 1.001, dtype=torch.float64, device=dev)
+    tau = torch.tensor([0.8], dtype=torch.float64, device=dev)
+    a = tp.new_state().zero_()
+    b = tp.new_state().zero_()
+    st = tp.stream
+    timings = {}
+
+    def time_step(choice):
+        lbm.lbm_plan_set_kernels(tq, **choice)
+        return _time(lambda: lbm.lbm_step(tq, rho_in, tau, 1.0, a, b, t_tune, tp.ws, st), repeats, st) / (t_tune + 1)
+
+    best_step, best_t = None, float("inf")
+    for name, fam, vec, rows in step_candidates(tq):
+        choice = dict(step_family=fam, adjoint_family=lbm.LBM_FAMILY_AUTO, vec=vec, tma_rows=rows, pdl=1, persist=0)
+        t = time_step(choice)
+        timings[f"step:{name}"] = round(t * 1e6, 3)
+        if t < best_t:
+            best_step, best_t = (name, fam, vec, rows), t
+
+    u_t = torch.zeros((tq.d, *tq.shape), dtype=torch.float64, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    lam = tp.new_state()
+    g_in = torch.zeros(tq.n_in, dtype=torch.float64, device=dev)
+    g_tau = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def time_sweeps(choice):
+        lbm.lbm_plan_set_kernels(tq, **choice)
+
+        def run():
+            lbm.lbm_forward(tq, rho_in, tau, 1.0, a, tp.ws, st)
+            lbm.lbm_loss_grad(tq, a, u_t, None, loss, lam, tp.ws, st)
+            lbm.lbm_adjoint(tq, rho_in, tau, 1.0, lam, g_in, g_tau, tp.ws, st)
+
+        return _time(run, repeats, st) / t_tune
+
+    _, sfam, svec, srows = best_step
+    best, best_t = None, float("inf")
+    for name, fam, vec, rows in step_candidates(tq):
+        choice = dict(step_family=sfam, adjoint_family=fam, vec=vec if fam != sfam else svec,
+                      tma_rows=rows if fam == lbm.LBM_FAMILY_TMA else srows, pdl=1, persist=0)
+        if fam == lbm.LBM_FAMILY_TMA and sfam == lbm.LBM_FAMILY_TMA and rows != srows:
+            continue  # one tile height per plan
+        t = time_sweeps(choice)
+        timings[f"sweep:step={best_step[0]},adjoint={name}"] = round(t * 1e6, 3)
+        if t < best_t:
+            best, best_t = choice, t
+    for pdl in (0,):
+        c = dict(best, pdl=pdl)
+        t = time_sweeps(c)
+        timings[f"sweep:best,pdl={pdl}"] = round(t * 1e6, 3)
+        if t < best_t:
+            best, best_t = c, t
+    if tq.N * tq.q * tq.precision <= 24 * 2 ** 20 and p.nx % 4 == 0:
+        c = dict(best, persist=1)
+        t = time_sweeps(c)
+        timings["sweep:best,persist=1"] = round(t * 1e6, 3)
+        if t < best_t:
+            best, best_t = c, t
+    result = {"choice": best, "timings_us": timings, "us_per_time_step": round(best_t * 1e6, 3), "key": key}
+    if cache:
+        _store(cache, key, result)
+    if apply:
+        lbm.lbm_plan_set_kernels(p, **best)
+    tp.plan.close()
+    return dict(result, cached=False)

@@ -128,9 +128,10 @@ static void launch(const PlanInfo& p, int t0, const void* gprev, const void* lam
         launch_k(p.pdl, k_adjoint<Q, T, false>, dim3(p.grid), dim3(kStepThreads), 0, s, gp, li, lo, p.geo, bc, tau, grad_acc, partial);
 }
 
-lbm_status adjoint_launch(const PlanInfo& p, int t_is_zero, const void* gprev, const void* lam_in, void* lam_out,
+lbm_status adjoint_launch(const PlanInfo& plan, int t_is_zero, const void* gprev, const void* lam_in, void* lam_out,
                           const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
+    const PlanInfo p = with_family(plan, plan.adj_family);
     if (adjoint_launch_tma(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s))
         return cuda_status(cudaGetLastError());
     if (adjoint_launch_vec(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s))

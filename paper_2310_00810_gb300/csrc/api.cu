@@ -135,6 +135,7 @@ PersistArgs persist_args(const lbm_plan* p, void* d_ws)
     a.T = p->desc.n_steps;
     a.k = p->k;
     a.S = p->S;
+    a.spin_limit = p->info.spin_limit;
     a.bar = reinterpret_cast<PersistBar*>(ws + p->ws.status + kBarOffset);
     return a;
 }
@@ -254,6 +255,14 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     const char* pm = std::getenv("LBM_PERSIST_MAX_MB");
     I.use_persist = I.max_vec >= 2 && pe && pe[0] == '1';
     I.persist_max_bytes = (size_t)(pm ? std::atof(pm) : 24.0) * (1u << 20);
+    // LBM_SPIN_LIMIT bounds each grid-barrier wait of the persistent sweeps (tests set it tiny to make
+    // the wait give up on purpose and check that LBM_ERR_TIMEOUT comes back)
+    const char* ty = std::getenv("LBM_TMA_ROWS");
+    I.tma_ty = ty && std::atoi(ty) == 4 ? 4 : 8;
+    I.step_family = LBM_FAMILY_AUTO;
+    I.adj_family = LBM_FAMILY_AUTO;
+    const char* sl = std::getenv("LBM_SPIN_LIMIT");
+    I.spin_limit = sl ? (unsigned)std::strtoul(sl, nullptr, 10) : (1u << 24);
     *out = p;
     return LBM_OK;
 }
@@ -261,6 +270,41 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
 lbm_status lbm_plan_destroy(lbm_plan* p)
 {
     delete p;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
+{
+    if (!p || !k) return LBM_ERR_INVALID_ARG;
+    auto fam_ok = [](int f) { return f >= LBM_FAMILY_AUTO && f <= LBM_FAMILY_TMA; };
+    if (!fam_ok(k->step_family) || !fam_ok(k->adjoint_family) || (k->vec != 2 && k->vec != 4) ||
+        (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1))
+        return LBM_ERR_INVALID_ARG;
+    PlanInfo& I = p->info;
+    I.step_family = k->step_family;
+    I.adj_family = k->adjoint_family;
+    I.max_vec = k->vec;
+    I.use_tma = 1;
+    I.tma_min_tiles = 1;
+    I.tma_ty = k->tma_rows;
+    I.pdl = k->pdl;
+    I.use_persist = k->persist;
+    for (auto& g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
+{
+    if (!p || !k) return LBM_ERR_INVALID_ARG;
+    const PlanInfo& I = p->info;
+    k->step_family = I.step_family;
+    k->adjoint_family = I.adj_family;
+    k->vec = I.max_vec >= 4 ? 4 : 2;
+    k->tma_rows = I.tma_ty;
+    k->pdl = I.pdl;
+    k->persist = I.use_persist;
     return LBM_OK;
 }
 

@@ -58,8 +58,12 @@ struct PlanInfo {
     int use_tma;      // 1: TMA-staged FP32 step/adjoint kernels where alignment allows
     int step_variant; // register stream-collide kernel: 0 link-dependent loads, 1 all loads up front
     int tma_variant;  // D2Q9 TMA stream-collide: 0 per-direction shifted boxes, 1 halo boxes + TMA link words
+    int tma_ty;       // D2Q9 halo TMA tile height: 8 or 4 rows
+    int step_family;  // LBM_FAMILY_* of the stream-collide kernels
+    int adj_family;   // LBM_FAMILY_* of the adjoint kernels
     int pdl;          // 1: launch the sweep kernels with programmatic dependent launch
     int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes
+    unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     size_t persist_max_bytes;
     int tma_min_tiles;  // smallest tile count for which the TMA kernels are used
     size_t state_bytes;
@@ -83,6 +87,7 @@ struct PersistArgs {
     void* out;               // f^T (forward sweep output)
     size_t state_stride;
     int T, k, S;
+    unsigned spin_limit;     // grid-barrier spins before a CTA gives up (LBM_ERR_TIMEOUT)
     PersistBar* bar;
 };
 constexpr size_t kBarOffset = 64;  // byte offset of the PersistBar in the status section
@@ -175,6 +180,24 @@ lbm_status adam_launch(int n, double* theta, double* m, double* v, const double*
                        double scale, int t, double lr, double b1, double b2, double eps, cudaStream_t s);
 lbm_status geometry_launch(const PlanInfo& p, const lbm_geom_desc& g, uint8_t* mask, uint32_t* link,
                            double* porosity, int64_t* info, cudaStream_t s);
+
+// The plan as seen by a launcher of the given kernel family.
+inline PlanInfo with_family(const PlanInfo& p, int family)
+{
+    PlanInfo q = p;
+    if (family == LBM_FAMILY_SCALAR) {
+        q.max_vec = 0;
+        q.use_tma = 0;
+    } else if (family == LBM_FAMILY_VEC) {
+        q.use_tma = 0;
+        if (q.max_vec < 2) q.max_vec = 4;
+    } else if (family == LBM_FAMILY_TMA) {
+        q.use_tma = 1;
+        q.tma_min_tiles = 1;
+        if (q.max_vec < 2) q.max_vec = 4;
+    }
+    return q;
+}
 
 bool persist_ok(const PlanInfo& p);
 lbm_status forward_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau, cudaStream_t s);

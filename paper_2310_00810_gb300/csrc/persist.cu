@@ -1,10 +1,10 @@
 // Persistent sweeps for lattices that fit in L2: the whole forward sweep is
 // one cooperative launch, and so is the whole reverse sweep (segment
 // recompute + adjoint steps), with a bounded grid barrier between time
-// steps.  For a 512x256 lattice one step moves 9.4 MB, well under a
-// microsecond of L2 traffic, so a launch per step would spend most of its
-// time in launch latency; here one barrier (about a microsecond) separates
-// steps instead.
+// steps instead of a kernel boundary.  Opt-in (LBM_PERSIST=1): on GB300 a
+// grid-wide barrier across both dies measured about 5.9 us per 512x256 step,
+// more than a kernel boundary inside a replayed CUDA graph with programmatic
+// dependent launch (about 4.4 us), so the per-step launches stay the default.
 //
 // The arithmetic is the one of step.cu / adjoint.cu (Eq. 1-6 of
 // arXiv 2310.00810 and their transpose) through the register helpers of
@@ -13,7 +13,7 @@
 // 32 * VEC nodes at a time so the +-1 x-shifts stay warp shuffles.
 //
 // Grid barrier: sense reversal on a counter and a generation word in the
-// workspace, spinning at most kSpinLimit times; a CTA that gives up latches
+// workspace, spinning at most spin_limit times; a CTA that gives up latches
 // LBM_ERR_TIMEOUT and raises an abort word that makes every other CTA leave
 // at its next barrier.
 #include <algorithm>
@@ -25,9 +25,8 @@ namespace lbm {
 namespace {
 
 constexpr int kPersistThreads = 256;
-constexpr unsigned kSpinLimit = 1u << 24;
 
-__device__ __forceinline__ bool grid_sync(PersistBar* b, unsigned nblocks, uint32_t* status)
+__device__ __forceinline__ bool grid_sync(PersistBar* b, unsigned nblocks, uint32_t* status, unsigned spin_limit)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -44,7 +43,7 @@ __device__ __forceinline__ bool grid_sync(PersistBar* b, unsigned nblocks, uint3
         } else {
             unsigned it = 0;
             while (*vgen == g0) {
-                if (*vabort || ++it > kSpinLimit) {
+                if (*vabort || ++it > spin_limit) {
                     ok = 0;
                     break;
                 }
@@ -250,7 +249,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_forward_persist(PersistA
     const T omega = T(1) / T(*tau);
     for (int t = 1; t <= a.T - 1; ++t) {
         step_all<Q, T, VEC>(state_at<T>(a, t - 1), state_at<T>(a, t), g, bc, omega, false, units, warp, nwarps, lane);
-        if (!grid_sync(a.bar, gridDim.x, bc.status)) return;
+        if (!grid_sync(a.bar, gridDim.x, bc.status, a.spin_limit)) return;
     }
     step_all<Q, T, VEC>(state_at<T>(a, a.T - 1), reinterpret_cast<T*>(a.out), g, bc, omega, true, units, warp, nwarps,
                         lane);
@@ -315,7 +314,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_reverse_persist(PersistA
             else
                 step_all<Q, T, VEC>(prev, seg(j), g, bc, omega, false, units, warp, nwarps, lane);
             prev = seg(j);
-            ok = grid_sync(a.bar, gridDim.x, bc.status);
+            ok = grid_sync(a.bar, gridDim.x, bc.status, a.spin_limit);
         }
         for (int j = len - 1; j >= 0 && ok; --j) {
             const T* src = j == 0 ? base : seg(j);  // nullptr: the rest state (sg = 0, j = 0)
@@ -323,7 +322,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1) k_reverse_persist(PersistA
             dom += adjoint_all<Q, T, VEC>(src, lam_cur, lo, g, bc, omega, grad_acc, units, warp, nwarps, lane);
             lam_cur = lo;
             lam_next ^= 1;
-            ok = grid_sync(a.bar, gridDim.x, bc.status);
+            ok = grid_sync(a.bar, gridDim.x, bc.status, a.spin_limit);
         }
     }
     // CTA sum of the dL/domega contributions (FP64; fixed order)

@@ -62,9 +62,10 @@ static void launch(const PlanInfo& p, int mode, const void* src, void* dst, cons
         launch_k(p.pdl, k_step<Q, T, kStreamOnly>, dim3(p.grid), dim3(block), 0, s, a, b, p.geo, bc, tau);
 }
 
-lbm_status step_launch(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
+lbm_status step_launch(const PlanInfo& plan, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
                        cudaStream_t s)
 {
+    const PlanInfo p = with_family(plan, plan.step_family);
     if (step_launch_tma(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (step_launch_vec(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (p.q == 9 && p.prec == 4) launch<9, float>(p, mode, src, dst, bc, tau, s);

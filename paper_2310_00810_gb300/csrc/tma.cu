@@ -266,8 +266,9 @@ __global__ void __launch_bounds__(Shape<Q, FwdTile<Q>>::NCONS + 32, 1)
 // node's pulled values AND its own values (bounce-back, Eq. 6) are all in
 // shared memory; the link words arrive by TMA as well.  Consumer threads
 // then touch global memory only to store their results.
-struct Halo2D {
-    static constexpr int TX = 128, TY = 8, STAGES = 4;
+template <int TY_, int STAGES_>
+struct Halo2DT {
+    static constexpr int TX = 128, TY = TY_, STAGES = STAGES_;
     static constexpr int BW = TX + 8, BH = TY + 2;
     static constexpr int BOX = ((BW * BH + 31) / 32) * 32;  // floats per direction box, padded to 128 B
     static constexpr int LINKS = TX * TY;                    // link words per tile
@@ -277,18 +278,21 @@ struct Halo2D {
     static constexpr uint32_t TX_BYTES = 9 * BW * BH * 4 + LINKS * 4;  // bytes the copies deliver (no padding)
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
 };
+using Halo2D8 = Halo2DT<8, 4>;
+using Halo2D4 = Halo2DT<4, 6>;
 // every TMA destination (each box, the link box, each stage) starts on 128 bytes
-static_assert((Halo2D::BOX * 4) % 128 == 0 && (Halo2D::LINKS * 4) % 128 == 0 && Halo2D::STAGE_BYTES % 128 == 0,
+static_assert((Halo2D8::BOX * 4) % 128 == 0 && (Halo2D8::LINKS * 4) % 128 == 0 && Halo2D8::STAGE_BYTES % 128 == 0,
               "TMA shared-memory destinations must be 128-byte aligned");
-static_assert(Halo2D::SMEM <= 227 * 1024, "shared memory per CTA");
+static_assert((Halo2D4::BOX * 4) % 128 == 0 && (Halo2D4::LINKS * 4) % 128 == 0 && Halo2D4::STAGE_BYTES % 128 == 0,
+              "TMA shared-memory destinations must be 128-byte aligned");
+static_assert(Halo2D8::SMEM <= 227 * 1024 && Halo2D4::SMEM <= 227 * 1024, "shared memory per CTA");
 
-template <int MODE>
-__global__ void __launch_bounds__(Halo2D::NCONS + 32, 1)
+template <class H, int MODE>
+__global__ void __launch_bounds__(H::NCONS + 32, 1)
     k_step_tma_halo(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_link,
                     float* __restrict__ dst, Geo g, Bc bc, const double* __restrict__ tau)
 {
     pdl_enter();
-    using H = Halo2D;
     using L = Lattice<9>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + H::STAGES * H::STAGE_BYTES);
@@ -376,8 +380,9 @@ __global__ void __launch_bounds__(Halo2D::NCONS + 32, 1)
 // of lambda^{t+1}, each over the tile rows plus one halo row on each side, and
 // the link words, so the pulls in both directions and every own value
 // (bounce-back, Eq. 6) come from shared memory.
-struct HaloAdj2D {
-    static constexpr int TX = 128, TY = 8, STAGES = 2;
+template <int TY_, int STAGES_>
+struct HaloAdj2DT {
+    static constexpr int TX = 128, TY = TY_, STAGES = STAGES_;
     static constexpr int BW = TX + 8, BH = TY + 2;
     static constexpr int BOX = ((BW * BH + 31) / 32) * 32;
     static constexpr int LINKS = TX * TY;
@@ -386,18 +391,20 @@ struct HaloAdj2D {
     static constexpr size_t STAGE_BYTES = (size_t)18 * BOX * 4 + (size_t)LINKS * 4;
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
 };
-static_assert((HaloAdj2D::BOX * 4) % 128 == 0 && HaloAdj2D::STAGE_BYTES % 128 == 0,
+using HaloAdj2D8 = HaloAdj2DT<8, 2>;
+using HaloAdj2D4 = HaloAdj2DT<4, 3>;
+static_assert((HaloAdj2D8::BOX * 4) % 128 == 0 && HaloAdj2D8::STAGE_BYTES % 128 == 0 &&
+                  (HaloAdj2D4::BOX * 4) % 128 == 0 && HaloAdj2D4::STAGE_BYTES % 128 == 0,
               "TMA shared-memory destinations must be 128-byte aligned");
-static_assert(HaloAdj2D::SMEM <= 227 * 1024, "shared memory per CTA");
+static_assert(HaloAdj2D8::SMEM <= 227 * 1024 && HaloAdj2D4::SMEM <= 227 * 1024, "shared memory per CTA");
 
-template <bool T0>
-__global__ void __launch_bounds__(HaloAdj2D::NCONS + 32, 1)
+template <class H, bool T0>
+__global__ void __launch_bounds__(H::NCONS + 32, 1)
     k_adjoint_tma_halo(const __grid_constant__ CUtensorMap map_g, const __grid_constant__ CUtensorMap map_l,
                        const __grid_constant__ CUtensorMap map_link, float* __restrict__ lam_out, Geo g, Bc bc,
                        const double* __restrict__ tau, double* __restrict__ grad_acc, double* __restrict__ partial)
 {
     pdl_enter();
-    using H = HaloAdj2D;
     using L = Lattice<9>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + H::STAGES * H::STAGE_BYTES);
@@ -668,10 +675,10 @@ bool tma_ok(const PlanInfo& p, const void* a, const void* b, const void* c)
            (reinterpret_cast<uintptr_t>(p.geo.link) & 15u) == 0;
 }
 
+template <class H>
 bool step_tma_halo(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
                    cudaStream_t s)
 {
-    using H = Halo2D;
     const long long tiles = (long long)((p.geo.nx + H::TX - 1) / H::TX) * ((p.geo.ny + H::TY - 1) / H::TY);
     if (tiles < (long long)p.tma_min_tiles) return false;
     CUtensorMap map, ml;
@@ -680,13 +687,13 @@ bool step_tma_halo(const PlanInfo& p, int mode, const void* src, void* dst, cons
     const int grid = (int)std::min<long long>(tiles, sm_count());
     float* b = static_cast<float*>(dst);
     if (mode == kStreamCollide) {
-        static bool ok = allow_smem(k_step_tma_halo<kStreamCollide>, H::SMEM);
+        static bool ok = allow_smem(k_step_tma_halo<H, kStreamCollide>, H::SMEM);
         if (!ok) return false;
-        launch_k(p.pdl, k_step_tma_halo<kStreamCollide>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, map, ml, b, p.geo, bc, tau);
+        launch_k(p.pdl, k_step_tma_halo<H, kStreamCollide>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, map, ml, b, p.geo, bc, tau);
     } else {
-        static bool ok = allow_smem(k_step_tma_halo<kStreamOnly>, H::SMEM);
+        static bool ok = allow_smem(k_step_tma_halo<H, kStreamOnly>, H::SMEM);
         if (!ok) return false;
-        launch_k(p.pdl, k_step_tma_halo<kStreamOnly>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, map, ml, b, p.geo, bc, tau);
+        launch_k(p.pdl, k_step_tma_halo<H, kStreamOnly>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, map, ml, b, p.geo, bc, tau);
     }
     return true;
 }
@@ -717,10 +724,10 @@ bool step_tma(const PlanInfo& p, int mode, const void* src, void* dst, const Bc&
     return true;
 }
 
+template <class H>
 bool adjoint_tma_halo(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
                       const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
-    using H = HaloAdj2D;
     const long long tiles = (long long)((p.geo.nx + H::TX - 1) / H::TX) * ((p.geo.ny + H::TY - 1) / H::TY);
     if (tiles < (long long)p.tma_min_tiles) return false;
     CUtensorMap mg, ml, mk;
@@ -731,14 +738,14 @@ bool adjoint_tma_halo(const PlanInfo& p, int t0, const void* gprev, const void* 
     const int grid = (int)std::min<long long>(std::min<long long>(tiles, sm_count()), p.n_partial);
     float* lo = static_cast<float*>(lam_out);
     if (t0) {
-        static bool ok = allow_smem(k_adjoint_tma_halo<true>, H::SMEM);
+        static bool ok = allow_smem(k_adjoint_tma_halo<H, true>, H::SMEM);
         if (!ok) return false;
-        launch_k(p.pdl, k_adjoint_tma_halo<true>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, mg, ml, mk, lo, p.geo, bc, tau, grad_acc,
+        launch_k(p.pdl, k_adjoint_tma_halo<H, true>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, mg, ml, mk, lo, p.geo, bc, tau, grad_acc,
                                                                       partial);
     } else {
-        static bool ok = allow_smem(k_adjoint_tma_halo<false>, H::SMEM);
+        static bool ok = allow_smem(k_adjoint_tma_halo<H, false>, H::SMEM);
         if (!ok) return false;
-        launch_k(p.pdl, k_adjoint_tma_halo<false>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, mg, ml, mk, lo, p.geo, bc, tau, grad_acc,
+        launch_k(p.pdl, k_adjoint_tma_halo<H, false>, dim3(grid), dim3(H::NCONS + 32), H::SMEM, s, mg, ml, mk, lo, p.geo, bc, tau, grad_acc,
                                                                        partial);
     }
     return true;
@@ -781,7 +788,9 @@ bool step_launch_tma(const PlanInfo& p, int mode, const void* src, void* dst, co
                      cudaStream_t s)
 {
     if (mode == kCollideOnly || !tma_ok(p, src, dst, nullptr)) return false;
-    if (p.q == 9 && p.tma_variant == 1) return step_tma_halo(p, mode, src, dst, bc, tau, s);
+    if (p.q == 9 && p.tma_variant == 1)
+        return p.tma_ty == 4 ? step_tma_halo<Halo2D4>(p, mode, src, dst, bc, tau, s)
+                             : step_tma_halo<Halo2D8>(p, mode, src, dst, bc, tau, s);
     return p.q == 9 ? step_tma<9>(p, mode, src, dst, bc, tau, s) : step_tma<19>(p, mode, src, dst, bc, tau, s);
 }
 
@@ -790,7 +799,8 @@ bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void
 {
     if (!tma_ok(p, gprev, lam_in, lam_out)) return false;
     if (p.q == 9 && p.tma_variant == 1)
-        return adjoint_tma_halo(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+        return p.tma_ty == 4 ? adjoint_tma_halo<HaloAdj2D4>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
+                             : adjoint_tma_halo<HaloAdj2D8>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
     return p.q == 9 ? adjoint_tma<9>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
                     : adjoint_tma<19>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
 }

@@ -26,8 +26,10 @@ LBM_INLET_CONST, LBM_INLET_PROFILE = 0, 1
 LBM_GEOM_CHANNEL, LBM_GEOM_DISKS, LBM_GEOM_SPHERES, LBM_GEOM_MASK = 0, 1, 2, 3
 LBM_LINK_SOLID = 0x80000000
 
+LBM_FAMILY_AUTO, LBM_FAMILY_SCALAR, LBM_FAMILY_VEC, LBM_FAMILY_TMA = 0, 1, 2, 3
+
 ENTRY_POINTS = (
-    "lbm_plan_create", "lbm_plan_destroy", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
+    "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
@@ -38,6 +40,11 @@ class lbm_desc(C.Structure):
     _fields_ = [("q", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
                 ("precision", C.c_int32), ("n_steps", C.c_int32), ("ckpt_stride", C.c_int32),
                 ("loss_kind", C.c_int32), ("loss_norm", C.c_int32), ("inlet_kind", C.c_int32)]
+
+
+class lbm_kernel_choice(C.Structure):
+    _fields_ = [("step_family", C.c_int32), ("adjoint_family", C.c_int32), ("vec", C.c_int32),
+                ("tma_rows", C.c_int32), ("pdl", C.c_int32), ("persist", C.c_int32)]
 
 
 class lbm_geom_desc(C.Structure):
@@ -73,6 +80,8 @@ def load():
             sig = {
                 "lbm_plan_create": [C.POINTER(lbm_desc), C.POINTER(vp)],
                 "lbm_plan_destroy": [vp],
+                "lbm_plan_set_kernels": [vp, C.POINTER(lbm_kernel_choice)],
+                "lbm_plan_get_kernels": [vp, C.POINTER(lbm_kernel_choice)],
                 "lbm_workspace_size": [vp, C.POINTER(C.c_size_t)],
                 "lbm_init_geometry": [vp, C.POINTER(lbm_geom_desc), vp, vp, vp, vp, vp],
                 "lbm_bind_geometry": [vp, vp],
@@ -172,6 +181,18 @@ def lbm_plan_create(q, nx, ny, nz=1, precision=4, n_steps=1, ckpt_stride=0, loss
 
 def lbm_plan_destroy(plan: Plan) -> None:
     plan.close()
+
+
+def lbm_plan_set_kernels(plan: Plan, step_family=LBM_FAMILY_AUTO, adjoint_family=LBM_FAMILY_AUTO, vec=4,
+                         tma_rows=8, pdl=1, persist=0) -> None:
+    k = lbm_kernel_choice(step_family, adjoint_family, vec, tma_rows, pdl, persist)
+    _check(load().lbm_plan_set_kernels(plan.handle, C.byref(k)), "lbm_plan_set_kernels")
+
+
+def lbm_plan_get_kernels(plan: Plan) -> dict:
+    k = lbm_kernel_choice()
+    _check(load().lbm_plan_get_kernels(plan.handle, C.byref(k)), "lbm_plan_get_kernels")
+    return {f: getattr(k, f) for f, _ in lbm_kernel_choice._fields_}
 
 
 def lbm_workspace_size(plan: Plan) -> int:
