@@ -111,6 +111,24 @@ static int lattice_make(int q, lattice* L)
     return 0;
 }
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads for the per-node loops of the step and the adjoint step (1 =
+ * serial).  Every sum over nodes is taken serially in node order, so results
+ * do not depend on the thread count. */
+int SYM(set_threads)(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Exported copies of the tables, for the isotropy pins in the tests. */
 int SYM(lattice)(int q, int* c_out /* q*3 */, double* w_out, int* opp_out)
 {
@@ -253,7 +271,8 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
         return -2;
     }
 
-    /* collision */
+    /* collision (nodes are independent: shared among OpenMP threads) */
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (is_solid(&D, n)) continue;
         real_t rho, u[3];
@@ -265,7 +284,8 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
         }
     }
 
-    /* streaming with boundaries */
+    /* streaming with boundaries (each node writes only its own populations) */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -479,7 +499,18 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
         return -2;
     }
 
-    /* 1. transpose of streaming + boundaries */
+    /* 1. transpose of streaming + boundaries.  Pull streaming with its
+     * boundary links is a permutation of the (direction, node) slots, so each
+     * mu slot and each node's ubar receive from one node only and nodes can be
+     * shared among threads.  The inlet terms (several nodes feed the single
+     * head) go to gin[n] first and are added in node order afterwards. */
+    double* gin = (double*)calloc((size_t)N, sizeof(double));
+    if (!gin) {
+        free(mu);
+        free(ubar);
+        return -2;
+    }
+#pragma omp parallel for collapse(2) schedule(static)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -501,7 +532,7 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
                         double cu = dot_cu(&L, i, u), uu = dot_uu(&L, u);
                         if (cls == LINK_ABB_IN) {
                             double d_rw = 2.0 * L.w[i] * (1.0 + cu * cu * INV_2CS4 - uu * INV_2CS2);
-                            g_rho_in[inlet_profile ? (long)z * ny + y : 0] += lam * d_rw;
+                            gin[n] += lam * d_rw;
                         }
                         for (int a = 0; a < L.d; ++a)
                             ubar[(long)a * N + n] +=
@@ -509,14 +540,30 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
                     }
                 }
             }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                long n = ((long)z * ny + y) * nx + x;
+                if (gin[n] != 0.0) g_rho_in[inlet_profile ? (long)z * ny + y : 0] += gin[n];
+            }
+    free(gin);
 
-    /* 2. transpose of collision and of the moments */
-    double gw = 0;
+    /* 2. transpose of collision and of the moments.  Nodes are independent
+     * here; each node's term of dL/domega goes to gwn[n] and the terms are
+     * summed in node order afterwards, so the thread count changes nothing. */
+    double* gwn = (double*)calloc((size_t)N, sizeof(double));
+    if (!gwn) {
+        free(mu);
+        free(ubar);
+        return -2;
+    }
+#pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
         if (is_solid(&D, n)) {
             for (int k = 0; k < q; ++k) lam_out[(long)k * N + n] = 0;
             continue;
         }
+        double gw = 0;
         double rho, u[3];
         moments(&L, f_t, N, n, &rho, u);
         double uu = dot_uu(&L, u);
@@ -537,8 +584,12 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
             for (int a = 0; a < L.d; ++a) s += ub[a] * ((double)L.c[k][a] - u[a]) / rho;
             lam_out[(long)k * N + n] = s;
         }
+        gwn[n] = gw;
     }
+    double gw = 0;
+    for (long n = 0; n < N; ++n) gw += gwn[n];
     *g_omega += gw;
+    free(gwn);
     free(mu);
     free(ubar);
     return 0;

@@ -24,7 +24,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _LIB_CS = os.path.join(_BUILD, "liboracle_cs.so")
 _SRC = [os.path.join(_HERE, "lbm_oracle.c"), os.path.join(_HERE, "geometry.c")]
-_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall"]
+_CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-Wall", "-fopenmp"]
 
 _lock = threading.Lock()
 _libs: dict = {}
@@ -74,6 +74,11 @@ def _dims(q: int, shape) -> tuple[int, int, int]:
         return nx, ny, 1
     nz, ny, nx = shape[-3:]
     return nx, ny, nz
+
+
+def set_threads(n: int) -> int:
+    """OpenMP threads for the per-node loops (results do not depend on it)."""
+    return int(_lib().orc_set_threads(int(n)))
 
 
 def lattice(q: int):

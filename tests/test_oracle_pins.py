@@ -533,3 +533,29 @@ def test_disk_packing_config_properties():
     m3, _ = O.geometry(9, 512, 256, kind=O.GEOM_DISKS, seed=1001, r_min=6, r_max=12, porosity=0.6)
     assert not np.array_equal(m, m3)
     assert info[0] > 100
+
+
+def test_thread_count_changes_nothing():
+    """The OpenMP forward gives the same bits with 1 and 4 threads."""
+    m, _ = O.geometry(9, 96, 48, kind=O.GEOM_DISKS, seed=8, r_min=3, r_max=6, porosity=0.7)
+    O.set_threads(1)
+    a = O.forward(9, m, 1.001, 1.0, 0.8, 40)
+    O.set_threads(4)
+    b = O.forward(9, m, 1.001, 1.0, 0.8, 40)
+    O.set_threads(1)
+    assert np.array_equal(a, b)
+
+
+def test_thread_count_changes_nothing_in_gradient():
+    """The OpenMP adjoint gives the same bits with 1 and 4 threads (constant head and profile)."""
+    m, _ = O.geometry(9, 64, 32, kind=O.GEOM_DISKS, seed=5, r_min=3, r_max=5, porosity=0.7)
+    rng = np.random.default_rng(3)
+    ut = rng.normal(0, 1e-4, (2, 32, 64))
+    for rin in (1.001, 1.0 + 1e-3 * rng.random(32)):
+        out = []
+        for th in (1, 4):
+            O.set_threads(th)
+            out.append(O.gradient(9, m, rin, 1.0, 0.8, 30, ut, ckpt_stride=6))
+        O.set_threads(1)
+        for a, b in zip(out[0], out[1]):
+            assert np.array_equal(np.asarray(a), np.asarray(b))
