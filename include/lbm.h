@@ -155,6 +155,34 @@ LBM_API lbm_status lbm_init_geometry(lbm_plan* plan, const lbm_geom_desc* g, uin
  * step count can share one geometry.  The pointer must stay valid. */
 LBM_API lbm_status lbm_bind_geometry(lbm_plan* plan, const uint32_t* d_link);
 
+/* Fluid-only ("compact") internal state layout.  The population traffic of
+ * the streaming step (section 2.2: streaming and boundaries are most of the
+ * time) is proportional to the nodes stored; a dense layout stores and moves
+ * solid nodes too, while the compact layout keeps only the n_fluid fluid
+ * nodes, in node order, with a neighbour table: for fluid node k and
+ * direction i >= 1 the compact index of x - c_i, or a code for a
+ * bounce-back (section 2.2) or Eq. 6 link.  The layout is internal: every
+ * call still takes and returns dense Q N arrays (f^T, lambda^T, the lbm_step
+ * states); only the plan's workspace and the tables change.
+ *
+ * lbm_compact_size: bytes of the table buffer for n_fluid fluid nodes
+ *   (4 n_fluid dense indices, 4 (Q - 1) n_fluid neighbour codes, 4 N
+ *   dense-to-compact map, scan scratch).
+ * lbm_compact_bind: builds the tables from the bound link array into
+ *   d_tables (device, caller-owned, 256-byte aligned, lbm_compact_size
+ *   bytes, valid while the plan uses it) and switches the plan to the compact
+ *   layout; lbm_workspace_size then reports the (smaller) compact workspace,
+ *   which the caller must provide from then on.  n_fluid must equal the
+ *   number of fluid nodes of the link array (d_info[3] of lbm_init_geometry);
+ *   the call synchronises the stream to check it.  n_fluid = 0 switches back
+ *   to the dense layout.  The kernel-family choice (lbm_plan_set_kernels)
+ *   applies to the dense layout only; the one-launch persistent sweeps are
+ *   not used with the compact layout.
+ * Errors: INVALID_ARG (no geometry bound, n_fluid out of range or not the
+ *   fluid count of the link array, misaligned d_tables), CUDA. */
+LBM_API lbm_status lbm_compact_size(const lbm_plan* plan, int64_t n_fluid, size_t* bytes);
+LBM_API lbm_status lbm_compact_bind(lbm_plan* plan, int64_t n_fluid, void* d_tables, void* stream);
+
 /* T steps from rest (f = w_i, rho = 1: init_field of section 2.2), keeping
  * the checkpoints the adjoint needs in d_ws.
  *  d_rho_in  double[1 or ny nz]  inlet density (Eq. 6 rho_w at x = -1/2)

@@ -1,12 +1,13 @@
-"""Autotuner for the kernel choice of a plan.
+"""Autotuner for the state layout and kernel choice of a plan.
 
 For a given lattice (size, Q, precision, geometry) it times, on the device,
-the candidate kernel families of the stream-collide and adjoint steps — TMA
-staging with 8- or 4-row tiles, register kernels with 4 or 2 nodes per
-thread, one node per thread — then programmatic dependent launch on/off and
-the one-launch persistent sweeps, and keeps the fastest.  Only the speed
-differs between candidates; every family computes the same step.  Results are
-cached in JSON keyed by GPU name, Q, precision and lattice size.
+the candidate kernel families of the stream-collide and adjoint steps in the
+dense layout — TMA staging with 8- or 4-row tiles, register kernels with 4 or
+2 nodes per thread, one node per thread — then programmatic dependent launch
+on/off and the one-launch persistent sweeps, then the fluid-only (compact)
+layout, and keeps the fastest.  Only the speed differs between candidates;
+every family and layout computes the same step.  Results are cached in JSON
+keyed by GPU name, Q, precision, lattice size and inlet kind.
 
 Timing uses a short tuning plan bound to the solver's geometry (T_tune time
 steps), with CUDA events around graph-replayed launch sequences.
@@ -88,11 +89,11 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
         hit = _load(cache).get(key)
         if hit:
             if apply:
-                lbm.lbm_plan_set_kernels(p, **hit["choice"])
+                _apply(solver, hit)
             return dict(hit, cached=True)
     dev = solver.device
     tp = lbm.Solver(p.q, p.nx, p.ny, p.nz, precision=p.precision, n_steps=t_tune, ckpt_stride=8,
-                    inlet_kind=p.inlet_kind, link=solver.link, mask=solver.mask, device=dev)
+                    inlet_kind=p.inlet_kind, link=solver.link, mask=solver.mask, device=dev, layout="dense")
     tq = tp.plan
     rho_in = torch.full((tq.n_in,), 1.001, dtype=torch.float64, device=dev)
     tau = torch.tensor([0.8], dtype=torch.float64, device=dev)
@@ -152,10 +153,25 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
         timings["sweep:best,persist=1"] = round(t * 1e6, 3)
         if t < best_t:
             best, best_t = c, t
-    result = {"choice": best, "timings_us": timings, "us_per_time_step": round(best_t * 1e6, 3), "key": key}
+    layout = "dense"
+    tp.set_layout("compact")
+    if tp.layout == "compact":
+        for pdl in (1, 0):
+            c = dict(best, pdl=pdl, persist=0)
+            t = time_sweeps(c)
+            timings[f"sweep:compact,pdl={pdl}"] = round(t * 1e6, 3)
+            if t < best_t:
+                best, best_t, layout = c, t, "compact"
+    result = {"choice": best, "layout": layout, "timings_us": timings, "us_per_time_step": round(best_t * 1e6, 3),
+              "key": key}
     if cache:
         _store(cache, key, result)
     if apply:
-        lbm.lbm_plan_set_kernels(p, **best)
+        _apply(solver, result)
     tp.plan.close()
     return dict(result, cached=False)
+
+
+def _apply(solver: lbm.Solver, result: dict) -> None:
+    solver.set_layout(result.get("layout", "dense"))
+    lbm.lbm_plan_set_kernels(solver.plan, **result["choice"])

@@ -131,6 +131,7 @@ static void launch(const PlanInfo& p, int t0, const void* gprev, const void* lam
 lbm_status adjoint_launch(const PlanInfo& plan, int t_is_zero, const void* gprev, const void* lam_in, void* lam_out,
                           const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
+    if (plan.cmp.nf) return adjoint_launch_cmp(plan, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
     const PlanInfo p = with_family(plan, plan.adj_family);
     if (adjoint_launch_tma(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s))
         return cuda_status(cudaGetLastError());

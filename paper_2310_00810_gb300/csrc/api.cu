@@ -63,6 +63,8 @@ struct lbm_plan {
     Workspace ws;
     uint8_t* mask = nullptr;
     uint32_t* link = nullptr;
+    size_t dense_state_bytes = 0;  // Q N precision: the caller's state arrays
+    int dense_n_partial = 0;       // FP64 partial slots of the dense kernels
     void* last_ws = nullptr;
     bool use_graphs = true;
     std::vector<GraphEntry> graphs;  // most recently used last
@@ -148,11 +150,38 @@ lbm_status check_common(const lbm_plan* p, const void* ws)
     return LBM_OK;
 }
 
+void drop_graphs(lbm_plan* p)
+{
+    for (auto& g : p->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    p->graphs.clear();
+}
+
+// Back to the dense layout (a new geometry invalidates the compact tables).
+void set_dense(lbm_plan* p)
+{
+    p->info.cmp = Cmp{0, nullptr, nullptr};
+    p->info.state_bytes = p->dense_state_bytes;
+    p->info.n_partial = p->dense_n_partial;
+    layout(p);
+    drop_graphs(p);
+}
+
 #define LBM_TRY(expr)                     \
     do {                                  \
         lbm_status st__ = (expr);         \
         if (st__ != LBM_OK) return st__;  \
     } while (0)
+
+// The last launch of a sweep: stream-only from the internal state cur into
+// the caller's dense array (compact layout: solids zeroed first).
+lbm_status final_stream(const lbm_plan* p, const void* cur, void* d_f, const Bc& bc, const double* tau,
+                        cudaStream_t s)
+{
+    if (!p->info.cmp.nf) return step_launch(p->info, kStreamOnly, cur, d_f, bc, tau, s);
+    if (cudaMemsetAsync(d_f, 0, p->dense_state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
+    return step_launch_cmp(p->info, kStreamOnly, cur, d_f, false, true, bc, tau, s);
+}
 
 // Issues `issue(s)` through a cached CUDA graph when that is possible.
 lbm_status run_sequence(lbm_plan* p, const GraphKey& key, cudaStream_t s,
@@ -228,6 +257,9 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     I.geo.skip_sectors = d->nx % 8 == 0 ? 1 : 0;
     I.n_partial = std::max(std::max(I.n_blocks, vec_blocks_max(I)), 1024);
     I.state_bytes = (size_t)d->q * (size_t)N * (size_t)d->precision;
+    I.cmp = Cmp{0, nullptr, nullptr};
+    p->dense_state_bytes = I.state_bytes;
+    p->dense_n_partial = I.n_partial;
     const int T = d->n_steps;
     p->k = d->ckpt_stride > 0 ? std::min(d->ckpt_stride, T) : std::max(1, (int)std::ceil(std::sqrt((double)T)));
     p->S = (T + p->k - 1) / p->k;
@@ -289,9 +321,7 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     I.tma_ty = k->tma_rows;
     I.pdl = k->pdl;
     I.use_persist = k->persist;
-    for (auto& g : p->graphs)
-        if (g.exec) cudaGraphExecDestroy(g.exec);
-    p->graphs.clear();
+    drop_graphs(p);
     return LBM_OK;
 }
 
@@ -334,6 +364,7 @@ lbm_status lbm_init_geometry(lbm_plan* p, const lbm_geom_desc* g, uint8_t* d_mas
     p->mask = d_mask;
     p->link = d_link;
     p->info.geo.link = d_link;
+    if (p->info.cmp.nf) set_dense(p);
     return LBM_OK;
 }
 
@@ -342,6 +373,32 @@ lbm_status lbm_bind_geometry(lbm_plan* p, const uint32_t* d_link)
     if (!p || !d_link) return LBM_ERR_INVALID_ARG;
     p->link = const_cast<uint32_t*>(d_link);
     p->info.geo.link = d_link;
+    if (p->info.cmp.nf) set_dense(p);
+    return LBM_OK;
+}
+
+lbm_status lbm_compact_size(const lbm_plan* p, int64_t n_fluid, size_t* bytes_out)
+{
+    if (!p || !bytes_out || n_fluid < 0 || n_fluid > p->info.geo.N) return LBM_ERR_INVALID_ARG;
+    *bytes_out = compact_table_bytes(p->info, n_fluid);
+    return LBM_OK;
+}
+
+lbm_status lbm_compact_bind(lbm_plan* p, int64_t n_fluid, void* d_tables, void* stream)
+{
+    if (!p || !p->link || n_fluid < 0 || n_fluid > p->info.geo.N) return LBM_ERR_INVALID_ARG;
+    if (n_fluid == 0) {
+        set_dense(p);
+        return LBM_OK;
+    }
+    if (!d_tables || !aligned256(d_tables)) return LBM_ERR_INVALID_ARG;
+    Cmp c{0, nullptr, nullptr};
+    LBM_TRY(compact_build(p->info, n_fluid, d_tables, &c, static_cast<cudaStream_t>(stream)));
+    p->info.cmp = c;
+    p->info.state_bytes = (size_t)p->info.q * (size_t)n_fluid * (size_t)p->info.prec;
+    p->info.n_partial = std::max(p->dense_n_partial, (int)((n_fluid + 31) / 32));  // one slot per warp
+    layout(p);
+    drop_graphs(p);
     return LBM_OK;
 }
 
@@ -383,7 +440,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, st_));
             cur = dst;
         }
-        return step_launch(p->info, kStreamOnly, cur, d_f, bc, d_tau, st_);
+        return final_stream(p, cur, d_f, bc, d_tau, st_);
     };
     GraphKey key;
     key.op = 1;
@@ -407,14 +464,17 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
     auto issue = [&](cudaStream_t st_) -> lbm_status {
-        LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, d_tau, st_));
+        if (p->info.cmp.nf)
+            LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bc, d_tau, st_));
+        else
+            LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, d_tau, st_));
         unsigned char* cur = ping0;
         for (int t = 1; t < n_steps; ++t) {
             unsigned char* dst = cur == ping0 ? ping1 : ping0;
             LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, st_));
             cur = dst;
         }
-        return step_launch(p->info, kStreamOnly, cur, d_f_out, bc, d_tau, st_);
+        return final_stream(p, cur, d_f_out, bc, d_tau, st_);
     };
     if (n_steps < 8) return issue(s);
     GraphKey key;
@@ -481,6 +541,10 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             return LBM_ERR_CUDA;
         const void* lam_cur = d_lambda;
         int lam_next = 0;
+        if (p->info.cmp.nf) {  // lambda^T into the compact layout
+            LBM_TRY(compact_gather_launch(p->info, d_lambda, ws + p->ws.lam[1], st_));
+            lam_cur = ws + p->ws.lam[1];
+        }
         for (int sg = S - 1; sg >= 0; --sg) {
             const int t0 = sg * k, len = std::min(k, T - t0);
             // seg(j) holds g^{t0 + j - 1}; for sg = 0, j = 0 stands for the rest state f^0

@@ -45,6 +45,15 @@ struct Bc {
     uint32_t* status;      // device status word (bounded waits latch LBM_ERR_TIMEOUT here)
 };
 
+// Fluid-only ("compact") layout tables (compact.cu).  nf = 0: dense layout.
+constexpr int32_t kCmpBB = -1;   // neighbour code: halfway bounce-back link
+constexpr int32_t kCmpABB = -2;  // neighbour code: Eq. 6 link through x = -1/2 or nx - 1/2
+struct Cmp {
+    long long nf;          // fluid nodes stored
+    const int32_t* idx;    // idx[k]: dense node index of compact node k (increasing)
+    const int32_t* nbr;    // nbr[(i - 1) * nf + k], i = 1..Q-1: compact index of x - c_i, or kCmpBB / kCmpABB
+};
+
 // Everything a launch needs to know about the lattice and its precision.
 struct PlanInfo {
     int q, d, prec;
@@ -66,7 +75,8 @@ struct PlanInfo {
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     size_t persist_max_bytes;
     int tma_min_tiles;  // smallest tile count for which the TMA kernels are used
-    size_t state_bytes;
+    size_t state_bytes;   // bytes of one internal state (Q N, or Q nf in the compact layout)
+    Cmp cmp;
 };
 
 // Grid barrier words of the persistent sweeps (in the status section).
@@ -198,6 +208,14 @@ inline PlanInfo with_family(const PlanInfo& p, int family)
     }
     return q;
 }
+
+size_t compact_table_bytes(const PlanInfo& p, long long nf);
+lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, cudaStream_t s);
+lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* dst, bool dense_in, bool dense_out,
+                           const Bc& bc, const double* tau, cudaStream_t s);
+lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,
+                              const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s);
+lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s);
 
 bool persist_ok(const PlanInfo& p);
 lbm_status forward_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau, cudaStream_t s);

@@ -1,0 +1,595 @@
+// Fluid-only ("compact") layout: the forward and adjoint steps over the
+// fluid nodes alone.
+//
+// The step of Eq. 1-6 of arXiv 2310.00810 (and, in the adjoint, its exact
+// transpose) moves Q populations in and Q out per node, so its time is set
+// by the bytes it moves.  A dense layout moves solid nodes as well: in a
+// Boolean sphere packing at porosity 0.45 with r = 6 the solid runs along x
+// are short, nearly every 32-byte sector holds some fluid node, and skipping
+// solid nodes saves almost nothing.  Here the state holds only the nf fluid
+// nodes, in node order (compact index k), and a neighbour table gives, per
+// direction i >= 1, where node k pulls from:
+//   nbr[(i - 1) nf + k] = compact index of x - c_i    (a fluid node)
+//                       = kCmpBB                     (halfway bounce-back link)
+//                       = kCmpABB                    (Eq. 6 link through x = -1/2 or nx - 1/2)
+// built once from the link words.  Per fluid-node update the forward moves
+// 2 Q populations plus 4 (Q - 1) table bytes and nothing for solid nodes.
+// Consecutive fluid nodes of a row have mostly consecutive neighbours, so
+// the table-driven loads of a warp stay nearly coalesced.
+//
+// Boundary rules, collision and the adjoint algebra are the ones of step.cu
+// and adjoint.cu (same helpers); only the addressing differs.  The dense
+// index idx[k] recovers (x, y, z) where the rules need it: the Eq. 6 nodes
+// (density and inlet-gradient slot of the row) and the conversions between
+// the caller's dense arrays and the internal compact states.
+#include "device.cuh"
+
+namespace lbm {
+
+namespace {
+
+constexpr int kCmpThreads = 256;
+constexpr int kScanNodes = 1024;  // nodes per block of the table-building scan (256 threads x 4)
+
+size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct TableLayout {
+    size_t idx, nbr, cmap, blk, total_slot, bytes;
+};
+
+TableLayout table_layout(const PlanInfo& p, long long nf)
+{
+    TableLayout t;
+    const long long nblk = (p.geo.N + kScanNodes - 1) / kScanNodes;
+    size_t o = 0;
+    t.idx = o;
+    o += a256(sizeof(int32_t) * (size_t)nf);
+    t.nbr = o;
+    o += a256(sizeof(int32_t) * (size_t)(p.q - 1) * (size_t)nf);
+    t.cmap = o;
+    o += a256(sizeof(int32_t) * (size_t)p.geo.N);
+    t.blk = o;
+    o += a256(sizeof(int32_t) * (size_t)nblk);
+    t.total_slot = o;
+    o += 256;
+    t.bytes = o;
+    return t;
+}
+
+// --------------------------------------------------------------- the tables
+
+__device__ __forceinline__ int block_sum_int(int v)
+{
+    __shared__ int s[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (int)threadIdx.x < nw ? s[threadIdx.x] : 0;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    return v;  // valid in thread 0
+}
+
+// Exclusive scan of one int per thread over the block (blockDim.x a multiple
+// of 32, at most 1024); *total gets the block sum.
+__device__ __forceinline__ int block_excl_scan(int v, int* total)
+{
+    __shared__ int s[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < nw ? s[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane < nw) s[lane] = x;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int before = w > 0 ? s[w - 1] : 0;
+    *total = s[nw - 1];
+    __syncthreads();
+    return before + inc - v;
+}
+
+// Fluid nodes per 1024-node block.
+__global__ void __launch_bounds__(256) k_cmp_count(const uint32_t* __restrict__ link, long long N, int* __restrict__ blk)
+{
+    const long long base = (long long)blockIdx.x * kScanNodes;
+    int c = 0;
+    for (int j = threadIdx.x; j < kScanNodes; j += blockDim.x) {
+        const long long n = base + j;
+        if (n < N && !(link[n] & kLinkSolid)) ++c;
+    }
+    c = block_sum_int(c);
+    if (threadIdx.x == 0) blk[blockIdx.x] = c;
+}
+
+// In-place exclusive scan of the block counts (one block); total fluid count out.
+__global__ void __launch_bounds__(1024) k_cmp_scan(int* __restrict__ blk, long long nblk, long long* __restrict__ total)
+{
+    long long carry = 0;
+    for (long long b0 = 0; b0 < nblk; b0 += blockDim.x) {
+        const long long b = b0 + threadIdx.x;
+        const int v = b < nblk ? blk[b] : 0;
+        int sum;
+        const int ex = block_excl_scan(v, &sum);
+        if (b < nblk) blk[b] = (int)(carry + ex);
+        carry += sum;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Dense -> compact map and the compact -> dense index, node order kept.
+__global__ void __launch_bounds__(256) k_cmp_index(const uint32_t* __restrict__ link, long long N,
+                                                   const int* __restrict__ blk, int32_t* __restrict__ cmap,
+                                                   int32_t* __restrict__ idx, long long nf)
+{
+    const long long n0 = (long long)blockIdx.x * kScanNodes + 4LL * threadIdx.x;
+    bool fl[4];
+    int c = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long long n = n0 + j;
+        fl[j] = n < N && !(link[n] & kLinkSolid);
+        c += fl[j] ? 1 : 0;
+    }
+    int sum;
+    long long k = (long long)blk[blockIdx.x] + block_excl_scan(c, &sum);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long long n = n0 + j;
+        if (n >= N) break;
+        if (fl[j] && k < nf) {
+            cmap[n] = (int32_t)k;
+            idx[k] = (int32_t)n;
+            ++k;
+        } else {
+            cmap[n] = -1;
+        }
+    }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(256) k_cmp_nbr(const uint32_t* __restrict__ link, const int32_t* __restrict__ cmap,
+                                                 const int32_t* __restrict__ idx, int32_t* __restrict__ nbr,
+                                                 long long nf, Geo g)
+{
+    using L = Lattice<Q>;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    const long long n = idx[k];
+    const int x = (int)(n % g.nx);
+    const uint32_t lw = link[n];
+    const long long plane = (long long)g.nx * g.ny;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        int32_t code;
+        const int xs = x - L::c(i, 0);
+        if ((lw >> i) & 1u) {
+            code = kCmpBB;
+        } else if (xs < 0 || xs >= g.nx) {
+            code = kCmpABB;
+        } else {
+            // a link that is neither bounce-back nor Eq. 6 starts at a fluid node inside the lattice;
+            // anything else (an inconsistent link array) is treated as bounce-back
+            const long long m = n - link_offset<Q>(i, g.nx, plane);
+            code = (m >= 0 && m < g.N) ? cmap[m] : kCmpBB;
+            if (code < 0) code = kCmpBB;
+        }
+        nbr[(long long)(i - 1) * nf + k] = code;
+    }
+}
+
+// ----------------------------------------------------------- the step kernels
+
+// The node's own inlet/outlet data for Eq. 6 (only nodes with an Eq. 6 link).
+struct Side {
+    bool xin;
+    long long row;  // z * ny + y
+};
+
+__device__ __forceinline__ Side side_of(const int32_t* __restrict__ idx, long long k, const Geo& g)
+{
+    const long long n = idx[k];
+    Side s;
+    s.xin = (n % g.nx) == 0;
+    s.row = n / g.nx;
+    return s;
+}
+
+// What compact node k receives, from the post-collision state src ([Q][nf]).
+template <int Q, typename T>
+__device__ __forceinline__ void pull_cmp(T (&v)[Q], const T* __restrict__ src, long long k, long long NF,
+                                         const int32_t (&code)[Q], bool bnd, const Cmp& c, const Geo& g,
+                                         const Bc& bc)
+{
+    using L = Lattice<Q>;
+    if (bnd) {
+        T loc[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) loc[i] = src[(long long)i * NF + k];
+        T drho, rho, u[3];
+        moments<Q, T>(loc, drho, rho, u);
+        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const Side sd = side_of(c.idx, k, g);
+        const double rw = sd.xin ? (bc.profile ? bc.rho_in[sd.row] : bc.rho_in[0]) : bc.rho_out;
+        const T drw = T(rw - 1.0), rwT = T(rw);
+        v[0] = loc[0];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            if (code[i] >= 0) {
+                v[i] = src[(long long)i * NF + code[i]];
+            } else if (code[i] == kCmpBB) {
+                v[i] = loc[L::opp(i)];
+            } else {
+                const T cu = cdot<Q, T>(i, u);
+                v[i] = -loc[L::opp(i)] + T(2.0 * L::w(i)) * (drw + rwT * (T(4.5) * cu * cu - T(1.5) * uu));
+            }
+        }
+    } else {
+        // per-direction base pointers are uniform across the block; the
+        // per-thread part of each address is a 32-bit index
+        const int32_t k32 = (int32_t)k;
+        v[0] = src[k32];
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const bool fl = code[i] >= 0;
+            const T* __restrict__ base = src + (size_t)(fl ? i : L::opp(i)) * (size_t)NF;
+            v[i] = base[fl ? code[i] : k32];
+        }
+    }
+}
+
+template <int Q>
+__device__ __forceinline__ bool load_codes(int32_t (&code)[Q], const Cmp& c, long long k)
+{
+    code[0] = 0;
+    bool bnd = false;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        code[i] = __ldg(c.nbr + (size_t)(i - 1) * (size_t)c.nf + (int32_t)k);
+        bnd |= code[i] == kCmpABB;
+    }
+    return bnd;
+}
+
+// Stores a node's Q values into the compact state, or into the caller's
+// dense array (DOUT).
+template <int Q, typename T, bool DOUT>
+__device__ __forceinline__ void store_node(T* __restrict__ dst, const T (&v)[Q], long long k, const Cmp& c,
+                                           const Geo& g)
+{
+    const long long n = DOUT ? (long long)c.idx[k] : k;
+    const size_t S = DOUT ? (size_t)g.N : (size_t)c.nf;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) dst[(size_t)i * S + n] = v[i];
+}
+
+// Update of a node with an Eq. 6 link (x = 0 or nx - 1), out of line so that
+// its extra live values (the node's own populations and velocity) do not
+// raise the register count, and lower the occupancy, of the interior path.
+template <int Q, typename T, int MODE, bool DOUT>
+__device__ __noinline__ void step_node_eq6(const T* __restrict__ src, T* __restrict__ dst, long long k, Cmp c, Geo g,
+                                           Bc bc, T omega)
+{
+    int32_t code[Q];
+    load_codes<Q>(code, c, k);
+    T v[Q];
+    pull_cmp<Q, T>(v, src, k, c.nf, code, true, c, g, bc);
+    if (MODE != kStreamOnly) collide<Q, T>(v, omega);
+    store_node<Q, T, DOUT>(dst, v, k, c, g);
+}
+
+// MODE: stream-collide, collide-only or stream-only (step.cu).  DIN: the
+// collide-only input is a dense [Q][N] state; DOUT: the output is written
+// into a dense [Q][N] state (solid entries are left to the caller).
+template <int Q, typename T, int MODE, bool DIN, bool DOUT>
+__global__ void __launch_bounds__(kCmpThreads, 4) k_step_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c,
+                                                             Geo g, Bc bc, const double* __restrict__ tau)
+{
+    pdl_enter();
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= c.nf) return;
+    const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
+    T v[Q];
+    if (MODE == kCollideOnly) {
+        const long long n = DIN ? (long long)c.idx[k] : k;
+        const size_t S = DIN ? (size_t)g.N : (size_t)c.nf;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) v[i] = src[(size_t)i * S + n];
+    } else {
+        int32_t code[Q];
+        if (load_codes<Q>(code, c, k)) {
+            step_node_eq6<Q, T, MODE, DOUT>(src, dst, k, c, g, bc, omega);
+            return;
+        }
+        pull_cmp<Q, T>(v, src, k, c.nf, code, false, c, g, bc);
+    }
+    if (MODE != kStreamOnly) collide<Q, T>(v, omega);
+    store_node<Q, T, DOUT>(dst, v, k, c, g);
+}
+
+// Transpose of the collision (adjoint.cu, step 3) at one node, from f^t (its
+// moments drho, rho, u) and mu = dL/df*: writes lambda^t and returns the
+// node's dL/domega term.  G holds the Eq. 6 velocity terms (zero inside).
+template <int Q, typename T>
+__device__ __forceinline__ T adjoint_collision(const T (&f)[Q], const T (&mu)[Q], T drho, T rho, const T (&u)[3],
+                                               const T (&G)[3], T omega, T* __restrict__ lam_out, long long k,
+                                               size_t NF)
+{
+    using L = Lattice<Q>;
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T A = 0, B[3] = {T(0), T(0), T(0)}, domT = 0;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+        const T cu = cdot<Q, T>(j, u);
+        const T wj = T(L::w(j));
+        const T P = T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+        const T feq = wj * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+        domT += mu[j] * (feq - f[j]);
+        A += mu[j] * wj * P;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a)
+            B[a] += mu[j] * wj * rho * (T(3 * L::c(j, a)) + T(9) * cu * T(L::c(j, a)) - T(3) * u[a]);
+    }
+    const T inv = T(1) / rho;
+    T Bt[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Bt[a] = (omega * B[a] + G[a]) * inv;
+    const T base = omega * A;
+    const T keep = T(1) - omega;
+#pragma unroll
+    for (int kk = 0; kk < Q; ++kk) {
+        T s = keep * mu[kk] + base;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) s += Bt[a] * (T(L::c(kk, a)) - u[a]);
+        lam_out[(size_t)kk * NF + k] = s;
+    }
+    return domT;
+}
+
+// Adjoint update of a node with an Eq. 6 link, out of line (see
+// step_node_eq6).  Adds the node's inlet gradient term (one owner per inlet
+// node) and returns its dL/domega term.
+template <int Q, typename T, bool T0>
+__device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T* __restrict__ lam_in,
+                                                T* __restrict__ lam_out, long long k, Cmp c, Geo g, Bc bc, T omega,
+                                                double* __restrict__ grad_acc)
+{
+    using L = Lattice<Q>;
+    const size_t NF = (size_t)c.nf;
+    int32_t code[Q];
+    load_codes<Q>(code, c, k);
+    // 1. f^t(x)
+    T f[Q];
+    if (T0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) f[i] = T(0);
+    } else {
+        pull_cmp<Q, T>(f, gprev, k, c.nf, code, true, c, g, bc);
+    }
+    T drho, rho, u[3];
+    moments<Q, T>(f, drho, rho, u);
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    // 2. transpose of streaming and boundaries
+    const Side sd = side_of(c.idx, k, g);
+    const T rwT = T(sd.xin ? (bc.profile ? bc.rho_in[sd.row] : bc.rho_in[0]) : bc.rho_out);
+    T mu[Q];
+    T G[3] = {T(0), T(0), T(0)};
+    double grw = 0.0;
+    mu[0] = lam_in[k];
+#pragma unroll
+    for (int j = 1; j < Q; ++j) {
+        const int o = L::opp(j);
+        const int32_t co = code[o];
+        if (co >= 0) {
+            mu[j] = lam_in[(size_t)j * NF + co];
+        } else if (co == kCmpBB) {
+            mu[j] = lam_in[(size_t)o * NF + k];
+        } else {
+            const T li = lam_in[(size_t)o * NF + k];
+            mu[j] = -li;
+            const T cu = cdot<Q, T>(o, u);
+            const T two_w = T(2.0 * L::w(o));
+            if (sd.xin) grw += (double)(li * two_w * (T(1) + T(4.5) * cu * cu - T(1.5) * uu));
+#pragma unroll
+            for (int a = 0; a < L::D; ++a) G[a] += li * two_w * rwT * (T(9) * cu * T(L::c(o, a)) - T(3) * u[a]);
+        }
+    }
+    const T domT = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF);
+    // 4. inlet gradient (one owner per inlet node)
+    if (sd.xin) grad_acc[sd.row] += grw;
+    return domT;
+}
+
+// Adjoint step in the compact layout: the gather form of adjoint.cu.  The
+// forward copies f*_j(x) to x + c_j, the node that pulls direction j from x;
+// its compact index is nbr of direction opp(j) at k (x + c_j = x - c_opp(j)).
+template <int Q, typename T, bool T0>
+__global__ void __launch_bounds__(kCmpThreads, 4)
+    k_adjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c, Geo g,
+                  Bc bc, const double* __restrict__ tau, double* __restrict__ grad_acc,
+                  double* __restrict__ partial)
+{
+    pdl_enter();
+    using L = Lattice<Q>;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
+    T dom = T(0);
+    if (k < c.nf) {
+        int32_t code[Q];
+        if (load_codes<Q>(code, c, k)) {
+            dom = adjoint_node_eq6<Q, T, T0>(gprev, lam_in, lam_out, k, c, g, bc, omega, grad_acc);
+        } else {
+            // Interior node: every load of f^t and of the gathered lambda
+            // depends only on the table, so all 2 Q are in flight together.
+            const size_t NF = (size_t)c.nf;
+            const int32_t k32 = (int32_t)k;
+            T f[Q], mu[Q];
+#pragma unroll
+            for (int i = 0; i < Q; ++i) {
+                const int o = L::opp(i);
+                if (T0) {
+                    f[i] = T(0);
+                } else {
+                    const bool fl = i > 0 && code[i] >= 0;
+                    f[i] = (gprev + (size_t)(fl ? i : o) * NF)[fl ? code[i] : k32];
+                }
+                const bool ml = i > 0 && code[o] >= 0;
+                mu[i] = (lam_in + (size_t)(ml ? i : o) * NF)[ml ? code[o] : k32];
+            }
+            T drho, rho, u[3];
+            moments<Q, T>(f, drho, rho, u);
+            const T G[3] = {T(0), T(0), T(0)};
+            dom = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF);
+        }
+    }
+    // one FP64 partial per warp (its sum in T), accumulated in place across
+    // time steps: no block barrier, so a warp that finishes early frees its
+    // slot at once instead of waiting for the slowest warp of the block
+    T dw = dom;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
+    if ((threadIdx.x & 31) == 0 && k < c.nf) partial[k >> 5] += (double)dw;  // lane 0: k = first node of the warp
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCmpThreads) k_cmp_gather(const T* __restrict__ dense, T* __restrict__ cmp, Cmp c,
+                                                            long long N, int q)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= c.nf) return;
+    const long long n = c.idx[k];
+    for (int i = 0; i < q; ++i) cmp[(long long)i * c.nf + k] = dense[(long long)i * N + n];
+}
+
+unsigned cmp_grid(long long nf) { return (unsigned)((nf + kCmpThreads - 1) / kCmpThreads); }
+
+// The sweeps use: stream-collide compact -> compact; collide-only from a
+// dense or compact state into compact; stream-only into compact or into the
+// caller's dense array.
+template <int Q, typename T>
+void launch_step(const PlanInfo& p, int mode, const void* src, void* dst, bool din, bool dout, const Bc& bc,
+                 const double* tau, cudaStream_t s)
+{
+    const T* a = static_cast<const T*>(src);
+    T* b = static_cast<T*>(dst);
+    const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
+    if (mode == kStreamCollide)
+        launch_k(p.pdl, k_step_cmp<Q, T, kStreamCollide, false, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc,
+                 tau);
+    else if (mode == kCollideOnly && din)
+        launch_k(p.pdl, k_step_cmp<Q, T, kCollideOnly, true, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc, tau);
+    else if (mode == kCollideOnly)
+        launch_k(p.pdl, k_step_cmp<Q, T, kCollideOnly, false, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc,
+                 tau);
+    else if (dout)
+        launch_k(p.pdl, k_step_cmp<Q, T, kStreamOnly, false, true>, grid, block, 0, s, a, b, p.cmp, p.geo, bc, tau);
+    else
+        launch_k(p.pdl, k_step_cmp<Q, T, kStreamOnly, false, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc, tau);
+}
+
+template <int Q, typename T>
+void launch_adjoint(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
+                    const double* tau, double* grad_acc, double* partial, cudaStream_t s)
+{
+    const T* gp = static_cast<const T*>(gprev);
+    const T* li = static_cast<const T*>(lam_in);
+    T* lo = static_cast<T*>(lam_out);
+    const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
+    if (t0)
+        launch_k(p.pdl, k_adjoint_cmp<Q, T, true>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
+                 partial);
+    else
+        launch_k(p.pdl, k_adjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
+                 partial);
+}
+
+}  // namespace
+
+size_t compact_table_bytes(const PlanInfo& p, long long nf) { return table_layout(p, nf).bytes; }
+
+lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, cudaStream_t s)
+{
+    const TableLayout t = table_layout(p, nf);
+    unsigned char* base = static_cast<unsigned char*>(tables);
+    int32_t* idx = reinterpret_cast<int32_t*>(base + t.idx);
+    int32_t* nbr = reinterpret_cast<int32_t*>(base + t.nbr);
+    int32_t* cmap = reinterpret_cast<int32_t*>(base + t.cmap);
+    int* blk = reinterpret_cast<int*>(base + t.blk);
+    long long* total = reinterpret_cast<long long*>(base + t.total_slot);
+    const long long N = p.geo.N;
+    const long long nblk = (N + kScanNodes - 1) / kScanNodes;
+    k_cmp_count<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, blk);
+    k_cmp_scan<<<1, 1024, 0, s>>>(blk, nblk, total);
+    long long got = -1;
+    if (cudaMemcpyAsync(&got, total, sizeof(got), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ERR_CUDA;
+    if (got != nf) return LBM_ERR_INVALID_ARG;
+    k_cmp_index<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, blk, cmap, idx, nf);
+    if (nf > 0) {
+        const unsigned g = cmp_grid(nf);
+        if (p.q == 9) k_cmp_nbr<9><<<g, 256, 0, s>>>(p.geo.link, cmap, idx, nbr, nf, p.geo);
+        else k_cmp_nbr<19><<<g, 256, 0, s>>>(p.geo.link, cmap, idx, nbr, nf, p.geo);
+    }
+    if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+    out->nf = nf;
+    out->idx = idx;
+    out->nbr = nbr;
+    return LBM_OK;
+}
+
+lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* dst, bool dense_in, bool dense_out,
+                           const Bc& bc, const double* tau, cudaStream_t s)
+{
+    if (p.cmp.nf == 0) return LBM_OK;
+    if (p.q == 9 && p.prec == 4) launch_step<9, float>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
+    else if (p.q == 9 && p.prec == 8) launch_step<9, double>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
+    else if (p.q == 19 && p.prec == 4) launch_step<19, float>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
+    else if (p.q == 19 && p.prec == 8) launch_step<19, double>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,
+                              const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
+{
+    if (p.cmp.nf == 0) return LBM_OK;
+    if (p.q == 9 && p.prec == 4) launch_adjoint<9, float>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    else if (p.q == 9 && p.prec == 8)
+        launch_adjoint<9, double>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    else if (p.q == 19 && p.prec == 4)
+        launch_adjoint<19, float>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    else if (p.q == 19 && p.prec == 8)
+        launch_adjoint<19, double>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s)
+{
+    if (p.cmp.nf == 0) return LBM_OK;
+    const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
+    if (p.prec == 4)
+        k_cmp_gather<float><<<grid, block, 0, s>>>(static_cast<const float*>(dense), static_cast<float*>(compact),
+                                                   p.cmp, p.geo.N, p.q);
+    else
+        k_cmp_gather<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
+                                                    p.cmp, p.geo.N, p.q);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace lbm

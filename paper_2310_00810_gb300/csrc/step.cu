@@ -65,6 +65,7 @@ static void launch(const PlanInfo& p, int mode, const void* src, void* dst, cons
 lbm_status step_launch(const PlanInfo& plan, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
                        cudaStream_t s)
 {
+    if (plan.cmp.nf) return step_launch_cmp(plan, mode, src, dst, false, false, bc, tau, s);
     const PlanInfo p = with_family(plan, plan.step_family);
     if (step_launch_tma(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (step_launch_vec(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());

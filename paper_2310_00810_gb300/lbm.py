@@ -30,6 +30,7 @@ LBM_FAMILY_AUTO, LBM_FAMILY_SCALAR, LBM_FAMILY_VEC, LBM_FAMILY_TMA = 0, 1, 2, 3
 
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
+    "lbm_compact_size", "lbm_compact_bind",
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
@@ -85,6 +86,8 @@ def load():
                 "lbm_workspace_size": [vp, C.POINTER(C.c_size_t)],
                 "lbm_init_geometry": [vp, C.POINTER(lbm_geom_desc), vp, vp, vp, vp, vp],
                 "lbm_bind_geometry": [vp, vp],
+                "lbm_compact_size": [vp, C.c_int64, C.POINTER(C.c_size_t)],
+                "lbm_compact_bind": [vp, C.c_int64, vp, vp],
                 "lbm_forward": [vp, vp, vp, f64, vp, vp, vp],
                 "lbm_step": [vp, vp, vp, f64, vp, vp, i32, vp, vp],
                 "lbm_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
@@ -218,6 +221,18 @@ def lbm_bind_geometry(plan: Plan, link) -> None:
     plan._link = link
 
 
+def lbm_compact_size(plan: Plan, n_fluid: int) -> int:
+    n = C.c_size_t()
+    _check(load().lbm_compact_size(plan.handle, int(n_fluid), C.byref(n)), "lbm_compact_size")
+    return n.value
+
+
+def lbm_compact_bind(plan: Plan, n_fluid: int, tables, stream=None) -> None:
+    _check(load().lbm_compact_bind(plan.handle, int(n_fluid), _ptr(tables, torch.uint8), _stream(stream)),
+           "lbm_compact_bind")
+    plan._tables = tables  # the plan reads the tables while it is bound to them
+
+
 def lbm_forward(plan: Plan, rho_in, tau, rho_out: float, f, ws, stream=None) -> None:
     _check(load().lbm_forward(plan.handle, _ptr(rho_in, torch.float64, plan.n_in), _ptr(tau, torch.float64, 1),
                               float(rho_out), _ptr(f, plan.dtype, plan.q * plan.N), _ptr(ws, torch.uint8),
@@ -293,11 +308,16 @@ class Solver:
     """One plan with its geometry and workspace held in torch device memory.
 
     ``geometry``: dict of ``lbm_init_geometry`` keyword arguments (kind, seed,
-    r_min, r_max, target_porosity, ...), or a uint8 mask tensor (kind MASK)."""
+    r_min, r_max, target_porosity, ...), or a uint8 mask tensor (kind MASK).
+
+    ``layout``: "dense" (every node stored), "compact" (fluid nodes only,
+    ``lbm_compact_bind``), or "auto" (compact for D3Q19, dense for D2Q9).
+    The default comes from the LBM_LAYOUT environment variable, else "auto".
+    Every array the caller sees is dense either way."""
 
     def __init__(self, q, nx, ny, nz=1, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
                  loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST, geometry=None, device="cuda", link=None,
-                 mask=None):
+                 mask=None, layout=None):
         self.device = torch.device(device)
         self.plan = Plan(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
         # the library replays its T-step sweeps as CUDA graphs on a non-default stream
@@ -320,6 +340,34 @@ class Solver:
                                   fill_isolated=False)
             else:
                 lbm_init_geometry(p, self.mask, self.link, self.info, self.porosity, **(geometry or {}))
+        self.layout, self.tables = "dense", None
+        layout = layout or os.environ.get("LBM_LAYOUT", "auto")
+        if layout not in ("dense", "compact", "auto"):
+            raise ValueError(f"layout must be dense, compact or auto, not {layout!r}")
+        self.set_layout(("compact" if q == 19 else "dense") if layout == "auto" else layout)
+
+    def set_layout(self, layout: str) -> None:
+        """Switches the plan between the dense and the fluid-only state layout
+        (results are the same; the workspace is reallocated)."""
+        p = self.plan
+        if layout == self.layout:
+            return
+        if layout == "compact":
+            with torch.cuda.device(self.device):
+                torch.cuda.current_stream().synchronize()
+            nf = int(self.info[3].item()) if self.info is not None else int((self.link[: p.N] >= 0).sum().item())
+            if nf == 0:
+                return  # nothing to compact: an all-solid lattice stays dense
+            tables = torch.empty(max(lbm_compact_size(p, nf), 256), dtype=torch.uint8, device=self.device)
+            self.run(lambda: lbm_compact_bind(p, nf, tables, self.stream))
+            self.tables, self.n_fluid = tables, nf
+        elif layout == "dense":
+            self.run(lambda: lbm_compact_bind(p, 0, None, self.stream))
+            self.tables = None
+        else:
+            raise ValueError(f"layout must be dense or compact, not {layout!r}")
+        self.layout = layout
+        self.ws = torch.zeros(lbm_workspace_size(p), dtype=torch.uint8, device=self.device)
 
     def run(self, fn):
         """Runs fn() on the solver's stream, ordered after and before the caller's stream."""

@@ -61,7 +61,8 @@ def test_batch_matches_single_instances(case, profile, monkeypatch):
     g_in, g_tau = b.adjoint(rho_in, tau, 1.0, lam)
     torch.cuda.synchronize()
     for i, (nx, ny, nz) in enumerate(sizes):
-        s = lbm.Solver(q, nx, ny, nz, precision=prec, n_steps=T, inlet_kind=inlet, geometry=geoms[i])
+        # the batch kernels follow the dense single-instance kernels operation for operation
+        s = lbm.Solver(q, nx, ny, nz, precision=prec, n_steps=T, inlet_kind=inlet, geometry=geoms[i], layout="dense")
         assert torch.equal(s.mask_field, b.view_mask(i))
         fi = s.forward(b.view_inlet(rho_in, i).contiguous(), tau[i:i + 1].contiguous(), 1.0)
         fl = ~s.mask_field.bool()

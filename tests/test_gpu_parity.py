@@ -100,11 +100,12 @@ def _state_case(q, precision, seed):
     return nx, ny, nz, g
 
 
-@pytest.fixture(params=["persist", "tma", "vec", "scalar"])
+@pytest.fixture(params=["persist", "tma", "vec", "scalar", "compact"])
 def kernel(request, monkeypatch):
-    """Runs a test with each kernel family: the one-launch persistent sweeps
-    (the default for lattices that fit in L2), the TMA-staged per-step
-    kernels, the vectorised register kernels, and one node per thread."""
+    """Runs a test with each kernel family: the one-launch persistent sweeps,
+    the TMA-staged per-step kernels, the vectorised register kernels and one
+    node per thread (all in the dense layout), and the fluid-only layout."""
+    monkeypatch.setenv("LBM_LAYOUT", "compact" if request.param == "compact" else "dense")
     if request.param == "persist":
         monkeypatch.setenv("LBM_PERSIST", "1")
     elif request.param == "tma":
