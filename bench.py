@@ -304,7 +304,9 @@ def run_native(args):
                        "nodes": N, "fluid_nodes": nf, "time_steps": wl.steps,
                        "l2": "512 MB buffer written between timed steps (L2 flush); per-step state is L2-resident",
                        "parallelism": f"replicas x{world} (independent inversions, no collective)",
-                       "kernels": tuned["choice"], "autotune_us_per_time_step": tuned.get("us_per_time_step")},
+                       "kernels": tuned["choice"], "layout": tuned.get("layout", "dense"),
+                       "autotune_us_per_time_step": tuned.get("us_per_time_step"),
+                       "autotune_timings_us": tuned.get("timings_us")},
             "e2e": e2e, "gpu_launches": launches_per_step(wl, s.plan_k if hasattr(s, "plan_k") else
                                                           max(1, math.ceil(math.sqrt(wl.steps)))) * args.steps,
             "roofline": roofline, "roofline_hbm": hbm, "cpu_baseline": cpu, "clocks": clocks,
@@ -377,7 +379,8 @@ def c3_leg(device, time_limit):
     k_ck = carman_kozeny(porosity, 2.0 * wl.r_max)
     out = {"workload": "spheres128x64x64: D3Q19 BGK FP32 128x64x64 duct, Boolean spheres r 6, "
                        f"porosity {porosity:.4f} (target 0.45), T={wl.steps}, constant head + tau",
-           "kernels": tuned["choice"], "us_per_time_step": tuned.get("us_per_time_step"),
+           "kernels": tuned["choice"], "layout": tuned.get("layout", "dense"),
+           "us_per_time_step": tuned.get("us_per_time_step"), "autotune_timings_us": tuned.get("timings_us"),
            "seconds": round(res.seconds, 2), "converged": bool(res.converged), "gradient_evaluations": inv.evaluations,
            "seconds_per_gradient_eval": round(res.seconds / max(1, inv.evaluations), 3),
            "rel_err_delta": res.rel_err_inlet, "rel_err_nu": res.rel_err_nu, "rel_err_delta_over_nu": ratio_err,

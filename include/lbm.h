@@ -116,6 +116,8 @@ typedef struct lbm_kernel_choice {
     int32_t tma_rows;        /* tile height of the D2Q9 TMA kernels: 4 or 8 */
     int32_t pdl;             /* 1: programmatic dependent launch between sweep kernels */
     int32_t persist;         /* 1: one cooperative launch per sweep (lattices up to 24 MB of state) */
+    int32_t overlap;         /* 1: the reverse sweep recomputes segment s - 1 on a second stream while
+                                the adjoint steps of segment s run (two segment buffers) */
 } lbm_kernel_choice;
 
 /* Sets / reads the plan's kernel choice (an autotuner's knob).  Cached CUDA
@@ -125,8 +127,8 @@ LBM_API lbm_status lbm_plan_set_kernels(lbm_plan* plan, const lbm_kernel_choice*
 LBM_API lbm_status lbm_plan_get_kernels(const lbm_plan* plan, lbm_kernel_choice* choice);
 
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
- * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and segment
- * buffer, adjoint ping-pong states and FP64 reduction slots. */
+ * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and two
+ * segment buffers, adjoint ping-pong states and FP64 reduction slots. */
 LBM_API lbm_status lbm_workspace_size(const lbm_plan* plan, size_t* bytes);
 
 /* Builds the geometry of section 3.1.1 / 3.3 stand-ins on the device

@@ -4,8 +4,8 @@ For a given lattice (size, Q, precision, geometry) it times, on the device,
 the candidate kernel families of the stream-collide and adjoint steps in the
 dense layout — TMA staging with 8- or 4-row tiles, register kernels with 4 or
 2 nodes per thread, one node per thread — then programmatic dependent launch
-on/off and the one-launch persistent sweeps, then the fluid-only (compact)
-layout, and keeps the fastest.  Only the speed differs between candidates;
+on/off and the one-launch persistent sweeps, the overlapped reverse sweep (recompute on a second stream) on/off, then
+the fluid-only (compact) layout, and keeps the fastest.  Only the speed differs between candidates;
 every family and layout computes the same step.  Results are cached in JSON
 keyed by GPU name, Q, precision, lattice size and inlet kind.
 
@@ -153,11 +153,17 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
         timings["sweep:best,persist=1"] = round(t * 1e6, 3)
         if t < best_t:
             best, best_t = c, t
+    for ov in (0,):
+        c = dict(best, overlap=ov)
+        t = time_sweeps(c)
+        timings[f"sweep:best,overlap={ov}"] = round(t * 1e6, 3)
+        if t < best_t:
+            best, best_t = c, t
     layout = "dense"
     tp.set_layout("compact")
     if tp.layout == "compact":
         for pdl in (1, 0):
-            c = dict(best, pdl=pdl, persist=0)
+            c = dict(best, pdl=pdl, persist=0, overlap=1)
             t = time_sweeps(c)
             timings[f"sweep:compact,pdl={pdl}"] = round(t * 1e6, 3)
             if t < best_t:

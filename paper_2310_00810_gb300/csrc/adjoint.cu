@@ -59,22 +59,32 @@ __global__ void __launch_bounds__(kStepThreads)
         double grw = 0.0;
         T rwT = T(0);
         if (xin || xout) rwT = T(xin ? (bc.profile ? bc.rho_in[(long long)z * g.ny + y] : bc.rho_in[0]) : bc.rho_out);
+        if (!(xin || xout)) {
+            // interior node: select the address, then load (all Q loads in flight together)
 #pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            const int o = L::opp(j), cx = L::c(j, 0);
-            if ((lw >> o) & 1u) {
-                mu[j] = lam_in[(long long)o * N + n];
-            } else if ((cx == -1 && xin) || (cx == 1 && xout)) {
-                const T li = lam_in[(long long)o * N + n];
-                mu[j] = -li;
-                const T cu = cdot<Q, T>(o, u);
-                const T two_w = T(2.0 * L::w(o));
-                if (xin) grw += (double)(li * two_w * (T(1) + T(4.5) * cu * cu - T(1.5) * uu));
+            for (int j = 0; j < Q; ++j) {
+                const int o = L::opp(j);
+                const bool bb = (lw >> o) & 1u;
+                mu[j] = lam_in[bb ? (long long)o * N + n : (long long)j * N + n + link_offset<Q>(j, g.nx, plane)];
+            }
+        } else {
 #pragma unroll
-                for (int a = 0; a < L::D; ++a)
-                    G[a] += li * two_w * rwT * (T(9) * cu * T(L::c(o, a)) - T(3) * u[a]);
-            } else {
-                mu[j] = lam_in[(long long)j * N + n + link_offset<Q>(j, g.nx, plane)];
+            for (int j = 0; j < Q; ++j) {
+                const int o = L::opp(j), cx = L::c(j, 0);
+                if ((lw >> o) & 1u) {
+                    mu[j] = lam_in[(long long)o * N + n];
+                } else if ((cx == -1 && xin) || (cx == 1 && xout)) {
+                    const T li = lam_in[(long long)o * N + n];
+                    mu[j] = -li;
+                    const T cu = cdot<Q, T>(o, u);
+                    const T two_w = T(2.0 * L::w(o));
+                    if (xin) grw += (double)(li * two_w * (T(1) + T(4.5) * cu * cu - T(1.5) * uu));
+#pragma unroll
+                    for (int a = 0; a < L::D; ++a)
+                        G[a] += li * two_w * rwT * (T(9) * cu * T(L::c(o, a)) - T(3) * u[a]);
+                } else {
+                    mu[j] = lam_in[(long long)j * N + n + link_offset<Q>(j, g.nx, plane)];
+                }
             }
         }
 

@@ -68,10 +68,16 @@ struct lbm_plan {
     void* last_ws = nullptr;
     bool use_graphs = true;
     std::vector<GraphEntry> graphs;  // most recently used last
+    // second stream and events of the overlapped reverse sweep (created on first use)
+    cudaStream_t helper = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // fork, join, recompute done, adjoint done
     ~lbm_plan()
     {
         for (auto& g : graphs)
             if (g.exec) cudaGraphExecDestroy(g.exec);
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (helper) cudaStreamDestroy(helper);
     }
 };
 
@@ -103,7 +109,7 @@ void layout(lbm_plan* p)
     w.ckpt = o;
     o += st * (size_t)(p->S - 1);
     w.seg = o;
-    o += st * (size_t)p->k;
+    o += st * (size_t)p->k * 2;
     w.total = o;
 }
 
@@ -286,6 +292,8 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     const char* pe = std::getenv("LBM_PERSIST");
     const char* pm = std::getenv("LBM_PERSIST_MAX_MB");
     I.use_persist = I.max_vec >= 2 && pe && pe[0] == '1';
+    const char* ov = std::getenv("LBM_OVERLAP");
+    I.overlap = !(ov && ov[0] == '0');
     I.persist_max_bytes = (size_t)(pm ? std::atof(pm) : 24.0) * (1u << 20);
     // LBM_SPIN_LIMIT bounds each grid-barrier wait of the persistent sweeps (tests set it tiny to make
     // the wait give up on purpose and check that LBM_ERR_TIMEOUT comes back)
@@ -310,7 +318,8 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     if (!p || !k) return LBM_ERR_INVALID_ARG;
     auto fam_ok = [](int f) { return f >= LBM_FAMILY_AUTO && f <= LBM_FAMILY_TMA; };
     if (!fam_ok(k->step_family) || !fam_ok(k->adjoint_family) || (k->vec != 2 && k->vec != 4) ||
-        (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1))
+        (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1) ||
+        (k->overlap != 0 && k->overlap != 1))
         return LBM_ERR_INVALID_ARG;
     PlanInfo& I = p->info;
     I.step_family = k->step_family;
@@ -321,6 +330,7 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     I.tma_ty = k->tma_rows;
     I.pdl = k->pdl;
     I.use_persist = k->persist;
+    I.overlap = k->overlap;
     drop_graphs(p);
     return LBM_OK;
 }
@@ -335,6 +345,7 @@ lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
     k->tma_rows = I.tma_ty;
     k->pdl = I.pdl;
     k->persist = I.use_persist;
+    k->overlap = I.overlap;
     return LBM_OK;
 }
 
@@ -534,39 +545,85 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
                                        reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
     }
+    // seg(b, j): state j of segment buffer b; buffer sg & 1 holds segment sg,
+    // g^{t0 + j - 1} at j >= 1 (for sg = 0, j = 0 stands for the rest state f^0)
+    auto seg = [&](int sg, int j) -> unsigned char* {
+        return ws + p->ws.seg + st * ((size_t)(sg & 1) * (size_t)k + (size_t)j);
+    };
+    auto base_of = [&](int sg) -> const unsigned char* {
+        return sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
+    };
+    auto recompute = [&](int sg, cudaStream_t s_) -> lbm_status {
+        const int len = std::min(k, T - sg * k);
+        const unsigned char* prev = base_of(sg);
+        for (int j = 1; j < len; ++j) {
+            if (sg == 0 && j == 1) {
+                if (cudaMemsetAsync(seg(0, 1), 0, p->info.state_bytes, s_) != cudaSuccess) return LBM_ERR_CUDA;
+            } else {
+                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), bc, d_tau, s_));
+            }
+            prev = seg(sg, j);
+        }
+        return LBM_OK;
+    };
+    const void* lam_cur = d_lambda;
+    int lam_next = 0;
+    auto adjoint_steps = [&](int sg, cudaStream_t s_) -> lbm_status {
+        const int len = std::min(k, T - sg * k);
+        for (int j = len - 1; j >= 0; --j) {
+            const unsigned char* src = j == 0 ? base_of(sg) : seg(sg, j);
+            const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
+            void* lam_out = ws + p->ws.lam[lam_next];
+            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, d_tau, grad_acc, partial, s_));
+            lam_cur = lam_out;
+            lam_next ^= 1;
+        }
+        return LBM_OK;
+    };
+    const bool overlap = p->info.overlap && S > 1;
+    if (overlap && !p->helper) {
+        if (cudaStreamCreateWithFlags(&p->helper, cudaStreamNonBlocking) != cudaSuccess) return LBM_ERR_CUDA;
+        for (auto& e : p->ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LBM_ERR_CUDA;
+    }
     auto issue = [&](cudaStream_t st_) -> lbm_status {
+        lam_cur = d_lambda;
+        lam_next = 0;
         if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, st_) != cudaSuccess)
             return LBM_ERR_CUDA;
         if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_partial, st_) != cudaSuccess)
             return LBM_ERR_CUDA;
-        const void* lam_cur = d_lambda;
-        int lam_next = 0;
         if (p->info.cmp.nf) {  // lambda^T into the compact layout
             LBM_TRY(compact_gather_launch(p->info, d_lambda, ws + p->ws.lam[1], st_));
             lam_cur = ws + p->ws.lam[1];
         }
-        for (int sg = S - 1; sg >= 0; --sg) {
-            const int t0 = sg * k, len = std::min(k, T - t0);
-            // seg(j) holds g^{t0 + j - 1}; for sg = 0, j = 0 stands for the rest state f^0
-            auto seg = [&](int j) -> unsigned char* { return ws + p->ws.seg + st * (size_t)j; };
-            const unsigned char* base = sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
-            const unsigned char* prev = base;
-            for (int j = 1; j < len; ++j) {
-                if (sg == 0 && j == 1) {
-                    if (cudaMemsetAsync(seg(1), 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
-                } else {
-                    LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(j), bc, d_tau, st_));
+        if (!overlap) {
+            for (int sg = S - 1; sg >= 0; --sg) {
+                LBM_TRY(recompute(sg, st_));
+                LBM_TRY(adjoint_steps(sg, st_));
+            }
+        } else {
+            // Segment sg - 1 is recomputed on the helper stream B while the
+            // adjoint steps of segment sg run on A; the two segment buffers
+            // alternate, so recomputing sg - 1 waits for the adjoint of sg + 1
+            // (the last reader of its buffer).
+            cudaStream_t A = st_, B = p->helper;
+            cudaEvent_t fork = p->ev[0], join = p->ev[1], rec_done = p->ev[2], adj_done = p->ev[3];
+            auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+            if (!ok(cudaEventRecord(fork, A)) || !ok(cudaStreamWaitEvent(B, fork, 0))) return LBM_ERR_CUDA;
+            LBM_TRY(recompute(S - 1, B));
+            if (!ok(cudaEventRecord(rec_done, B)) || !ok(cudaStreamWaitEvent(A, rec_done, 0))) return LBM_ERR_CUDA;
+            for (int sg = S - 1; sg >= 0; --sg) {
+                if (sg >= 1) {
+                    if (sg + 1 <= S - 1 && !ok(cudaStreamWaitEvent(B, adj_done, 0))) return LBM_ERR_CUDA;
+                    LBM_TRY(recompute(sg - 1, B));
+                    if (!ok(cudaEventRecord(rec_done, B))) return LBM_ERR_CUDA;
                 }
-                prev = seg(j);
+                LBM_TRY(adjoint_steps(sg, A));
+                if (!ok(cudaEventRecord(adj_done, A))) return LBM_ERR_CUDA;
+                if (sg >= 1 && !ok(cudaStreamWaitEvent(A, rec_done, 0))) return LBM_ERR_CUDA;
             }
-            for (int j = len - 1; j >= 0; --j) {
-                const unsigned char* src = j == 0 ? base : seg(j);
-                const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
-                void* lam_out = ws + p->ws.lam[lam_next];
-                LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, d_tau, grad_acc, partial, st_));
-                lam_cur = lam_out;
-                lam_next ^= 1;
-            }
+            if (!ok(cudaEventRecord(join, B)) || !ok(cudaStreamWaitEvent(A, join, 0))) return LBM_ERR_CUDA;
         }
         return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
                                        reinterpret_cast<uint32_t*>(ws + p->ws.status), st_);

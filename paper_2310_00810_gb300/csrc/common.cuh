@@ -27,7 +27,7 @@ struct Workspace {
     size_t ping[2];     // forward ping-pong states
     size_t lam[2];      // adjoint ping-pong states
     size_t ckpt;        // (S - 1) checkpoint states, slot s (1..S-1) at index s - 1
-    size_t seg;         // k segment states
+    size_t seg;         // two buffers of k segment states
     size_t total;
 };
 
@@ -72,6 +72,7 @@ struct PlanInfo {
     int adj_family;   // LBM_FAMILY_* of the adjoint kernels
     int pdl;          // 1: launch the sweep kernels with programmatic dependent launch
     int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes
+    int overlap;      // 1: reverse sweep recomputes the next segment on a second stream during the adjoint steps
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     size_t persist_max_bytes;
     int tma_min_tiles;  // smallest tile count for which the TMA kernels are used

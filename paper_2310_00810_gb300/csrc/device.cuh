@@ -92,12 +92,13 @@ __device__ __forceinline__ void pull(T (&v)[Q], const T* __restrict__ src, long 
             }
         }
     } else {
+        // the address is selected, then loaded unconditionally: the Q loads
+        // then issue together instead of one branch (and one wait) at a time
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            if ((lw >> i) & 1u)
-                v[i] = src[(long long)L::opp(i) * N + n];
-            else
-                v[i] = src[(long long)i * N + n - link_offset<Q>(i, g.nx, plane)];
+            const bool bb = (lw >> i) & 1u;
+            const long long a = bb ? (long long)L::opp(i) * N + n : (long long)i * N + n - link_offset<Q>(i, g.nx, plane);
+            v[i] = src[a];
         }
     }
 }

@@ -280,6 +280,12 @@ struct Halo2DT {
 };
 using Halo2D8 = Halo2DT<8, 4>;
 using Halo2D4 = Halo2DT<4, 6>;
+// One stage for lattices of at most one tile per SM (nothing to pipeline):
+// a quarter of the shared memory, so the next kernel's CTAs can become
+// resident beside these ones and wait at griddepcontrol.wait instead of
+// being scheduled after them.
+using Halo2D8x1 = Halo2DT<8, 1>;
+using Halo2D4x1 = Halo2DT<4, 1>;
 // every TMA destination (each box, the link box, each stage) starts on 128 bytes
 static_assert((Halo2D8::BOX * 4) % 128 == 0 && (Halo2D8::LINKS * 4) % 128 == 0 && Halo2D8::STAGE_BYTES % 128 == 0,
               "TMA shared-memory destinations must be 128-byte aligned");
@@ -393,6 +399,8 @@ struct HaloAdj2DT {
 };
 using HaloAdj2D8 = HaloAdj2DT<8, 2>;
 using HaloAdj2D4 = HaloAdj2DT<4, 3>;
+using HaloAdj2D8x1 = HaloAdj2DT<8, 1>;
+using HaloAdj2D4x1 = HaloAdj2DT<4, 1>;
 static_assert((HaloAdj2D8::BOX * 4) % 128 == 0 && HaloAdj2D8::STAGE_BYTES % 128 == 0 &&
                   (HaloAdj2D4::BOX * 4) % 128 == 0 && HaloAdj2D4::STAGE_BYTES % 128 == 0,
               "TMA shared-memory destinations must be 128-byte aligned");
@@ -662,6 +670,11 @@ int sm_count()
     return n;
 }
 
+long long halo_tiles(const PlanInfo& p, int ty)
+{
+    return (long long)((p.geo.nx + 127) / 128) * ((p.geo.ny + ty - 1) / ty);
+}
+
 template <class K>
 bool allow_smem(K kernel, size_t bytes)
 {
@@ -788,9 +801,14 @@ bool step_launch_tma(const PlanInfo& p, int mode, const void* src, void* dst, co
                      cudaStream_t s)
 {
     if (mode == kCollideOnly || !tma_ok(p, src, dst, nullptr)) return false;
-    if (p.q == 9 && p.tma_variant == 1)
-        return p.tma_ty == 4 ? step_tma_halo<Halo2D4>(p, mode, src, dst, bc, tau, s)
-                             : step_tma_halo<Halo2D8>(p, mode, src, dst, bc, tau, s);
+    if (p.q == 9 && p.tma_variant == 1) {
+        const bool one = halo_tiles(p, p.tma_ty) <= sm_count();
+        if (p.tma_ty == 4)
+            return one ? step_tma_halo<Halo2D4x1>(p, mode, src, dst, bc, tau, s)
+                       : step_tma_halo<Halo2D4>(p, mode, src, dst, bc, tau, s);
+        return one ? step_tma_halo<Halo2D8x1>(p, mode, src, dst, bc, tau, s)
+                   : step_tma_halo<Halo2D8>(p, mode, src, dst, bc, tau, s);
+    }
     return p.q == 9 ? step_tma<9>(p, mode, src, dst, bc, tau, s) : step_tma<19>(p, mode, src, dst, bc, tau, s);
 }
 
@@ -798,9 +816,14 @@ bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void
                         const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
     if (!tma_ok(p, gprev, lam_in, lam_out)) return false;
-    if (p.q == 9 && p.tma_variant == 1)
-        return p.tma_ty == 4 ? adjoint_tma_halo<HaloAdj2D4>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
-                             : adjoint_tma_halo<HaloAdj2D8>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    if (p.q == 9 && p.tma_variant == 1) {
+        const bool one = halo_tiles(p, p.tma_ty) <= sm_count();
+        if (p.tma_ty == 4)
+            return one ? adjoint_tma_halo<HaloAdj2D4x1>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
+                       : adjoint_tma_halo<HaloAdj2D4>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+        return one ? adjoint_tma_halo<HaloAdj2D8x1>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
+                   : adjoint_tma_halo<HaloAdj2D8>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    }
     return p.q == 9 ? adjoint_tma<9>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
                     : adjoint_tma<19>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
 }

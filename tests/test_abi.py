@@ -62,8 +62,8 @@ def test_workspace_size_counts_checkpoints(lib):
     p0 = lbm.Plan(9, 64, 32, 1, 4, n_steps=100)  # sqrt(T) = 10
     s1, s10, s0 = (lbm.lbm_workspace_size(p) for p in (p1, p10, p0))
     assert s10 == s0
-    # stride 1 keeps T - 1 checkpoints + 1 segment state; stride 10 keeps 9 + 10
-    assert s1 - s10 == (99 + 1 - 9 - 10) * st
+    # stride 1 keeps T - 1 checkpoints + two 1-state segment buffers; stride 10 keeps 9 + 2 x 10
+    assert s1 - s10 == (99 + 2 - 9 - 20) * st
     assert s1 > 100 * st
 
 

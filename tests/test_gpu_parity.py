@@ -281,3 +281,25 @@ def test_darcy_and_adam():
         O.adam(theta, gp * 1e-3, mm, vv, t, 0.02)
     assert np.allclose(th_d.cpu().numpy(), theta, rtol=1e-13, atol=1e-15)
     assert np.allclose(p_d.cpu().numpy(), 1.0 + 1e-3 * theta, rtol=1e-14)
+
+
+@pytest.mark.parametrize("q", [9, 19])
+@pytest.mark.parametrize("layout", ["dense", "compact"])
+def test_overlapped_reverse_sweep_is_bitwise_the_serial_one(q, layout):
+    """Recomputing segment s - 1 on a second stream during the adjoint steps
+    of segment s changes nothing: the adjoint launches and their reduction
+    order are the same."""
+    nx, ny, nz, g = _state_case(q, 4, 51)
+    T = 23
+    out = []
+    for overlap in (0, 1):
+        s = lbm.Solver(q, nx, ny, nz, precision=4, n_steps=T, ckpt_stride=4, inlet_kind=lbm.LBM_INLET_PROFILE,
+                       geometry=g, layout=layout)
+        lbm.lbm_plan_set_kernels(s.plan, overlap=overlap)
+        rin = 1.0 + W.inlet_profile(ny * nz, seed=52)
+        ut = W.perturbation((s.plan.d, *s.plan.shape), seed=53, scale=1e-3)
+        f = s.forward(dev(rin), dev([0.8]), 1.0)
+        L, lam = s.loss_grad(f, dev(ut))
+        g_in, g_tau = s.adjoint(dev(rin), dev([0.8]), 1.0, lam)
+        out.append((g_in.cpu().numpy(), g_tau.item()))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
