@@ -277,10 +277,11 @@ def run_native(args):
                 "note": "512x256 state (9.4 MB read+write per step) is L2-resident; see roofline_hbm"}
 
     e2e = None if args.no_e2e else run_e2e(P, args, device, barrier, world)
-    hbm = None if args.no_hbm_roofline else kernel_rooflines(device, hbm_peak, "disks8192x4096", 20)
-    if hbm:
-        for kern, tr in HBM_TRAFFIC.items():
-            hbm[kern]["traffic"] = tr
+    hbm = None
+    if not args.no_hbm_roofline:
+        hbm = {f"{name}/{layout}": kernel_rooflines(device, hbm_peak, name, 20, layout)
+               for name, layout in (("disks8192x4096", "dense"), ("disks8192x4096", "compact"),
+                                    ("spheres512x256x256", "compact"))}
 
     inversion = None if args.no_invert else time_to_target(P, args.invert_time_limit)
     batched = None if args.no_batch else batch_leg(device, args.batch_instances, rank)
@@ -505,58 +506,28 @@ def run_e2e(P, args, device, barrier, world):
             "steps": K, "ms_per_step": round(ms / K, 3)}
 
 
-# DRAM bytes (read + write) per launch of the two kernels on disks8192x4096, from ncu captures of
-# disks4096x2048 (profiles/k_step_tma_halo_disks4096x2048.md, profiles/k_adjoint_tma_halo_disks4096x2048.md)
-# scaled by the 4x larger node count (traffic grows in proportion to the nodes).
-HBM_TRAFFIC = {"stream-collide": 4 * (343.118080e6 + 201.248512e6), "adjoint": 4 * (642.651648e6 + 217.033472e6)}
+# DRAM bytes (read + write) per launch on the roofline lattices, from one ncu capture of each kernel
+# on a smaller lattice of the same recipe, scaled by the fluid nodes processed (traffic grows in
+# proportion): dense TMA kernels from disks4096x2048 (x 4 nodes), compact kernels from
+# disks4096x2048 (x 4.0001 fluid nodes) and spheres256x128x128 (x 8.0006 fluid nodes).  Summaries in
+# profiles/ (k_step_tma_halo_disks4096x2048.md, k_adjoint_tma_halo_disks4096x2048.md,
+# k_step_cmp_*.md, k_adjoint_cmp_*.md).
+HBM_TRAFFIC = {
+    ("disks8192x4096", "dense"): {"stream-collide": 4 * (343.118080e6 + 201.248512e6),
+                                  "adjoint": 4 * (642.651648e6 + 217.033472e6)},
+    ("disks8192x4096", "compact"): {"stream-collide": 20132542 / 5032998 * (342.648320e6 + 151.244800e6),
+                                    "adjoint": 20132542 / 5032998 * (525.750016e6 + 161.217024e6)},
+    ("spheres512x256x256", "compact"): {"stream-collide": 15090843 / 1886221 * (293.573888e6 + 116.221696e6),
+                                        "adjoint": 15090843 / 1886221 * (534.989824e6 + 171.275264e6)},
+}
 
 
-def roofline_large(device, hbm_peak):
-    """HBM roofline of the stream-collide step on a lattice larger than L2:
-    D2Q9 FP32 8192x4096 disk packing (two 1.2 GB population buffers)."""
-    import torch
-
-    from paper_2310_00810_gb300 import lbm
-    from paper_2310_00810_gb300 import workloads as W
-
-    wl = W.WORKLOADS["disks8192x4096"]
-    s = lbm.Solver(wl.q, wl.nx, wl.ny, precision=4, n_steps=2, geometry=dict(
-        kind=lbm.LBM_GEOM_DISKS, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max, target_porosity=wl.porosity),
-        device=device)
-    nf = int(s.info[3].item())
-    N = wl.nodes
-    rho_in = torch.tensor([1.001], dtype=torch.float64, device=device)
-    tau = torch.tensor([wl.tau], dtype=torch.float64, device=device)
-    a = torch.zeros((9, wl.ny, wl.nx), dtype=torch.float32, device=device)
-    b = torch.zeros_like(a)
-    n_launch = 20
-    # n steps = 1 collide-only + (n-1) stream-collide + 1 stream-only launches
-    lbm.lbm_step(s.plan, rho_in, tau, 1.0, a, b, 4, s.ws, s.stream)
-    torch.cuda.synchronize(device)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s.stream)
-    lbm.lbm_step(s.plan, rho_in, tau, 1.0, a, b, n_launch, s.ws, s.stream)
-    e1.record(s.stream)
-    torch.cuda.synchronize(device)
-    per = e0.elapsed_time(e1) * 1e-3 / (n_launch + 1)
-    byts = 2 * 9 * 4 * nf + 4 * N
-    ach = byts / per / 1e9
-    out = {"bound": "hbm", "kernel": "k_step<9,float> on disks8192x4096", "achieved": round(ach, 1),
-           "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None,
-           "bytes_per_launch": byts, "fluid_nodes": nf, "nodes": N,
-           "glups_fluid": round(nf / per / 1e9, 2)}
-    del a, b, s
-    torch.cuda.empty_cache()
-    return out
-
-
-def kernel_rooflines(device, hbm_peak, name, n_launch):
+def kernel_rooflines(device, hbm_peak, name, n_launch, layout=None):
     """Stream-collide and adjoint kernels alone on workload `name` (a lattice
-    larger than L2 for the HBM roofline): CUDA events around n_launch
-    back-to-back launches of each.  Algorithmic bytes count fluid nodes:
-    2 Q s per stream-collide update, 3 Q s per adjoint update, plus the
-    4-byte link word of every node."""
+    larger than L2 for the HBM roofline) in the given state layout: CUDA
+    events around n_launch back-to-back launches of each.  Algorithmic bytes
+    count fluid nodes: 2 Q s per stream-collide update, 3 Q s per adjoint
+    update, plus the 4-byte link word of every node."""
     import torch
 
     from paper_2310_00810_gb300 import lbm
@@ -565,7 +536,7 @@ def kernel_rooflines(device, hbm_peak, name, n_launch):
     wl = W.WORKLOADS[name]
     s = lbm.Solver(wl.q, wl.nx, wl.ny, wl.nz, precision=wl.precision, n_steps=n_launch, ckpt_stride=n_launch,
                    geometry=dict(kind=wl.geom_kind, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max,
-                                 target_porosity=wl.porosity), device=device)
+                                 target_porosity=wl.porosity), device=device, layout=layout)
     nf, N, q, sz = int(s.info[3].item()), wl.nodes, wl.q, wl.precision
     rho_in = torch.tensor([1.001], dtype=torch.float64, device=device)
     tau = torch.tensor([wl.tau], dtype=torch.float64, device=device)
@@ -597,8 +568,10 @@ def kernel_rooflines(device, hbm_peak, name, n_launch):
     for kern, t, per in (("stream-collide", t_sc, 2 * q * sz), ("adjoint", t_adj, 3 * q * sz)):
         byts = per * nf + 4 * N
         ach = byts / t / 1e9
-        out[kern] = {"bound": "hbm", "kernel": f"{kern} on {name}", "achieved": round(ach, 1), "peak": hbm_peak,
-                     "unit": "GB/s", "frac": round(ach / hbm_peak, 4), "traffic": None, "bytes_per_launch": byts,
+        tr = HBM_TRAFFIC.get((name, s.layout), {}).get(kern)
+        out[kern] = {"bound": "hbm", "kernel": f"{kern} on {name} ({s.layout} layout)", "achieved": round(ach, 1),
+                     "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                     "traffic": round(tr) if tr else None, "bytes_per_launch": byts,
                      "us_per_launch": round(t * 1e6, 2), "fluid_nodes": nf, "nodes": N,
                      "glups_fluid": round(nf / t / 1e9, 2)}
     del a, b, s
