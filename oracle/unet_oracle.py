@@ -147,61 +147,73 @@ def init_params(base: int, c_in: int, seed: int):
     return p
 
 
-def forward(p, x):
-    """Network output [b, h] and the activations the backward pass needs."""
+def keep(a):
+    return a
+
+
+def forward(p, x, store=keep):
+    """Network output [b, h] and the activations the backward pass needs.
+    `store` models the precision in which an implementation keeps each
+    activation (identity: exact FP64; a rounding function: e.g. BF16 storage);
+    it is applied to every stored layer output."""
     a = {"x": x}
     h = x
     for l in range(4):
-        h = relu(conv3x3(h, p[f"enc{l}a.w"], p[f"enc{l}a.b"]))
+        h = store(relu(conv3x3(h, p[f"enc{l}a.w"], p[f"enc{l}a.b"])))
         a[f"enc{l}a"] = h
-        h = relu(conv3x3(h, p[f"enc{l}b.w"], p[f"enc{l}b.b"]))
+        h = store(relu(conv3x3(h, p[f"enc{l}b.w"], p[f"enc{l}b.b"])))
         a[f"enc{l}b"] = h
         if l < 3:
             h, arg = maxpool2(h)
             a[f"pool{l}"], a[f"arg{l}"] = h, arg
     for l in (2, 1, 0):
-        u = upconv2(h, p[f"up{l}.w"], p[f"up{l}.b"])
+        u = store(upconv2(h, p[f"up{l}.w"], p[f"up{l}.b"]))
         a[f"up{l}"] = u
         cat = np.concatenate([u, a[f"enc{l}b"]], axis=3)
         a[f"cat{l}"] = cat
-        h = relu(conv3x3(cat, p[f"dec{l}a.w"], p[f"dec{l}a.b"]))
+        h = store(relu(conv3x3(cat, p[f"dec{l}a.w"], p[f"dec{l}a.b"])))
         a[f"dec{l}a"] = h
-        h = relu(conv3x3(h, p[f"dec{l}b.w"], p[f"dec{l}b.b"]))
+        h = store(relu(conv3x3(h, p[f"dec{l}b.w"], p[f"dec{l}b.b"])))
         a[f"dec{l}b"] = h
     out = head(h, p["head.w"], p["head.b"])
     return out, a
 
 
-def backward(p, a, gout):
-    """dL/dparams given dL/dout, through the activations of forward()."""
+def backward(p, a, gout, store=keep):
+    """dL/dparams given dL/dout, through the activations of forward(); `store`
+    is applied to every stored activation gradient (see forward)."""
     g = {}
     gh, g["head.w"], gb = head_backward(a["dec0b"], p["head.w"], gout)
+    gh = store(gh)
     g["head.b"] = np.array([gb])
     skips = {}
     for l in (0, 1, 2):
         gh = relu_backward(a[f"dec{l}b"], gh)
         gh, g[f"dec{l}b.w"], g[f"dec{l}b.b"] = conv3x3_backward(a[f"dec{l}a"], p[f"dec{l}b.w"], gh)
-        gh = relu_backward(a[f"dec{l}a"], gh)
+        gh = relu_backward(a[f"dec{l}a"], store(gh))
         gcat, g[f"dec{l}a.w"], g[f"dec{l}a.b"] = conv3x3_backward(a[f"cat{l}"], p[f"dec{l}a.w"], gh)
+        gcat = store(gcat)
         cu = a[f"up{l}"].shape[3]
         skips[l] = gcat[..., cu:]
         below = a["enc3b"] if l == 2 else a[f"dec{l + 1}b"]
         gh, g[f"up{l}.w"], g[f"up{l}.b"] = upconv2_backward(below, p[f"up{l}.w"], gcat[..., :cu])
+        gh = store(gh)
     for l in (3, 2, 1, 0):
         if l < 3:
-            gh = maxpool2_backward(a[f"arg{l}"], gh, a[f"enc{l}b"].shape) + skips[l]
+            gh = store(maxpool2_backward(a[f"arg{l}"], gh, a[f"enc{l}b"].shape) + skips[l])
         gh = relu_backward(a[f"enc{l}b"], gh)
         gh, g[f"enc{l}b.w"], g[f"enc{l}b.b"] = conv3x3_backward(a[f"enc{l}a"], p[f"enc{l}b.w"], gh)
-        gh = relu_backward(a[f"enc{l}a"], gh)
+        gh = relu_backward(a[f"enc{l}a"], store(gh))
         inp = a["x"] if l == 0 else a[f"pool{l - 1}"]
         gh, g[f"enc{l}a.w"], g[f"enc{l}a.b"] = conv3x3_backward(inp, p[f"enc{l}a.w"], gh)
+        gh = store(gh)
     return g
 
 
-def loss_and_grad(p, x, target):
-    out, a = forward(p, x)
+def loss_and_grad(p, x, target, store=keep):
+    out, a = forward(p, x, store)
     L, gout = mse(out, target)
-    return L, backward(p, a, gout), out
+    return L, backward(p, a, gout, store), out
 
 
 def adam(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

@@ -1,0 +1,925 @@
+// Learned inlet-profile initialiser (include/unet.h): a 4-level U-Net,
+// forward and backward, BF16 operands with FP32 accumulation on the tensor
+// cores (mma.sync m16n8k16), FP32 master weights and Adam.
+//
+// Every convolution is an implicit GEMM through one kernel, k_gemm, whose
+// operand loaders and epilogue are template parameters:
+//   3x3 convolution        C[pixel][co]  = sum_(tap,ci) X[pixel+tap][ci]  W[tap][ci][co]      (+bias, ReLU)
+//   its input gradient     C[pixel][ci]  = sum_(tap,co) G[pixel-tap][co]  W[tap][ci][co]
+//                          (the same GEMM with the taps flipped and the channel roles swapped)
+//   its weight gradient    C[(tap,ci)][co] = sum_pixel X[pixel+tap][ci] G[pixel][co]          (split-K)
+//   2x2 stride-2 transposed convolution: one GEMM per output phase (dy, dx), and its two
+//   gradients the same way.
+// A CTA computes a 128 x 64 tile of C with 8 warps (32 x 32 each), staging
+// 128 x 32 and 64 x 32 operand tiles in shared memory (k contiguous, rows
+// padded to 40 elements: conflict-free fragment loads).  Activations are
+// NHWC bf16 with channel counts that are multiples of 8, so every operand
+// load is a 16-byte vector.  Weight-gradient GEMMs split the pixel sum over
+// blockIdx.z into FP32 partials that a second kernel adds in a fixed order
+// (deterministic), as are the bias and head reductions.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/unet.h"
+#include "common.cuh"
+
+namespace lbm {
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int BM = 128, BN = 64, BK = 32, LDS = BK + 8;
+constexpr int kGemmThreads = 256;
+
+__device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2])
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Pixel index m of an image batch [b][h][w] -> (b, y, x).
+struct Pix {
+    int b, y, x;
+};
+__device__ __forceinline__ Pix pix_of(long long m, int H, int W)
+{
+    Pix p;
+    p.x = (int)(m % W);
+    const long long t = m / W;
+    p.y = (int)(t % H);
+    p.b = (int)(t / H);
+    return p;
+}
+
+// ---------------------------------------------------------------- loaders
+// Each fills a ROWS x BK tile (row index = m or n, k contiguous) with zeros
+// outside [0, rows) x [k0, kend).
+
+// Rows of an activation batch gathered through a tap (3x3 with zero padding,
+// or 1 tap): row = pixel, k = tap * C + c.
+struct LdIm2col {
+    const bf16* x;
+    int H, W, C, ld, off, taps;
+    __device__ void set_phase(int) {}
+    template <int ROWS>
+    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    {
+        for (int e = threadIdx.x; e < ROWS * (BK / 8); e += kGemmThreads) {
+            const int r = e / (BK / 8), j = e % (BK / 8);
+            const long long m = r0 + r;
+            const int k = k0 + 8 * j;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (m < R && k < kend) {
+                const int tap = k / C, ci = k - tap * C;
+                const Pix p = pix_of(m, H, W);
+                int yy = p.y, xx = p.x;
+                if (taps == 9) {
+                    yy += tap / 3 - 1;
+                    xx += tap % 3 - 1;
+                }
+                if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    v = *reinterpret_cast<const uint4*>(x + ((size_t)((long long)p.b * H + yy) * W + xx) * ld + off + ci);
+            }
+            *reinterpret_cast<uint4*>(&S[r][8 * j]) = v;
+        }
+    }
+};
+
+// The gradient of a 2x2 stride-2 transposed convolution's output, gathered
+// onto its input pixels: row = input pixel (b, y, x) of an H x W image,
+// k = phase * C + c, value dY[b][2y + dy][2x + dx][c].
+struct LdUpGather {
+    const bf16* g;
+    int H, W, C, ld, off;
+    __device__ void set_phase(int) {}
+    template <int ROWS>
+    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    {
+        for (int e = threadIdx.x; e < ROWS * (BK / 8); e += kGemmThreads) {
+            const int r = e / (BK / 8), j = e % (BK / 8);
+            const long long m = r0 + r;
+            const int k = k0 + 8 * j;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (m < R && k < kend) {
+                const int ph = k / C, c = k - ph * C;
+                const Pix p = pix_of(m, H, W);
+                const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
+                v = *reinterpret_cast<const uint4*>(g + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + c);
+            }
+            *reinterpret_cast<uint4*>(&S[r][8 * j]) = v;
+        }
+    }
+};
+
+// Weight rows: S[r][k] = w[row * ld + k] (+ phase * phase_stride).
+struct LdRows {
+    const bf16* w;
+    int ld;
+    long long phase_stride;
+    __device__ void set_phase(int ph) { w += ph * phase_stride; }
+    template <int ROWS>
+    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    {
+        for (int e = threadIdx.x; e < ROWS * (BK / 8); e += kGemmThreads) {
+            const int r = e / (BK / 8), j = e % (BK / 8);
+            const long long n = r0 + r;
+            const int k = k0 + 8 * j;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (n < R && k < kend) v = *reinterpret_cast<const uint4*>(w + (size_t)n * ld + k);
+            *reinterpret_cast<uint4*>(&S[r][8 * j]) = v;
+        }
+    }
+};
+
+// Transposed gather for weight gradients: row = (tap, c) with tap in
+// [0, taps), k = pixel; value X[pixel + tap][c] (zero padding).  With
+// up_phase >= 0 the pixel is an input pixel of a transposed convolution and
+// the value comes from its output pixel (2y + dy, 2x + dx) of a 2H x 2W image.
+struct LdGatherT {
+    const bf16* x;
+    int H, W, C, ld, off, taps;
+    int up;  // 1: phase-mapped output pixels (set_phase)
+    int ph;
+    __device__ void set_phase(int p) { ph = p; }
+    template <int ROWS>
+    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    {
+        constexpr int CH = ROWS / 8;  // 8-row chunks per k
+        for (int e = threadIdx.x; e < BK * CH; e += kGemmThreads) {
+            const int kk = e / CH, jc = e % CH;
+            const long long m = r0 + 8 * jc;
+            const int k = k0 + kk;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (m < R && k < kend) {
+                const int tap = (int)(m / C), c = (int)(m - (long long)tap * C);
+                const Pix p = pix_of(k, H, W);
+                if (up) {
+                    const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
+                    v = *reinterpret_cast<const uint4*>(x + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + c);
+                } else {
+                    int yy = p.y, xx = p.x;
+                    if (taps == 9) {
+                        yy += tap / 3 - 1;
+                        xx += tap % 3 - 1;
+                    }
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                        v = *reinterpret_cast<const uint4*>(x + ((size_t)((long long)p.b * H + yy) * W + xx) * ld + off + c);
+                }
+            }
+            const bf16* pv = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) S[8 * jc + i][kk] = pv[i];
+        }
+    }
+};
+
+// -------------------------------------------------------------- epilogues
+
+// y[m][off + n] = act(acc + bias[n]) in bf16.
+struct EpAct {
+    bf16* y;
+    int ld, off;
+    const float* bias;
+    int relu;
+    __device__ void set_phase(int) {}
+    __device__ void store(long long m, int n, float v0, float v1) const
+    {
+        if (bias) {
+            v0 += bias[n];
+            v1 += bias[n + 1];
+        }
+        if (relu) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+        }
+        *reinterpret_cast<__nv_bfloat162*>(y + (size_t)m * ld + off + n) = __floats2bfloat162_rn(v0, v1);
+    }
+};
+
+// Transposed-convolution output: input pixel m of an H x W image -> output
+// pixel (2y + dy, 2x + dx) of the 2H x 2W image, + bias, no activation.
+struct EpUp {
+    bf16* y;
+    int H, W, ld, off;
+    const float* bias;
+    int ph;
+    __device__ void set_phase(int p) { ph = p; }
+    __device__ void store(long long m, int n, float v0, float v1) const
+    {
+        const Pix p = pix_of(m, H, W);
+        const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
+        v0 += bias[n];
+        v1 += bias[n + 1];
+        *reinterpret_cast<__nv_bfloat162*>(y + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + n) =
+            __floats2bfloat162_rn(v0, v1);
+    }
+};
+
+// FP32 partial of a split-K product: p[split][phase][m][n].
+struct EpPartial {
+    float* p;
+    int N;
+    long long split_stride, phase_stride;
+    int split, ph;
+    __device__ void set_phase(int q) { ph = q; }
+    __device__ void store(long long m, int n, float v0, float v1) const
+    {
+        float* d = p + split * split_stride + ph * phase_stride + m * N + n;
+        d[0] = v0;
+        d[1] = v1;
+    }
+};
+
+// C[M][N] = sum_k A[m][k] B[n][k] over the k range of split blockIdx.z % splits;
+// blockIdx.z / splits is the phase handed to the loaders and the epilogue.
+template <class LA, class LB, class EP>
+__global__ void __launch_bounds__(kGemmThreads) k_gemm(LA la, LB lb, EP ep, long long M, int N, int K, int k_split,
+                                                       int splits)
+{
+    __shared__ __align__(16) bf16 As[BM][LDS];
+    __shared__ __align__(16) bf16 Bs[BN][LDS];
+    const int split = blockIdx.z % splits, ph = blockIdx.z / splits;
+    la.set_phase(ph);
+    lb.set_phase(ph);
+    ep.set_phase(ph);
+    if constexpr (std::is_same<EP, EpPartial>::value) ep.split = split;
+    const long long m0 = (long long)blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int kbeg = split * k_split, kend = min(K, kbeg + k_split);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp & 3, wn = warp >> 2, g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        la.template load<BM>(As, m0, k0, kend, M);
+        lb.template load<BN>(Bs, n0, k0, kend, N);
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t a[2][4], b[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm * 32 + i * 16 + g;
+                a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t]);
+                a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t]);
+                a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t + 8]);
+                a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn * 32 + j * 8 + g;
+                b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t]);
+                b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma16816(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long r0 = m0 + wm * 32 + i * 16 + g;
+            const int c = n0 + wn * 32 + j * 8 + 2 * t;
+            if (c >= N) continue;
+            if (r0 < M) ep.store(r0, c, acc[i][j][0], acc[i][j][1]);
+            if (r0 + 8 < M) ep.store(r0 + 8, c, acc[i][j][2], acc[i][j][3]);
+        }
+}
+
+// ------------------------------------------------------ elementwise kernels
+
+__global__ void k_sum_partials(const float* __restrict__ part, long long count, int splits, long long stride,
+                               float* __restrict__ out)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < splits; ++k) s += part[k * stride + i];
+        out[i] = s;
+    }
+}
+
+// Column sums of g[P][C] (row stride ld, channel offset off) over a range of
+// rows per block: part[block][c].
+__global__ void k_colsum(const bf16* __restrict__ g, long long P, int C, int ld, int off, long long rows,
+                         float* __restrict__ part)
+{
+    const long long r0 = (long long)blockIdx.x * rows, r1 = min(P, r0 + rows);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.0f;
+        for (long long r = r0; r < r1; ++r) s += __bfloat162float(g[r * ld + off + c]);
+        part[(long long)blockIdx.x * C + c] = s;
+    }
+}
+
+// out[p][c] = dy[p][off + c] * (y[p][c] > 0)
+__global__ void k_relu_grad(const bf16* __restrict__ dy, int ld_dy, int off_dy, const bf16* __restrict__ y,
+                            bf16* __restrict__ out, long long P, int C)
+{
+    const long long n = P * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C;
+        const int c = (int)(i - p * C);
+        const float v = __bfloat162float(y[i]) > 0.0f ? __bfloat162float(dy[p * ld_dy + off_dy + c]) : 0.0f;
+        out[i] = __float2bfloat16(v);
+    }
+}
+
+// 2x2 max-pool of x[B][H][W][C] (first maximum in tap order), tap index kept.
+__global__ void k_maxpool(const bf16* __restrict__ x, int B, int H, int W, int C, bf16* __restrict__ y,
+                          uint8_t* __restrict__ arg)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    const long long n = (long long)B * Ho * Wo * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long q = i / C;
+        const int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho);
+        const long long b = q / ((long long)Wo * Ho);
+        float best = -INFINITY;
+        int bt = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float v = __bfloat162float(x[(((b * H) + 2 * yo + t / 2) * W + 2 * xo + t % 2) * C + c]);
+            if (v > best) {
+                best = v;
+                bt = t;
+            }
+        }
+        y[i] = __float2bfloat16(best);
+        arg[i] = (uint8_t)bt;
+    }
+}
+
+// dx[B][H][W][C] = scatter of dy at the max-pool taps + skip[...][off + c] (row stride ld_s)
+__global__ void k_maxpool_grad(const bf16* __restrict__ dy, const uint8_t* __restrict__ arg, int B, int H, int W,
+                               int C, const bf16* __restrict__ skip, int ld_s, int off_s, bf16* __restrict__ dx)
+{
+    const long long n = (long long)B * H * W * C;
+    const int Ho = H / 2, Wo = W / 2;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long p = i / C;
+        const int xx = (int)(p % W), yy = (int)((p / W) % H);
+        const long long b = p / ((long long)W * H);
+        const long long o = (((b * Ho) + yy / 2) * Wo + xx / 2) * C + c;
+        const int t = (yy % 2) * 2 + (xx % 2);
+        float v = arg[o] == t ? __bfloat162float(dy[o]) : 0.0f;
+        v += __bfloat162float(skip[p * ld_s + off_s + c]);
+        dx[i] = __float2bfloat16(v);
+    }
+}
+
+// dst[p][off + c] = src[p][c]
+__global__ void k_copy_channels(const bf16* __restrict__ src, long long P, int C, bf16* __restrict__ dst, int ld,
+                                int off)
+{
+    const long long n = P * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long p = i / C;
+        dst[p * ld + off + (i - p * C)] = src[i];
+    }
+}
+
+// out[b][h] = mean_w (sum_c x[b][h][w][c] w[c] + bias): one block per row (b, h).
+__global__ void k_head(const bf16* __restrict__ x, int W, int C, const float* __restrict__ w,
+                       const float* __restrict__ bias, float* __restrict__ out)
+{
+    const long long row = blockIdx.x;
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < W * C; i += blockDim.x) s += __bfloat162float(x[row * W * C + i]) * w[i % C];
+    __shared__ float red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        out[row] = t / (float)W + bias[0];
+    }
+}
+
+// Loss mean((out - target)^2) and gout = 2 (out - target) / n (one block).
+__global__ void k_mse(const float* __restrict__ out, const float* __restrict__ target, int n, float* __restrict__ loss,
+                      float* __restrict__ gout)
+{
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float d = out[i] - target[i];
+        s += d * d;
+        gout[i] = 2.0f * d / (float)n;
+    }
+    __shared__ float red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        *loss = t / (float)n;
+    }
+}
+
+// Head backward, one block per row (b, h): dx[b][h][w][c] = gout[b][h] / W * w[c];
+// part_w[row][c] = sum_w x[b][h][w][c] gout / W.
+__global__ void k_head_grad(const bf16* __restrict__ x, int W, int C, const float* __restrict__ w,
+                            const float* __restrict__ gout, bf16* __restrict__ dx, float* __restrict__ part_w)
+{
+    const long long row = blockIdx.x;
+    const float gr = gout[row] / (float)W;
+    for (int i = threadIdx.x; i < W * C; i += blockDim.x) dx[row * W * C + i] = __float2bfloat16(gr * w[i % C]);
+    for (int c = threadIdx.x; c < C; c += blockDim.x) {
+        float s = 0.0f;
+        for (int xw = 0; xw < W; ++xw) s += __bfloat162float(x[(row * W + xw) * C + c]);
+        part_w[row * C + c] = s * gr;
+    }
+}
+
+__global__ void k_sum_vector(const float* __restrict__ v, int n, float* __restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        float s = 0.0f;
+        for (int i = 0; i < n; ++i) s += v[i];
+        *out = s;
+    }
+}
+
+// Input packing: x[b][h][w][c] = (u_x s, u_y s, mask, 0 ...).
+__global__ void k_pack(const double* __restrict__ u, const uint8_t* __restrict__ mask, int B, int H, int W,
+                       float scale, bf16* __restrict__ x)
+{
+    const long long n = (long long)B * H * W;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / ((long long)H * W), hw = i - b * H * W;
+        bf16* o = x + i * UNET_IN_CHANNELS;
+        o[0] = __float2bfloat16((float)u[(b * 2 + 0) * H * W + hw] * scale);
+        o[1] = __float2bfloat16((float)u[(b * 2 + 1) * H * W + hw] * scale);
+        o[2] = __float2bfloat16(mask[i] ? 1.0f : 0.0f);
+#pragma unroll
+        for (int c = 3; c < UNET_IN_CHANNELS; ++c) o[c] = __float2bfloat16(0.0f);
+    }
+}
+
+// FP32 master [taps][Cin][Cout] -> fwd[co][tap * Cin + ci] and
+// bwd[ci][tap' * Cout + co] (tap' = taps - 1 - tap for a 3x3 kernel: the
+// input gradient is the correlation with the flipped kernel; for the
+// transposed convolution tap' = tap, fwd is [phase][co][ci]).
+__global__ void k_prep_weights(const float* __restrict__ w, int taps, int Cin, int Cout, int flip, int phase_major,
+                               bf16* __restrict__ fwd, bf16* __restrict__ bwd)
+{
+    const long long n = (long long)taps * Cin * Cout;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int co = (int)(i % Cout), ci = (int)((i / Cout) % Cin), tap = (int)(i / ((long long)Cout * Cin));
+        const bf16 v = __float2bfloat16(w[i]);
+        if (phase_major) fwd[((long long)tap * Cout + co) * Cin + ci] = v;
+        else fwd[(long long)co * taps * Cin + (long long)tap * Cin + ci] = v;
+        const int tb = flip ? taps - 1 - tap : tap;
+        bwd[(long long)ci * taps * Cout + (long long)tb * Cout + co] = v;
+    }
+}
+
+__global__ void k_adam_f32(long long n, float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                           const float* __restrict__ g, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.0f - b1) * gi;
+        const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// ------------------------------------------------------------ host side
+
+unsigned ew_grid(long long n) { return (unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152 * 16)); }
+
+struct Tensor {
+    int64_t off, count;
+};
+
+// Parameter tensors in the order of unet.h.
+std::vector<Tensor> param_tensors(int base, std::vector<int>* taps_out = nullptr, std::vector<int>* cin_out = nullptr,
+                                  std::vector<int>* cout_out = nullptr)
+{
+    std::vector<Tensor> t;
+    std::vector<int> taps, cin, cout;
+    int64_t o = 0;
+    auto add = [&](int tp, int ci, int co) {
+        t.push_back({o, (int64_t)tp * ci * co});
+        o += (int64_t)tp * ci * co;
+        taps.push_back(tp), cin.push_back(ci), cout.push_back(co);
+        t.push_back({o, co});  // bias
+        o += co;
+        taps.push_back(0), cin.push_back(0), cout.push_back(co);
+    };
+    const int c[4] = {base, 2 * base, 4 * base, 8 * base};
+    int prev = UNET_IN_CHANNELS;
+    for (int l = 0; l < 4; ++l) {
+        add(9, prev, c[l]);
+        add(9, c[l], c[l]);
+        prev = c[l];
+    }
+    for (int l = 2; l >= 0; --l) {
+        add(4, c[l + 1], c[l]);
+        add(9, 2 * c[l], c[l]);
+        add(9, c[l], c[l]);
+    }
+    t.push_back({o, base});
+    o += base;
+    taps.push_back(1), cin.push_back(base), cout.push_back(1);
+    t.push_back({o, 1});
+    taps.push_back(0), cin.push_back(0), cout.push_back(1);
+    if (taps_out) *taps_out = taps;
+    if (cin_out) *cin_out = cin;
+    if (cout_out) *cout_out = cout;
+    return t;
+}
+
+constexpr int kMaxSplits = 16;
+constexpr long long kSplitPixels = 8192;
+
+struct Layout {
+    int B, H, W, c[4];
+    int Hl[4], Wl[4];
+    long long P[4];                              // pixels per level (all samples)
+    size_t wf[17], wb[17];                       // bf16 operand layouts of the 17 convolution layers (forward order)
+    size_t bias;                                 // FP32 copy of all parameters (biases and head read from it)
+    size_t ea[4], eb[4], pool[3], arg[3], cat[3], da[3], db[3];
+    size_t out, gout, loss_tmp;
+    size_t gA, gB, gC, gcat[3];
+    size_t part;                                 // split-K / column-sum partials (FP32)
+    long long part_floats;
+    size_t total;
+    int64_t n_params;
+};
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool make_layout(const unet_desc* d, Layout* L)
+{
+    if (!d || d->base < 8 || d->base % 8 || d->height < 8 || d->height % 8 || d->width < 8 || d->width % 8 ||
+        d->batch < 1 || d->base > 256)
+        return false;
+    Layout& l = *L;
+    l.B = d->batch;
+    l.H = d->height;
+    l.W = d->width;
+    for (int i = 0; i < 4; ++i) {
+        l.c[i] = d->base << i;
+        l.Hl[i] = l.H >> i;
+        l.Wl[i] = l.W >> i;
+        l.P[i] = (long long)l.B * l.Hl[i] * l.Wl[i];
+    }
+    std::vector<int> taps, cin, cout;
+    const auto t = param_tensors(d->base, &taps, &cin, &cout);
+    l.n_params = t.back().off + t.back().count;
+    size_t o = 0;
+    int wi = 0;
+    long long max_part = 0;
+    for (size_t i = 0; i + 2 < t.size(); i += 2) {  // weight tensors of the 11 layers
+        const size_t bytes = al256(sizeof(bf16) * (size_t)t[i].count);
+        l.wf[wi] = o;
+        o += bytes;
+        l.wb[wi] = o;
+        o += bytes;
+        ++wi;
+    }
+    l.bias = o;
+    o += al256(sizeof(float) * (size_t)l.n_params);
+    auto act = [&](long long P, int C) {
+        const size_t off = o;
+        o += al256(sizeof(bf16) * (size_t)P * C);
+        return off;
+    };
+    for (int i = 0; i < 4; ++i) {
+        l.ea[i] = act(l.P[i], l.c[i]);
+        l.eb[i] = act(l.P[i], l.c[i]);
+    }
+    for (int i = 0; i < 3; ++i) {
+        l.pool[i] = act(l.P[i + 1], l.c[i]);
+        l.arg[i] = o;
+        o += al256((size_t)l.P[i + 1] * l.c[i]);
+        l.cat[i] = act(l.P[i], 2 * l.c[i]);
+        l.da[i] = act(l.P[i], l.c[i]);
+        l.db[i] = act(l.P[i], l.c[i]);
+        l.gcat[i] = act(l.P[i], 2 * l.c[i]);
+    }
+    long long gmax = 0;
+    for (int i = 0; i < 4; ++i) gmax = std::max(gmax, l.P[i] * 2 * l.c[i]);
+    l.gA = act(gmax, 1);
+    l.gB = act(gmax, 1);
+    l.gC = act(gmax, 1);
+    l.out = o;
+    o += al256(sizeof(float) * (size_t)l.B * l.H);
+    l.gout = o;
+    o += al256(sizeof(float) * (size_t)l.B * l.H);
+    l.loss_tmp = o;
+    o += 256;
+    // partials: weight gradients (splits x taps Cin Cout), column sums (blocks x C), head (rows x c0)
+    for (int i = 0; i < 4; ++i) {
+        const long long s = std::min<long long>(kMaxSplits, (l.P[i] + kSplitPixels - 1) / kSplitPixels);
+        const long long cmax = 2LL * l.c[std::min(i + 1, 3)];
+        max_part = std::max(max_part, s * 9 * cmax * cmax);
+        max_part = std::max(max_part, 256LL * cmax);
+    }
+    max_part = std::max(max_part, (long long)l.B * l.H * l.c[0]);
+    l.part = o;
+    l.part_floats = max_part;
+    o += al256(sizeof(float) * (size_t)max_part);
+    l.total = o;
+    return true;
+}
+
+template <class T>
+T* at(void* ws, size_t off)
+{
+    return reinterpret_cast<T*>(static_cast<unsigned char*>(ws) + off);
+}
+
+struct Ctx {
+    const Layout& L;
+    void* ws;
+    cudaStream_t s;
+    std::vector<Tensor> t;
+    bf16* wf(int layer) const { return at<bf16>(ws, L.wf[layer]); }
+    bf16* wb(int layer) const { return at<bf16>(ws, L.wb[layer]); }
+    const float* pw(int tensor) const { return at<float>(ws, L.bias) + t[tensor].off; }  // FP32 copy of a tensor
+};
+
+template <class LA, class LB, class EP>
+void gemm(cudaStream_t s, const LA& la, const LB& lb, const EP& ep, long long M, int N, int K, int splits, int phases)
+{
+    const int k_split = ((K + splits - 1) / splits + BK - 1) / BK * BK;
+    const dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)(splits * phases));
+    k_gemm<LA, LB, EP><<<grid, kGemmThreads, 0, s>>>(la, lb, ep, M, N, K, k_split, splits);
+}
+
+// conv3x3 (+bias, ReLU) of x (level geometry H x W, Cin channels at ld/off) into y (contiguous Cout).
+void conv_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W, int Cin, int ld, int off, bf16* y,
+              int Cout)
+{
+    const long long P = (long long)C.L.B * H * W;
+    LdIm2col la{x, H, W, Cin, ld, off, 9};
+    LdRows lb{C.wf(layer), 9 * Cin, 0};
+    EpAct ep{y, Cout, 0, C.pw(wtensor + 1), 1};
+    gemm(C.s, la, lb, ep, P, Cout, 9 * Cin, 1, 1);
+}
+
+int splits_for(long long P) { return (int)std::min<long long>(kMaxSplits, (P + kSplitPixels - 1) / kSplitPixels); }
+
+// Weight and bias gradients of a 3x3 convolution with input x (ld/off) and
+// pre-activation gradient g (contiguous [P][Cout]); dx into dxo (contiguous
+// [P][Cin]) unless null.
+void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W, int Cin, int ld, int off,
+              const bf16* g, int Cout, float* grad, bf16* dxo)
+{
+    const long long P = (long long)C.L.B * H * W;
+    float* part = at<float>(C.ws, C.L.part);
+    // dW[(tap, ci)][co] = sum_p x[p + tap][ci] g[p][co]
+    const int sp = splits_for(P);
+    LdGatherT la{x, H, W, Cin, ld, off, 9, 0, 0};
+    LdGatherT lb{g, H, W, Cout, Cout, 0, 1, 0, 0};
+    const long long Mw = 9LL * Cin;
+    EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
+    gemm(C.s, la, lb, ep, Mw, Cout, (int)P, sp, 1);
+    k_sum_partials<<<ew_grid(Mw * Cout), 256, 0, C.s>>>(part, Mw * Cout, sp, Mw * Cout, grad + C.t[wtensor].off);
+    // db[co] = sum_p g[p][co]
+    const long long rows = (P + 255) / 256;
+    const int nb = (int)((P + rows - 1) / rows);
+    k_colsum<<<nb, 256, 0, C.s>>>(g, P, Cout, Cout, 0, rows, part);
+    k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
+    if (dxo) {
+        LdIm2col la2{g, H, W, Cout, Cout, 0, 9};
+        LdRows lb2{C.wb(layer), 9 * Cout, 0};
+        EpAct ep2{dxo, Cin, 0, nullptr, 0};
+        gemm(C.s, la2, lb2, ep2, P, Cin, 9 * Cout, 1, 1);
+    }
+}
+
+// Transposed convolution (2x2, stride 2) of x (level l+1 geometry Hs x Ws,
+// Cin contiguous) into the first Cout channels of y (level l, row stride ld).
+void up_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws, int Cin, bf16* y, int Cout, int ld)
+{
+    const long long P = (long long)C.L.B * Hs * Ws;
+    LdIm2col la{x, Hs, Ws, Cin, Cin, 0, 1};
+    LdRows lb{C.wf(layer), Cin, (long long)Cout * Cin};
+    EpUp ep{y, Hs, Ws, ld, 0, C.pw(wtensor + 1), 0};
+    gemm(C.s, la, lb, ep, P, Cout, Cin, 1, 4);
+}
+
+// Gradients of the transposed convolution: input x (Hs x Ws, Cin), output
+// gradient in the first Cout channels of gy (row stride ld, level l).
+void up_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws, int Cin, const bf16* gy, int Cout,
+            int ld, float* grad, bf16* dxo)
+{
+    const long long P = (long long)C.L.B * Hs * Ws;
+    float* part = at<float>(C.ws, C.L.part);
+    const int sp = splits_for(P);
+    // dW[phase][ci][co] = sum_p x[p][ci] gy[up(p, phase)][co]
+    LdGatherT la{x, Hs, Ws, Cin, Cin, 0, 1, 0, 0};
+    LdGatherT lb{gy, Hs, Ws, Cout, ld, 0, 1, 1, 0};
+    EpPartial ep{part, Cout, 4LL * Cin * Cout, (long long)Cin * Cout, 0, 0};
+    gemm(C.s, la, lb, ep, Cin, Cout, (int)P, sp, 4);
+    k_sum_partials<<<ew_grid(4LL * Cin * Cout), 256, 0, C.s>>>(part, 4LL * Cin * Cout, sp, 4LL * Cin * Cout,
+                                                               grad + C.t[wtensor].off);
+    // db[co] = sum over output pixels of gy[..][co]
+    const long long Po = 4 * P;
+    const long long rows = (Po + 255) / 256;
+    const int nb = (int)((Po + rows - 1) / rows);
+    k_colsum<<<nb, 256, 0, C.s>>>(gy, Po, Cout, ld, 0, rows, part);
+    k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
+    // dx[p][ci] = sum_(phase, co) gy[up(p, phase)][co] W[phase][ci][co]
+    LdUpGather la2{gy, Hs, Ws, Cout, ld, 0};
+    LdRows lb2{C.wb(layer), 4 * Cout, 0};
+    EpAct ep2{dxo, Cin, 0, nullptr, 0};
+    gemm(C.s, la2, lb2, ep2, P, Cin, 4 * Cout, 1, 1);
+}
+
+}  // namespace
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+lbm_status unet_param_layout(int32_t base, int32_t* n_tensors, int64_t* n_params, int64_t* offsets, int64_t* counts)
+{
+    if (base < 8 || base % 8 || base > 256 || !n_tensors || !n_params) return LBM_ERR_INVALID_ARG;
+    const auto t = param_tensors(base);
+    *n_tensors = (int32_t)t.size();
+    *n_params = t.back().off + t.back().count;
+    for (size_t i = 0; i < t.size(); ++i) {
+        if (offsets) offsets[i] = t[i].off;
+        if (counts) counts[i] = t[i].count;
+    }
+    return LBM_OK;
+}
+
+lbm_status unet_workspace_size(const unet_desc* d, size_t* bytes)
+{
+    Layout L;
+    if (!bytes || !make_layout(d, &L)) return LBM_ERR_INVALID_ARG;
+    *bytes = L.total;
+    return LBM_OK;
+}
+
+lbm_status unet_pack_input(const unet_desc* d, const double* d_u, const uint8_t* d_mask, double scale, uint16_t* d_x,
+                           void* stream)
+{
+    Layout L;
+    if (!make_layout(d, &L) || !d_u || !d_mask || !d_x) return LBM_ERR_INVALID_ARG;
+    const long long n = (long long)L.B * L.H * L.W;
+    k_pack<<<ew_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(d_u, d_mask, L.B, L.H, L.W, (float)scale,
+                                                                      reinterpret_cast<bf16*>(d_x));
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status unet_prepare_weights(const unet_desc* d, const float* d_params, void* d_ws, void* stream)
+{
+    Layout L;
+    if (!make_layout(d, &L) || !d_params || !d_ws) return LBM_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int> taps, cin, cout;
+    const auto t = param_tensors(d->base, &taps, &cin, &cout);
+    for (size_t i = 0, layer = 0; i + 2 < t.size(); i += 2, ++layer) {
+        const bool up = taps[i] == 4;
+        k_prep_weights<<<ew_grid(t[i].count), 256, 0, s>>>(d_params + t[i].off, taps[i], cin[i], cout[i], up ? 0 : 1,
+                                                           up ? 1 : 0, at<bf16>(d_ws, L.wf[layer]),
+                                                           at<bf16>(d_ws, L.wb[layer]));
+    }
+    if (cudaMemcpyAsync(at<float>(d_ws, L.bias), d_params, sizeof(float) * (size_t)L.n_params,
+                        cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status unet_forward(const unet_desc* d, const uint16_t* d_x, float* d_out, void* d_ws, void* stream)
+{
+    Layout L;
+    if (!make_layout(d, &L) || !d_x || !d_out || !d_ws) return LBM_ERR_INVALID_ARG;
+    Ctx C{L, d_ws, static_cast<cudaStream_t>(stream), param_tensors(d->base)};
+    const bf16* x = reinterpret_cast<const bf16*>(d_x);
+    int tensor = 0, layer = 0;
+    const bf16* in = x;
+    int cin = UNET_IN_CHANNELS;
+    for (int l = 0; l < 4; ++l) {
+        bf16* ea = at<bf16>(d_ws, L.ea[l]);
+        bf16* eb = at<bf16>(d_ws, L.eb[l]);
+        conv_fwd(C, layer++, tensor, in, L.Hl[l], L.Wl[l], cin, cin, 0, ea, L.c[l]);
+        tensor += 2;
+        conv_fwd(C, layer++, tensor, ea, L.Hl[l], L.Wl[l], L.c[l], L.c[l], 0, eb, L.c[l]);
+        tensor += 2;
+        if (l < 3) {
+            bf16* pool = at<bf16>(d_ws, L.pool[l]);
+            k_maxpool<<<ew_grid(L.P[l + 1] * L.c[l]), 256, 0, C.s>>>(eb, L.B, L.Hl[l], L.Wl[l], L.c[l], pool,
+                                                                       at<uint8_t>(d_ws, L.arg[l]));
+            k_copy_channels<<<ew_grid(L.P[l] * L.c[l]), 256, 0, C.s>>>(eb, L.P[l], L.c[l], at<bf16>(d_ws, L.cat[l]),
+                                                                        2 * L.c[l], L.c[l]);
+            in = pool;
+            cin = L.c[l];
+        }
+    }
+    const bf16* below = at<bf16>(d_ws, L.eb[3]);
+    for (int l = 2; l >= 0; --l) {
+        bf16* cat = at<bf16>(d_ws, L.cat[l]);
+        up_fwd(C, layer++, tensor, below, L.Hl[l + 1], L.Wl[l + 1], L.c[l + 1], cat, L.c[l], 2 * L.c[l]);
+        tensor += 2;
+        bf16* da = at<bf16>(d_ws, L.da[l]);
+        bf16* db = at<bf16>(d_ws, L.db[l]);
+        conv_fwd(C, layer++, tensor, cat, L.Hl[l], L.Wl[l], 2 * L.c[l], 2 * L.c[l], 0, da, L.c[l]);
+        tensor += 2;
+        conv_fwd(C, layer++, tensor, da, L.Hl[l], L.Wl[l], L.c[l], L.c[l], 0, db, L.c[l]);
+        tensor += 2;
+        below = db;
+    }
+    float* out = at<float>(d_ws, L.out);
+    k_head<<<L.B * L.H, 256, 0, C.s>>>(below, L.W, L.c[0], C.pw(tensor), C.pw(tensor + 1), out);
+    if (cudaMemcpyAsync(d_out, out, sizeof(float) * (size_t)L.B * L.H, cudaMemcpyDeviceToDevice, C.s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status unet_backward(const unet_desc* d, const uint16_t* d_x, const float* d_target, float* d_loss, float* d_grad,
+                         void* d_ws, void* stream)
+{
+    Layout L;
+    if (!make_layout(d, &L) || !d_x || !d_target || !d_loss || !d_grad || !d_ws) return LBM_ERR_INVALID_ARG;
+    Ctx C{L, d_ws, static_cast<cudaStream_t>(stream), param_tensors(d->base)};
+    const int nt = (int)C.t.size();
+    float* gout = at<float>(d_ws, L.gout);
+    float* part = at<float>(d_ws, L.part);
+    const int rows = L.B * L.H;
+    k_mse<<<1, 256, 0, C.s>>>(at<float>(d_ws, L.out), d_target, rows, d_loss, gout);
+    // head: tensors nt-2 (w), nt-1 (b)
+    bf16* gA = at<bf16>(d_ws, L.gA);
+    bf16* gB = at<bf16>(d_ws, L.gB);
+    bf16* gC = at<bf16>(d_ws, L.gC);
+    const bf16* db0 = at<bf16>(d_ws, L.db[0]);
+    k_head_grad<<<rows, 256, 0, C.s>>>(db0, L.W, L.c[0], C.pw(nt - 2), gout, gA, part);
+    k_sum_partials<<<ew_grid(L.c[0]), 256, 0, C.s>>>(part, L.c[0], rows, L.c[0], d_grad + C.t[nt - 2].off);
+    k_sum_vector<<<1, 32, 0, C.s>>>(gout, rows, d_grad + C.t[nt - 1].off);
+    // decoder, l = 0, 1, 2 (tensors and layers counted from the end)
+    int tensor = nt - 2, layer = 16;  // 17 convolution layers, numbered in forward order
+    for (int l = 0; l <= 2; ++l) {
+        const int Hl = L.Hl[l], Wl = L.Wl[l], c = L.c[l];
+        // gA = dL/d(db_l)
+        tensor -= 2;  // dec{l}b
+        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.db[l]), gB, L.P[l], c);
+        conv_bwd(C, layer--, tensor, at<bf16>(d_ws, L.da[l]), Hl, Wl, c, c, 0, gB, c, d_grad, gA);
+        tensor -= 2;  // dec{l}a
+        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.da[l]), gB, L.P[l], c);
+        bf16* gcat = at<bf16>(d_ws, L.gcat[l]);
+        conv_bwd(C, layer--, tensor, at<bf16>(d_ws, L.cat[l]), Hl, Wl, 2 * c, 2 * c, 0, gB, c, d_grad, gcat);
+        tensor -= 2;  // up{l}
+        const bf16* below = l == 2 ? at<bf16>(d_ws, L.eb[3]) : at<bf16>(d_ws, L.db[l + 1]);
+        up_bwd(C, layer--, tensor, below, L.Hl[l + 1], L.Wl[l + 1], L.c[l + 1], gcat, c, 2 * c, d_grad, gA);
+    }
+    // encoder, l = 3 .. 0; gA = dL/d(eb_3) on entry
+    for (int l = 3; l >= 0; --l) {
+        const int Hl = L.Hl[l], Wl = L.Wl[l], c = L.c[l];
+        if (l < 3) {  // gA = dL/d(pool_l) -> dL/d(eb_l), plus the skip gradient
+            k_maxpool_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, at<uint8_t>(d_ws, L.arg[l]), L.B, Hl, Wl, c,
+                                                                   at<bf16>(d_ws, L.gcat[l]), 2 * c, c, gC);
+            std::swap(gA, gC);
+        }
+        tensor -= 2;  // enc{l}b
+        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.eb[l]), gB, L.P[l], c);
+        conv_bwd(C, layer--, tensor, at<bf16>(d_ws, L.ea[l]), Hl, Wl, c, c, 0, gB, c, d_grad, gA);
+        tensor -= 2;  // enc{l}a
+        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.ea[l]), gB, L.P[l], c);
+        const int cin = l == 0 ? UNET_IN_CHANNELS : L.c[l - 1];
+        const bf16* in = l == 0 ? reinterpret_cast<const bf16*>(d_x) : at<bf16>(d_ws, L.pool[l - 1]);
+        conv_bwd(C, layer--, tensor, in, Hl, Wl, cin, cin, 0, gB, c, d_grad, l == 0 ? nullptr : gA);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status unet_adam(int64_t n, float* d_params, float* d_m, float* d_v, const float* d_grad, int32_t t, float lr,
+                     float beta1, float beta2, float eps, void* stream)
+{
+    if (n < 1 || t < 1 || !d_params || !d_m || !d_v || !d_grad) return LBM_ERR_INVALID_ARG;
+    const float c1 = 1.0f - powf(beta1, (float)t), c2 = 1.0f - powf(beta2, (float)t);
+    k_adam_f32<<<ew_grid(n), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, d_params, d_m, d_v, d_grad, lr, beta1,
+                                                                          beta2, eps, c1, c2);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -34,6 +34,8 @@ ENTRY_POINTS = (
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
+    "unet_param_layout", "unet_workspace_size", "unet_pack_input", "unet_prepare_weights", "unet_forward",
+    "unet_backward", "unet_adam",
 )
 
 
@@ -105,6 +107,13 @@ def load():
                 "lbm_batch_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
                 "lbm_batch_adjoint": [vp, vp, vp, f64, vp, vp, vp, vp, vp],
                 "lbm_error_string": [C.c_int],
+                "unet_param_layout": [i32, vp, vp, vp, vp],
+                "unet_workspace_size": [vp, C.POINTER(C.c_size_t)],
+                "unet_pack_input": [vp, vp, vp, f64, vp, vp],
+                "unet_prepare_weights": [vp, vp, vp, vp],
+                "unet_forward": [vp, vp, vp, vp, vp],
+                "unet_backward": [vp, vp, vp, vp, vp, vp, vp],
+                "unet_adam": [C.c_int64, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)

@@ -1,5 +1,5 @@
 """CPU checks of the C ABI: the library builds, loads, and exports every
-entry point include/lbm.h declares; host-only calls validate arguments.
+entry point include/*.h declares; host-only calls validate arguments.
 No kernel is launched here."""
 import ctypes as C
 import os
@@ -24,7 +24,8 @@ def _declared():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             text = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:LBM_API\s+)?(?:lbm_status|const char\s*\*)\s+(lbm_\w+)\s*\(", text, re.M))
+            names |= set(re.findall(r"^\s*(?:LBM_API\s+)?(?:lbm_status|const char\s*\*)\s+((?:lbm|unet)_\w+)\s*\(",
+                                    text, re.M))
     return names
 
 
@@ -39,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_nothing_else_is_exported(lib):
     out = os.popen(f"nm -D --defined-only {B.LIB}").read()
     exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
-    assert {n for n in exported if n.startswith("lbm_")} == set(lbm.ENTRY_POINTS)
+    assert {n for n in exported if n.startswith(("lbm_", "unet_"))} == set(lbm.ENTRY_POINTS)
 
 
 @pytest.mark.parametrize("bad", [

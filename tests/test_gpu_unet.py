@@ -1,0 +1,134 @@
+"""The learned initialiser's CUDA kernels (through the C ABI) against the FP64
+oracle, training, and what the trained network gains over the zero start.
+
+Tolerances.  The GPU network stores every activation and activation gradient
+in BF16 (unit roundoff 2^-9) and accumulates every product in FP32; the oracle
+runs the same BF16-rounded weights and input in FP64, either keeping exact
+activations or rounding them to BF16 at the same storage points (the `store`
+model of the oracle).  With the storage model the two differ only where FP32
+and FP64 accumulation round a value to different BF16 neighbours; on the
+small case below no such value occurs and the agreement is 1e-6, pinned at
+1e-3.  On larger cases a few such values do occur and their one-ulp
+difference spreads through the later layers (a few thousand elements change
+by an ulp after 17 layers): measured 1.6e-3 on the output and 1.5e-2 on the
+whole gradient vector (5e-2 on the deepest tensor), bounded here by 1e-2,
+3e-2 and 0.1; against exact FP64 activations 2e-2 on the gradient vector,
+bounded by 5e-2."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import unet_oracle as U
+from paper_2310_00810_gb300 import lbm
+from paper_2310_00810_gb300 import unet as N
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_00810_gb300 import build
+
+    build.build()
+    lbm.load()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def bf16_round(a):
+    return torch.as_tensor(np.asarray(a, np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def oracle_params(net):
+    names = [n for n, _ in U.param_shapes(net.desc.base, N.IN_CHANNELS)]
+    p = {}
+    for name, t in zip(names, net.tensors()):
+        a = t.detach().cpu().numpy().astype(np.float64)
+        p[name] = bf16_round(a) if name.endswith(".w") and not name.startswith("head") else a
+    return p, names
+
+
+def gpu_case(base, H, W, B, seed=11):
+    net = N.UNet(base=base, height=H, width=W, batch=B, seed=seed)
+    r = np.random.Generator(np.random.PCG64(seed + 1))
+    with torch.no_grad():  # nonzero biases so that their gradients are exercised
+        for (o, c), s in zip(zip(net.offsets, net.counts), net.shapes()):
+            if len(s) == 1 and o != net.offsets[-2]:
+                net.params[o:o + c] = torch.as_tensor(r.normal(0, 0.05, c), dtype=torch.float32, device="cuda")
+    x = np.zeros((B, H, W, N.IN_CHANNELS), np.float32)
+    x[..., :3] = r.normal(0, 1, (B, H, W, 3))
+    xb = torch.as_tensor(x, device="cuda").to(torch.bfloat16)
+    target = r.normal(0, 1, (B, H)).astype(np.float32)
+    loss = net.loss_and_grad(xb.view(torch.int16).contiguous(), torch.as_tensor(target, device="cuda"))
+    grads = [net.grad[o:o + c].cpu().numpy() for o, c in zip(net.offsets, net.counts)]
+    return net, xb.to(torch.float64).cpu().numpy(), target.astype(np.float64), loss.item(), net.out.cpu().numpy(), grads
+
+
+def test_small_case_matches_the_bf16_storage_oracle():
+    net, x, target, loss, out, grads = gpu_case(8, 16, 32, 2)
+    p, names = oracle_params(net)
+    Lw, g, out_w = U.loss_and_grad(p, x, target, store=bf16_round)
+    assert rel(out, out_w) < 1e-4 and abs(loss - Lw) <= 1e-4 * Lw
+    for name, gg in zip(names, grads):
+        assert rel(gg, g[name].reshape(-1)) < 1e-3, name
+
+
+def test_larger_case_matches_the_oracle_within_bf16_error():
+    net, x, target, loss, out, grads = gpu_case(16, 32, 64, 3)
+    p, names = oracle_params(net)
+    gv = np.concatenate(grads)
+    Lw, g, out_w = U.loss_and_grad(p, x, target, store=bf16_round)
+    assert rel(out, out_w) < 1e-2 and abs(loss - Lw) <= 1e-2 * Lw
+    assert rel(gv, np.concatenate([g[n].reshape(-1) for n in names])) < 3e-2
+    for name, gg in zip(names, grads):
+        assert rel(gg, g[name].reshape(-1)) < 0.1, name
+    Le, ge, out_e = U.loss_and_grad(p, x, target)  # exact FP64 activations
+    assert rel(out, out_e) < 1e-2
+    assert rel(gv, np.concatenate([ge[n].reshape(-1) for n in names])) < 5e-2
+
+
+def test_adam_kernel_matches_oracle():
+    r = np.random.Generator(np.random.PCG64(13))
+    n = 1000
+    p0, g = r.normal(size=n).astype(np.float32), r.normal(size=n).astype(np.float32)
+    p, m, v = (torch.as_tensor(a, device="cuda") for a in (p0, np.zeros(n, np.float32), np.zeros(n, np.float32)))
+    gd = torch.as_tensor(g, device="cuda")
+    po, mo, vo = {"a": p0.astype(np.float64)}, {"a": np.zeros(n)}, {"a": np.zeros(n)}
+    for t in (1, 2, 3):
+        N.unet_adam(p, m, v, gd, t, 1e-2)
+        po, mo, vo = U.adam(po, {"a": g.astype(np.float64)}, mo, vo, t, 1e-2)
+    np.testing.assert_allclose(p.cpu().numpy(), po["a"], rtol=1e-5, atol=1e-6)
+
+
+def test_training_reduces_the_loss_on_a_fixed_batch():
+    net = N.UNet(base=8, height=16, width=32, batch=4, seed=14)
+    r = np.random.Generator(np.random.PCG64(15))
+    x = np.zeros((4, 16, 32, N.IN_CHANNELS), np.float32)
+    x[..., :3] = r.normal(0, 1, (4, 16, 32, 3))
+    xd = torch.as_tensor(x, device="cuda").to(torch.bfloat16).view(torch.int16).contiguous()
+    t = torch.as_tensor(r.normal(1, 0.3, (4, 16)).astype(np.float32), device="cuda")
+    first = float(net.train_step(xd, t, 1e-3).item())
+    for _ in range(60):
+        last = float(net.train_step(xd, t, 1e-3).item())
+    assert last < 0.3 * first
+
+
+def test_trained_network_beats_the_zero_start():
+    """Train on library-generated solves of small disk packings, then invert
+    held-out packings from the network's guess and from delta = 0: the guess
+    is closer than zero (relative error < 1, zero's is exactly 1) and the
+    inversion from it needs fewer gradient evaluations on average."""
+    nx, ny, steps = 64, 32, 3000
+    data = N.generate(384, 900000, nx=nx, ny=ny, steps=steps, chunk=64, r_min=3, r_max=5)
+    net = N.UNet(base=8, height=ny, width=nx, batch=32, seed=16)
+    N.train(net, data, epochs=40, lr=2e-3)
+    rows = N.evaluate(net, [910000 + i for i in range(4)], nx=nx, ny=ny, steps=steps, max_evals=300,
+                      time_limit=60.0, r_min=3, r_max=5)
+    pred = np.mean([r["prediction_rel_err"] for r in rows])
+    assert pred < 0.5
+    assert all(r["unet"]["converged"] for r in rows)
+    assert np.mean([r["unet"]["gradient_evaluations"] for r in rows]) < np.mean(
+        [r["zero"]["gradient_evaluations"] for r in rows])

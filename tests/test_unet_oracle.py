@@ -95,3 +95,19 @@ def test_param_shapes_follow_the_unet_recipe():
     assert s["enc0a.w"] == (3, 3, 8, 32) and s["enc3b.w"] == (3, 3, 256, 256)
     assert s["up2.w"] == (2, 2, 256, 128) and s["dec2a.w"] == (3, 3, 256, 128)
     assert s["dec0b.w"] == (3, 3, 32, 32) and s["head.w"] == (32,)
+
+
+def test_storage_model_identity_changes_nothing_and_rounding_is_applied():
+    """forward/backward with an explicit identity store give the same bits as
+    the default; a rounding store changes the result by about its unit."""
+    base, c_in = 2, 4
+    p = U.init_params(base, c_in, seed=7)
+    r = rng(8)
+    x = r.normal(size=(1, 8, 16, c_in))
+    t = r.normal(size=(1, 8))
+    L0, g0, o0 = U.loss_and_grad(p, x, t)
+    L1, g1, o1 = U.loss_and_grad(p, x, t, store=lambda a: a)
+    assert L0 == L1 and all(np.array_equal(g0[k], g1[k]) for k in g0)
+    r8 = lambda a: np.round(a * 256.0) / 256.0
+    L2, _, o2 = U.loss_and_grad(p, x, t, store=r8)
+    assert 0 < np.max(np.abs(o2 - o0)) < 0.1
