@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--no-c3", action="store_true", help="skip the 3D joint (head, tau) inversion leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser leg")
+    ap.add_argument("--learned-solves", type=int, default=1024, help="training solves of the learned initialiser")
+    ap.add_argument("--learned-epochs", type=int, default=15)
+    ap.add_argument("--learned-eval", type=int, default=2, help="held-out inversions (from the guess and from zero)")
     ap.add_argument("--invert-time-limit", type=float, default=180.0)
     return ap.parse_args()
 
@@ -286,6 +290,8 @@ def run_native(args):
     inversion = None if args.no_invert else time_to_target(P, args.invert_time_limit)
     batched = None if args.no_batch else batch_leg(device, args.batch_instances, rank)
     c3 = None if args.no_c3 else c3_leg(device, args.invert_time_limit)
+    learned = None if args.no_learned else learned_init_leg(device, args.learned_solves, args.learned_epochs,
+                                                            args.learned_eval, args.invert_time_limit / 2)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -316,6 +322,7 @@ def run_native(args):
             "time_to_1e-3": inversion,
             "batched": batched,
             "joint_inversion_3d": c3,
+            "learned_initialiser": learned,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -392,6 +399,63 @@ def c3_leg(device, time_limit):
     del s, inv
     torch.cuda.empty_cache()
     return out
+
+
+def unet_flops_per_sample(base, H, W):
+    """Multiply-add FLOPs (2 per MAC) of one forward pass of the U-Net."""
+    c = [base << l for l in range(4)]
+    f, prev = 0, 8
+    for l in range(4):
+        px = (H >> l) * (W >> l)
+        f += 2 * px * 9 * (prev * c[l] + c[l] * c[l])
+        prev = c[l]
+    for l in (2, 1, 0):
+        px = (H >> l) * (W >> l)
+        f += 2 * px * c[l + 1] * c[l]  # transposed convolution: one tap per output pixel
+        f += 2 * px * 9 * (2 * c[l] * c[l] + c[l] * c[l])
+    return f + 2 * H * W * c[0]
+
+
+def learned_init_leg(device, n_train, epochs, n_eval, time_limit):
+    """The learned initialiser at 256x128: generate training solves with the
+    library (batched forward, T = 10000, disks r 6-12, porosity U[0.5, 0.7],
+    4-mode sine profiles), train the U-Net (base 32, BF16 kernels), then invert
+    held-out packings by L-BFGS from the network's guess and from delta = 0."""
+    import torch
+
+    from paper_2310_00810_gb300 import unet as N
+
+    nx, ny, T, base, batch = 256, 128, 10000, 32, 16
+    t0 = time.perf_counter()
+    data = N.generate(n_train, 5000, nx=nx, ny=ny, steps=T, chunk=64, device=device)
+    torch.cuda.synchronize(device)
+    t_gen = time.perf_counter() - t0
+    net = N.UNet(base=base, height=ny, width=nx, batch=batch, seed=5)
+    N.train(net, data, epochs=1, lr=1e-3)  # warm-up epoch (first launches, allocations)
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    hist = N.train(net, data, epochs=epochs, lr=1e-3, seed=1)
+    torch.cuda.synchronize(device)
+    t_train = time.perf_counter() - t0
+    samples = epochs * (n_train // batch) * batch
+    flops = 3 * unet_flops_per_sample(base, ny, nx) * samples  # forward + two backward products
+    rows = N.evaluate(net, [5000 + 20000 + i for i in range(n_eval)], nx=nx, ny=ny, steps=T, max_evals=600,
+                      time_limit=time_limit)
+    mean = lambda key, f: float(np.mean([f(r[key]) for r in rows]))
+    return {"workload": f"U-Net base {base}, input 2 velocity channels + mask at {nx}x{ny}, BF16 weights/activations, "
+                        f"FP32 accumulation (mma.sync tensor cores); {n_train} training solves (D2Q9 FP32, T={T}, "
+                        f"disks r 6-12, porosity U[0.5, 0.7], seeds 5000+j), {epochs} epochs, held-out seeds 25000+i",
+            "generation_s": round(t_gen, 2), "solves_per_s": round(n_train / t_gen, 2),
+            "train_s": round(t_train, 2), "train_samples_per_s": round(samples / t_train, 1),
+            "train_tflops": round(flops / t_train / 1e12, 2), "final_train_loss": hist[-1],
+            "prediction_rel_err": float(np.mean([r["prediction_rel_err"] for r in rows])),
+            "lbfgs_from_unet": {"gradient_evaluations": mean("unet", lambda r: r["gradient_evaluations"]),
+                                "seconds": mean("unet", lambda r: r["seconds"]),
+                                "converged": all(r["unet"]["converged"] for r in rows)},
+            "lbfgs_from_zero": {"gradient_evaluations": mean("zero", lambda r: r["gradient_evaluations"]),
+                                "seconds": mean("zero", lambda r: r["seconds"]),
+                                "converged": all(r["zero"]["converged"] for r in rows)},
+            "held_out": rows}
 
 
 def batch_leg(device, count, rank, steps=2):
