@@ -58,35 +58,66 @@ __device__ __forceinline__ Pix pix_of(long long m, int H, int W)
 }
 
 // ---------------------------------------------------------------- loaders
-// Each fills a ROWS x BK tile (row index = m or n, k contiguous) with zeros
-// outside [0, rows) x [k0, kend).
+// Each stages a ROWS x BK operand tile (row index = m or n, k contiguous) in
+// three steps: prepare(r0) once per CTA (the per-thread row coordinates,
+// fixed along k), fetch(k0, kend) global -> registers (zeros outside
+// [0, R) x [k0, kend)), put(S) registers -> shared memory.  fetch of the next
+// tile is issued before the MMAs of the current one.  Pixel counts stay below
+// 2^31, so index arithmetic is 32-bit except the final address.
+
+template <int ROWS>
+struct Items {
+    static constexpr int N = ROWS * (BK / 8) / kGemmThreads;  // 16-byte items per thread
+};
 
 // Rows of an activation batch gathered through a tap (3x3 with zero padding,
 // or 1 tap): row = pixel, k = tap * C + c.
+template <int ROWS>
 struct LdIm2col {
     const bf16* x;
     int H, W, C, ld, off, taps;
+    static constexpr int NI = Items<ROWS>::N;
+    int y[NI], xw[NI];
+    size_t base[NI];
+    bool ok[NI];
+    uint4 v[NI];
     __device__ void set_phase(int) {}
-    template <int ROWS>
-    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    __device__ void prepare(long long r0, long long R)
     {
-        for (int e = threadIdx.x; e < ROWS * (BK / 8); e += kGemmThreads) {
-            const int r = e / (BK / 8), j = e % (BK / 8);
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads, r = e >> 2;
             const long long m = r0 + r;
+            ok[i] = m < R;
+            const int mi = ok[i] ? (int)m : 0;
+            xw[i] = mi % W;
+            const int t = mi / W;
+            y[i] = t % H;
+            base[i] = ((size_t)(t / H) * H * W + (size_t)y[i] * W + xw[i]) * ld + off;
+        }
+    }
+    __device__ void fetch(int k0, int kend)
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads, j = e & 3;
             const int k = k0 + 8 * j;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m < R && k < kend) {
+            v[i] = make_uint4(0, 0, 0, 0);
+            if (ok[i] && k < kend) {
                 const int tap = k / C, ci = k - tap * C;
-                const Pix p = pix_of(m, H, W);
-                int yy = p.y, xx = p.x;
-                if (taps == 9) {
-                    yy += tap / 3 - 1;
-                    xx += tap % 3 - 1;
-                }
+                const int dy = taps == 9 ? tap / 3 - 1 : 0, dx = taps == 9 ? tap % 3 - 1 : 0;
+                const int yy = y[i] + dy, xx = xw[i] + dx;
                 if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    v = *reinterpret_cast<const uint4*>(x + ((size_t)((long long)p.b * H + yy) * W + xx) * ld + off + ci);
+                    v[i] = *reinterpret_cast<const uint4*>(x + base[i] + (long long)(dy * W + dx) * ld + ci);
             }
-            *reinterpret_cast<uint4*>(&S[r][8 * j]) = v;
+        }
+    }
+    __device__ void put(bf16 (*S)[LDS]) const
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads;
+            *reinterpret_cast<uint4*>(&S[e >> 2][8 * (e & 3)]) = v[i];
         }
     }
 };
@@ -94,87 +125,146 @@ struct LdIm2col {
 // The gradient of a 2x2 stride-2 transposed convolution's output, gathered
 // onto its input pixels: row = input pixel (b, y, x) of an H x W image,
 // k = phase * C + c, value dY[b][2y + dy][2x + dx][c].
+template <int ROWS>
 struct LdUpGather {
     const bf16* g;
     int H, W, C, ld, off;
+    static constexpr int NI = Items<ROWS>::N;
+    size_t base[NI];
+    bool ok[NI];
+    uint4 v[NI];
     __device__ void set_phase(int) {}
-    template <int ROWS>
-    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    __device__ void prepare(long long r0, long long R)
     {
-        for (int e = threadIdx.x; e < ROWS * (BK / 8); e += kGemmThreads) {
-            const int r = e / (BK / 8), j = e % (BK / 8);
-            const long long m = r0 + r;
-            const int k = k0 + 8 * j;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m < R && k < kend) {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads;
+            const long long m = r0 + (e >> 2);
+            ok[i] = m < R;
+            const int mi = ok[i] ? (int)m : 0;
+            const int x = mi % W, t = mi / W, y = t % H, b = t / H;
+            base[i] = (((size_t)b * 2 * H + 2 * y) * (2 * W) + 2 * x) * ld + off;
+        }
+    }
+    __device__ void fetch(int k0, int kend)
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads, k = k0 + 8 * (e & 3);
+            v[i] = make_uint4(0, 0, 0, 0);
+            if (ok[i] && k < kend) {
                 const int ph = k / C, c = k - ph * C;
-                const Pix p = pix_of(m, H, W);
-                const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
-                v = *reinterpret_cast<const uint4*>(g + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + c);
+                v[i] = *reinterpret_cast<const uint4*>(g + base[i] + (long long)((ph >> 1) * 2 * W + (ph & 1)) * ld + c);
             }
-            *reinterpret_cast<uint4*>(&S[r][8 * j]) = v;
+        }
+    }
+    __device__ void put(bf16 (*S)[LDS]) const
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads;
+            *reinterpret_cast<uint4*>(&S[e >> 2][8 * (e & 3)]) = v[i];
         }
     }
 };
 
 // Weight rows: S[r][k] = w[row * ld + k] (+ phase * phase_stride).
+template <int ROWS>
 struct LdRows {
     const bf16* w;
     int ld;
     long long phase_stride;
+    static constexpr int NI = Items<ROWS>::N;
+    size_t base[NI];
+    bool ok[NI];
+    uint4 v[NI];
     __device__ void set_phase(int ph) { w += ph * phase_stride; }
-    template <int ROWS>
-    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    __device__ void prepare(long long r0, long long R)
     {
-        for (int e = threadIdx.x; e < ROWS * (BK / 8); e += kGemmThreads) {
-            const int r = e / (BK / 8), j = e % (BK / 8);
-            const long long n = r0 + r;
-            const int k = k0 + 8 * j;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (n < R && k < kend) v = *reinterpret_cast<const uint4*>(w + (size_t)n * ld + k);
-            *reinterpret_cast<uint4*>(&S[r][8 * j]) = v;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const long long n = r0 + ((threadIdx.x + i * kGemmThreads) >> 2);
+            ok[i] = n < R;
+            base[i] = ok[i] ? (size_t)n * ld : 0;
+        }
+    }
+    __device__ void fetch(int k0, int kend)
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int k = k0 + 8 * ((threadIdx.x + i * kGemmThreads) & 3);
+            v[i] = ok[i] && k < kend ? *reinterpret_cast<const uint4*>(w + base[i] + k) : make_uint4(0, 0, 0, 0);
+        }
+    }
+    __device__ void put(bf16 (*S)[LDS]) const
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads;
+            *reinterpret_cast<uint4*>(&S[e >> 2][8 * (e & 3)]) = v[i];
         }
     }
 };
 
 // Transposed gather for weight gradients: row = (tap, c) with tap in
-// [0, taps), k = pixel; value X[pixel + tap][c] (zero padding).  With
-// up_phase >= 0 the pixel is an input pixel of a transposed convolution and
-// the value comes from its output pixel (2y + dy, 2x + dx) of a 2H x 2W image.
+// [0, taps), k = pixel; value X[pixel + tap][c] (zero padding).  With up = 1
+// the pixel is an input pixel of a transposed convolution and the value comes
+// from its output pixel (2y + dy, 2x + dx) of the 2H x 2W image (phase from
+// set_phase).
+template <int ROWS>
 struct LdGatherT {
     const bf16* x;
     int H, W, C, ld, off, taps;
-    int up;  // 1: phase-mapped output pixels (set_phase)
+    int up;
     int ph;
+    static constexpr int CH = ROWS / 8;                     // 8-row chunks per k
+    static constexpr int NI = BK * CH / kGemmThreads;       // items per thread
+    int dy[NI], dx[NI], c[NI];
+    bool ok[NI];
+    uint4 v[NI];
     __device__ void set_phase(int p) { ph = p; }
-    template <int ROWS>
-    __device__ void load(bf16 (*S)[LDS], long long r0, int k0, int kend, long long R) const
+    __device__ void prepare(long long r0, long long R)
     {
-        constexpr int CH = ROWS / 8;  // 8-row chunks per k
-        for (int e = threadIdx.x; e < BK * CH; e += kGemmThreads) {
-            const int kk = e / CH, jc = e % CH;
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads, jc = e % CH;
             const long long m = r0 + 8 * jc;
+            ok[i] = m < R;
+            const int mi = ok[i] ? (int)m : 0;
+            const int tap = mi / C;
+            c[i] = mi - tap * C;
+            dy[i] = up ? ph >> 1 : (taps == 9 ? tap / 3 - 1 : 0);
+            dx[i] = up ? ph & 1 : (taps == 9 ? tap % 3 - 1 : 0);
+        }
+    }
+    __device__ void fetch(int k0, int kend)
+    {
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads, kk = e / CH;
             const int k = k0 + kk;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m < R && k < kend) {
-                const int tap = (int)(m / C), c = (int)(m - (long long)tap * C);
-                const Pix p = pix_of(k, H, W);
+            v[i] = make_uint4(0, 0, 0, 0);
+            if (ok[i] && k < kend) {
+                const int xw = k % W, t = k / W, y = t % H, b = t / H;
                 if (up) {
-                    const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
-                    v = *reinterpret_cast<const uint4*>(x + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + c);
+                    const size_t a = (((size_t)b * 2 * H + 2 * y + dy[i]) * (2 * W) + 2 * xw + dx[i]) * ld + off + c[i];
+                    v[i] = *reinterpret_cast<const uint4*>(x + a);
                 } else {
-                    int yy = p.y, xx = p.x;
-                    if (taps == 9) {
-                        yy += tap / 3 - 1;
-                        xx += tap % 3 - 1;
-                    }
+                    const int yy = y + dy[i], xx = xw + dx[i];
                     if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                        v = *reinterpret_cast<const uint4*>(x + ((size_t)((long long)p.b * H + yy) * W + xx) * ld + off + c);
+                        v[i] = *reinterpret_cast<const uint4*>(x + (((size_t)b * H + yy) * W + xx) * ld + off + c[i]);
                 }
             }
-            const bf16* pv = reinterpret_cast<const bf16*>(&v);
+        }
+    }
+    __device__ void put(bf16 (*S)[LDS]) const
+    {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) S[8 * jc + i][kk] = pv[i];
+        for (int i = 0; i < NI; ++i) {
+            const int e = threadIdx.x + i * kGemmThreads, kk = e / CH, jc = e % CH;
+            const bf16* pv = reinterpret_cast<const bf16*>(&v[i]);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) S[8 * jc + q][kk] = pv[q];
         }
     }
 };
@@ -212,7 +302,8 @@ struct EpUp {
     __device__ void set_phase(int p) { ph = p; }
     __device__ void store(long long m, int n, float v0, float v1) const
     {
-        const Pix p = pix_of(m, H, W);
+        const int mi = (int)m, x = mi % W, t = mi / W;
+        const Pix p{t / H, t % H, x};
         const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
         v0 += bias[n];
         v1 += bias[n + 1];
@@ -261,10 +352,20 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(LA la, LB lb, EP ep, long
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
+    la.prepare(m0, M);
+    lb.prepare(n0, N);
+    if (kbeg < kend) {
+        la.fetch(kbeg, kend);
+        lb.fetch(kbeg, kend);
+    }
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        la.template load<BM>(As, m0, k0, kend, M);
-        lb.template load<BN>(Bs, n0, k0, kend, N);
+        la.put(As);
+        lb.put(Bs);
         __syncthreads();
+        if (k0 + BK < kend) {  // the next tile's loads, in flight during these MMAs
+            la.fetch(k0 + BK, kend);
+            lb.fetch(k0 + BK, kend);
+        }
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t a[2][4], b[4][2];
@@ -314,15 +415,24 @@ __global__ void k_sum_partials(const float* __restrict__ part, long long count, 
 }
 
 // Column sums of g[P][C] (row stride ld, channel offset off) over a range of
-// rows per block: part[block][c].
-__global__ void k_colsum(const bf16* __restrict__ g, long long P, int C, int ld, int off, long long rows,
-                         float* __restrict__ part)
+// rows per block: part[block][c].  The block's threads cover 256 / C rows at
+// a time (C <= 256, a power-of-two multiple of 8 or not: threads beyond
+// (256 / C) * C idle), then add their row groups in shared memory.
+__global__ void __launch_bounds__(256) k_colsum(const bf16* __restrict__ g, long long P, int C, int ld, int off,
+                                                long long rows, float* __restrict__ part)
 {
+    __shared__ float red[256];
     const long long r0 = (long long)blockIdx.x * rows, r1 = min(P, r0 + rows);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.0f;
-        for (long long r = r0; r < r1; ++r) s += __bfloat162float(g[r * ld + off + c]);
-        part[(long long)blockIdx.x * C + c] = s;
+    const int groups = max(1, 256 / C), c = threadIdx.x % C, gi = threadIdx.x / C;
+    float s = 0.0f;
+    if (gi < groups)
+        for (long long r = r0 + gi; r < r1; r += groups) s += __bfloat162float(g[r * ld + off + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int q = 0; q < groups; ++q) t += red[q * C + threadIdx.x];
+        part[(long long)blockIdx.x * C + threadIdx.x] = t;
     }
 }
 
@@ -553,8 +663,8 @@ std::vector<Tensor> param_tensors(int base, std::vector<int>* taps_out = nullptr
     return t;
 }
 
-constexpr int kMaxSplits = 16;
-constexpr long long kSplitPixels = 8192;
+constexpr int kMaxSplits = 256;
+constexpr long long kTargetCtas = 608;  // weight-gradient CTAs aimed for (4 per SM)
 
 struct Layout {
     int B, H, W, c[4];
@@ -633,11 +743,12 @@ bool make_layout(const unet_desc* d, Layout* L)
     o += al256(sizeof(float) * (size_t)l.B * l.H);
     l.loss_tmp = o;
     o += 256;
-    // partials: weight gradients (splits x taps Cin Cout), column sums (blocks x C), head (rows x c0)
+    // partials: weight gradients (splits x (phases) x M x N: at most (kTargetCtas + tiles) x BM x BN, or the
+    // largest product at 16 k-tiles per split), column sums (blocks x C), head (rows x c0)
+    max_part = (kTargetCtas + 1) * BM * BN * 2;
     for (int i = 0; i < 4; ++i) {
-        const long long s = std::min<long long>(kMaxSplits, (l.P[i] + kSplitPixels - 1) / kSplitPixels);
         const long long cmax = 2LL * l.c[std::min(i + 1, 3)];
-        max_part = std::max(max_part, s * 9 * cmax * cmax);
+        max_part = std::max(max_part, 4 * 9 * cmax * cmax);
         max_part = std::max(max_part, 256LL * cmax);
     }
     max_part = std::max(max_part, (long long)l.B * l.H * l.c[0]);
@@ -677,13 +788,21 @@ void conv_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
               int Cout)
 {
     const long long P = (long long)C.L.B * H * W;
-    LdIm2col la{x, H, W, Cin, ld, off, 9};
-    LdRows lb{C.wf(layer), 9 * Cin, 0};
+    LdIm2col<BM> la{x, H, W, Cin, ld, off, 9};
+    LdRows<BN> lb{C.wf(layer), 9 * Cin, 0};
     EpAct ep{y, Cout, 0, C.pw(wtensor + 1), 1};
     gemm(C.s, la, lb, ep, P, Cout, 9 * Cin, 1, 1);
 }
 
-int splits_for(long long P) { return (int)std::min<long long>(kMaxSplits, (P + kSplitPixels - 1) / kSplitPixels); }
+// Split-K count of a weight-gradient product (M x N output, K pixels): enough
+// CTAs to fill the GPU (about 4 per SM), at least 16 k-tiles per split.
+int splits_for(long long M, long long N, long long K)
+{
+    const long long tiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    const long long want = (kTargetCtas + tiles - 1) / tiles;
+    const long long most = std::max(1LL, K / (16 * BK));
+    return (int)std::max(1LL, std::min(want, std::min(most, (long long)kMaxSplits)));
+}
 
 // Weight and bias gradients of a 3x3 convolution with input x (ld/off) and
 // pre-activation gradient g (contiguous [P][Cout]); dx into dxo (contiguous
@@ -694,10 +813,10 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
     const long long P = (long long)C.L.B * H * W;
     float* part = at<float>(C.ws, C.L.part);
     // dW[(tap, ci)][co] = sum_p x[p + tap][ci] g[p][co]
-    const int sp = splits_for(P);
-    LdGatherT la{x, H, W, Cin, ld, off, 9, 0, 0};
-    LdGatherT lb{g, H, W, Cout, Cout, 0, 1, 0, 0};
     const long long Mw = 9LL * Cin;
+    const int sp = splits_for(Mw, Cout, P);
+    LdGatherT<BM> la{x, H, W, Cin, ld, off, 9, 0, 0};
+    LdGatherT<BN> lb{g, H, W, Cout, Cout, 0, 1, 0, 0};
     EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
     gemm(C.s, la, lb, ep, Mw, Cout, (int)P, sp, 1);
     k_sum_partials<<<ew_grid(Mw * Cout), 256, 0, C.s>>>(part, Mw * Cout, sp, Mw * Cout, grad + C.t[wtensor].off);
@@ -707,8 +826,8 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
     k_colsum<<<nb, 256, 0, C.s>>>(g, P, Cout, Cout, 0, rows, part);
     k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
     if (dxo) {
-        LdIm2col la2{g, H, W, Cout, Cout, 0, 9};
-        LdRows lb2{C.wb(layer), 9 * Cout, 0};
+        LdIm2col<BM> la2{g, H, W, Cout, Cout, 0, 9};
+        LdRows<BN> lb2{C.wb(layer), 9 * Cout, 0};
         EpAct ep2{dxo, Cin, 0, nullptr, 0};
         gemm(C.s, la2, lb2, ep2, P, Cin, 9 * Cout, 1, 1);
     }
@@ -719,8 +838,8 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
 void up_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws, int Cin, bf16* y, int Cout, int ld)
 {
     const long long P = (long long)C.L.B * Hs * Ws;
-    LdIm2col la{x, Hs, Ws, Cin, Cin, 0, 1};
-    LdRows lb{C.wf(layer), Cin, (long long)Cout * Cin};
+    LdIm2col<BM> la{x, Hs, Ws, Cin, Cin, 0, 1};
+    LdRows<BN> lb{C.wf(layer), Cin, (long long)Cout * Cin};
     EpUp ep{y, Hs, Ws, ld, 0, C.pw(wtensor + 1), 0};
     gemm(C.s, la, lb, ep, P, Cout, Cin, 1, 4);
 }
@@ -732,10 +851,10 @@ void up_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws,
 {
     const long long P = (long long)C.L.B * Hs * Ws;
     float* part = at<float>(C.ws, C.L.part);
-    const int sp = splits_for(P);
+    const int sp = std::max(1, splits_for(Cin, Cout, P) / 4);  // the four phases multiply the CTAs
     // dW[phase][ci][co] = sum_p x[p][ci] gy[up(p, phase)][co]
-    LdGatherT la{x, Hs, Ws, Cin, Cin, 0, 1, 0, 0};
-    LdGatherT lb{gy, Hs, Ws, Cout, ld, 0, 1, 1, 0};
+    LdGatherT<BM> la{x, Hs, Ws, Cin, Cin, 0, 1, 0, 0};
+    LdGatherT<BN> lb{gy, Hs, Ws, Cout, ld, 0, 1, 1, 0};
     EpPartial ep{part, Cout, 4LL * Cin * Cout, (long long)Cin * Cout, 0, 0};
     gemm(C.s, la, lb, ep, Cin, Cout, (int)P, sp, 4);
     k_sum_partials<<<ew_grid(4LL * Cin * Cout), 256, 0, C.s>>>(part, 4LL * Cin * Cout, sp, 4LL * Cin * Cout,
@@ -747,8 +866,8 @@ void up_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws,
     k_colsum<<<nb, 256, 0, C.s>>>(gy, Po, Cout, ld, 0, rows, part);
     k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
     // dx[p][ci] = sum_(phase, co) gy[up(p, phase)][co] W[phase][ci][co]
-    LdUpGather la2{gy, Hs, Ws, Cout, ld, 0};
-    LdRows lb2{C.wb(layer), 4 * Cout, 0};
+    LdUpGather<BM> la2{gy, Hs, Ws, Cout, ld, 0};
+    LdRows<BN> lb2{C.wb(layer), 4 * Cout, 0};
     EpAct ep2{dxo, Cin, 0, nullptr, 0};
     gemm(C.s, la2, lb2, ep2, P, Cin, 4 * Cout, 1, 1);
 }
