@@ -43,19 +43,29 @@ __device__ __forceinline__ void mma16816(float (&c)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// Pixel index m of an image batch [b][h][w] -> (b, y, x).
+// Four 8x8 b16 matrices from shared memory, transposed: thread t receives,
+// of matrix q (row addresses from threads 8q..8q+7), the elements
+// (row 2 (t % 4), column t / 4) and (row 2 (t % 4) + 1, column t / 4).
+__device__ __forceinline__ void ldmatrix_x4_trans(uint32_t (&r)[4], const void* row_addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(row_addr)));
+}
+
+// The same without transposition: thread t receives, of matrix q, the
+// elements (row t / 4, columns 2 (t % 4) and 2 (t % 4) + 1).
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* row_addr)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(row_addr)));
+}
+
+// Pixel (b, y, x) of an image batch [b][h][w].
 struct Pix {
     int b, y, x;
 };
-__device__ __forceinline__ Pix pix_of(long long m, int H, int W)
-{
-    Pix p;
-    p.x = (int)(m % W);
-    const long long t = m / W;
-    p.y = (int)(t % H);
-    p.b = (int)(t / H);
-    return p;
-}
 
 // ---------------------------------------------------------------- loaders
 // Each stages a ROWS x BK operand tile (row index = m or n, k contiguous) in
@@ -74,6 +84,7 @@ struct Items {
 // or 1 tap): row = pixel, k = tap * C + c.
 template <int ROWS>
 struct LdIm2col {
+    static constexpr bool KMAJOR = false;  // shared tile [row][k]
     const bf16* x;
     int H, W, C, ld, off, taps;
     static constexpr int NI = Items<ROWS>::N;
@@ -127,6 +138,7 @@ struct LdIm2col {
 // k = phase * C + c, value dY[b][2y + dy][2x + dx][c].
 template <int ROWS>
 struct LdUpGather {
+    static constexpr bool KMAJOR = false;  // shared tile [row][k]
     const bf16* g;
     int H, W, C, ld, off;
     static constexpr int NI = Items<ROWS>::N;
@@ -171,6 +183,7 @@ struct LdUpGather {
 // Weight rows: S[r][k] = w[row * ld + k] (+ phase * phase_stride).
 template <int ROWS>
 struct LdRows {
+    static constexpr bool KMAJOR = false;  // shared tile [row][k]
     const bf16* w;
     int ld;
     long long phase_stride;
@@ -213,6 +226,7 @@ struct LdRows {
 // set_phase).
 template <int ROWS>
 struct LdGatherT {
+    static constexpr bool KMAJOR = true;  // shared tile [k][row]: fragments through ldmatrix.trans
     const bf16* x;
     int H, W, C, ld, off, taps;
     int up;
@@ -257,14 +271,12 @@ struct LdGatherT {
             }
         }
     }
-    __device__ void put(bf16 (*S)[LDS]) const
+    __device__ void put(bf16 (*S)[ROWS + 8]) const
     {
 #pragma unroll
         for (int i = 0; i < NI; ++i) {
             const int e = threadIdx.x + i * kGemmThreads, kk = e / CH, jc = e % CH;
-            const bf16* pv = reinterpret_cast<const bf16*>(&v[i]);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) S[8 * jc + q][kk] = pv[q];
+            *reinterpret_cast<uint4*>(&S[kk][8 * jc]) = v[i];
         }
     }
 };
@@ -333,8 +345,14 @@ template <class LA, class LB, class EP>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm(LA la, LB lb, EP ep, long long M, int N, int K, int k_split,
                                                        int splits)
 {
-    __shared__ __align__(16) bf16 As[BM][LDS];
-    __shared__ __align__(16) bf16 Bs[BN][LDS];
+    // operand tiles: [row][k] (k contiguous), or [k][row] for k-major loaders
+    constexpr int A_BYTES = (LA::KMAJOR ? BK * (BM + 8) : BM * LDS) * 2;
+    constexpr int B_BYTES = (LB::KMAJOR ? BK * (BN + 8) : BN * LDS) * 2;
+    __shared__ __align__(16) unsigned char sm[A_BYTES + B_BYTES];
+    auto As = reinterpret_cast<bf16(*)[LDS]>(sm);
+    auto AsT = reinterpret_cast<bf16(*)[BM + 8]>(sm);
+    auto Bs = reinterpret_cast<bf16(*)[LDS]>(sm + A_BYTES);
+    auto BsT = reinterpret_cast<bf16(*)[BN + 8]>(sm + A_BYTES);
     const int split = blockIdx.z % splits, ph = blockIdx.z / splits;
     la.set_phase(ph);
     lb.set_phase(ph);
@@ -359,8 +377,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(LA la, LB lb, EP ep, long
         lb.fetch(kbeg, kend);
     }
     for (int k0 = kbeg; k0 < kend; k0 += BK) {
-        la.put(As);
-        lb.put(Bs);
+        if constexpr (LA::KMAJOR) la.put(AsT);
+        else la.put(As);
+        if constexpr (LB::KMAJOR) lb.put(BsT);
+        else lb.put(Bs);
         __syncthreads();
         if (k0 + BK < kend) {  // the next tile's loads, in flight during these MMAs
             la.fetch(k0 + BK, kend);
@@ -369,19 +389,40 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(LA la, LB lb, EP ep, long
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 16) {
             uint32_t a[2][4], b[4][2];
+            const int q = lane >> 3, rr = lane & 7;  // ldmatrix: matrix q, row rr
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const int r = wm * 32 + i * 16 + g;
-                a[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t]);
-                a[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t]);
-                a[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * t + 8]);
-                a[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * t + 8]);
+                if constexpr (LA::KMAJOR) {
+                    // matrices (k 0-7, m 0-7), (k 0-7, m 8-15), (k 8-15, m 0-7), (k 8-15, m 8-15)
+                    ldmatrix_x4_trans(a[i], &AsT[kk + (q & 2) * 4 + rr][wm * 32 + i * 16 + (q & 1) * 8]);
+                } else {
+                    // matrices (m 0-7, k 0-7), (m 8-15, k 0-7), (m 0-7, k 8-15), (m 8-15, k 8-15)
+                    (void)r;
+                    ldmatrix_x4(a[i], &As[wm * 32 + i * 16 + (q & 1) * 8 + rr][kk + (q & 2) * 4]);
+                }
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const int c = wn * 32 + j * 8 + g;
-                b[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t]);
-                b[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * t + 8]);
+                if constexpr (LB::KMAJOR) {
+                    if (j % 2 == 0) {
+                        // matrices (k 0-7, n 0-7), (k 8-15, n 0-7), (k 0-7, n 8-15), (k 8-15, n 8-15)
+                        uint32_t r4[4];
+                        ldmatrix_x4_trans(r4, &BsT[kk + (q & 1) * 8 + rr][wn * 32 + j * 8 + (q & 2) * 4]);
+                        b[j][0] = r4[0];
+                        b[j][1] = r4[1];
+                        b[j + 1][0] = r4[2];
+                        b[j + 1][1] = r4[3];
+                    }
+                } else if (j % 2 == 0) {
+                    // matrices (n 0-7, k 0-7), (n 0-7, k 8-15), (n 8-15, k 0-7), (n 8-15, k 8-15)
+                    uint32_t r4[4];
+                    ldmatrix_x4(r4, &Bs[wn * 32 + j * 8 + (q & 2) * 4 + rr][kk + (q & 1) * 8]);
+                    b[j][0] = r4[0];
+                    b[j][1] = r4[1];
+                    b[j + 1][0] = r4[2];
+                    b[j + 1][1] = r4[3];
+                }
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
