@@ -118,6 +118,7 @@ typedef struct lbm_kernel_choice {
     int32_t persist;         /* 1: one cooperative launch per sweep (lattices up to 24 MB of state) */
     int32_t overlap;         /* 1: the reverse sweep recomputes segment s - 1 on a second stream while
                                 the adjoint steps of segment s run (two segment buffers) */
+    int32_t adjoint_tma_rows; /* tile height of the D2Q9 TMA adjoint kernels: 4 or 8 (0: as tma_rows) */
 } lbm_kernel_choice;
 
 /* Sets / reads the plan's kernel choice (an autotuner's knob).  Cached CUDA

@@ -133,10 +133,8 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
     _, sfam, svec, srows = best_step
     best, best_t = None, float("inf")
     for name, fam, vec, rows in step_candidates(tq):
-        choice = dict(step_family=sfam, adjoint_family=fam, vec=vec if fam != sfam else svec,
-                      tma_rows=rows if fam == lbm.LBM_FAMILY_TMA else srows, pdl=1, persist=0)
-        if fam == lbm.LBM_FAMILY_TMA and sfam == lbm.LBM_FAMILY_TMA and rows != srows:
-            continue  # one tile height per plan
+        choice = dict(step_family=sfam, adjoint_family=fam, vec=vec if fam != sfam else svec, tma_rows=srows,
+                      pdl=1, persist=0, adjoint_tma_rows=rows if fam == lbm.LBM_FAMILY_TMA else 0)
         t = time_sweeps(choice)
         timings[f"sweep:step={best_step[0]},adjoint={name}"] = round(t * 1e6, 3)
         if t < best_t:

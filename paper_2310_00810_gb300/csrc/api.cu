@@ -299,6 +299,7 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     // the wait give up on purpose and check that LBM_ERR_TIMEOUT comes back)
     const char* ty = std::getenv("LBM_TMA_ROWS");
     I.tma_ty = ty && std::atoi(ty) == 4 ? 4 : 8;
+    I.adj_tma_ty = I.tma_ty;
     I.step_family = LBM_FAMILY_AUTO;
     I.adj_family = LBM_FAMILY_AUTO;
     const char* sl = std::getenv("LBM_SPIN_LIMIT");
@@ -319,7 +320,8 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     auto fam_ok = [](int f) { return f >= LBM_FAMILY_AUTO && f <= LBM_FAMILY_TMA; };
     if (!fam_ok(k->step_family) || !fam_ok(k->adjoint_family) || (k->vec != 2 && k->vec != 4) ||
         (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1) ||
-        (k->overlap != 0 && k->overlap != 1))
+        (k->overlap != 0 && k->overlap != 1) ||
+        (k->adjoint_tma_rows != 0 && k->adjoint_tma_rows != 4 && k->adjoint_tma_rows != 8))
         return LBM_ERR_INVALID_ARG;
     PlanInfo& I = p->info;
     I.step_family = k->step_family;
@@ -328,6 +330,7 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     I.use_tma = 1;
     I.tma_min_tiles = 1;
     I.tma_ty = k->tma_rows;
+    I.adj_tma_ty = k->adjoint_tma_rows ? k->adjoint_tma_rows : k->tma_rows;
     I.pdl = k->pdl;
     I.use_persist = k->persist;
     I.overlap = k->overlap;
@@ -343,6 +346,7 @@ lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
     k->adjoint_family = I.adj_family;
     k->vec = I.max_vec >= 4 ? 4 : 2;
     k->tma_rows = I.tma_ty;
+    k->adjoint_tma_rows = I.adj_tma_ty;
     k->pdl = I.pdl;
     k->persist = I.use_persist;
     k->overlap = I.overlap;

@@ -67,7 +67,8 @@ struct PlanInfo {
     int use_tma;      // 1: TMA-staged FP32 step/adjoint kernels where alignment allows
     int step_variant; // register stream-collide kernel: 0 link-dependent loads, 1 all loads up front
     int tma_variant;  // D2Q9 TMA stream-collide: 0 per-direction shifted boxes, 1 halo boxes + TMA link words
-    int tma_ty;       // D2Q9 halo TMA tile height: 8 or 4 rows
+    int tma_ty;       // D2Q9 halo TMA tile height of the stream-collide kernels: 8 or 4 rows
+    int adj_tma_ty;   // the same for the adjoint kernels
     int step_family;  // LBM_FAMILY_* of the stream-collide kernels
     int adj_family;   // LBM_FAMILY_* of the adjoint kernels
     int pdl;          // 1: launch the sweep kernels with programmatic dependent launch

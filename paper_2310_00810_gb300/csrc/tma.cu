@@ -817,8 +817,8 @@ bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void
 {
     if (!tma_ok(p, gprev, lam_in, lam_out)) return false;
     if (p.q == 9 && p.tma_variant == 1) {
-        const bool one = halo_tiles(p, p.tma_ty) <= sm_count();
-        if (p.tma_ty == 4)
+        const bool one = halo_tiles(p, p.adj_tma_ty) <= sm_count();
+        if (p.adj_tma_ty == 4)
             return one ? adjoint_tma_halo<HaloAdj2D4x1>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
                        : adjoint_tma_halo<HaloAdj2D4>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
         return one ? adjoint_tma_halo<HaloAdj2D8x1>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
