@@ -61,9 +61,9 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--no-c3", action="store_true", help="skip the 3D joint (head, tau) inversion leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser leg")
-    ap.add_argument("--learned-solves", type=int, default=1024, help="training solves of the learned initialiser")
-    ap.add_argument("--learned-epochs", type=int, default=15)
-    ap.add_argument("--learned-eval", type=int, default=2, help="held-out inversions (from the guess and from zero)")
+    ap.add_argument("--learned-solves", type=int, default=2048, help="training solves of the learned initialiser")
+    ap.add_argument("--learned-epochs", type=int, default=25)
+    ap.add_argument("--learned-eval", type=int, default=3, help="held-out inversions (from the guess and from zero)")
     ap.add_argument("--invert-time-limit", type=float, default=180.0)
     return ap.parse_args()
 
