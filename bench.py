@@ -438,7 +438,7 @@ def learned_init_leg(device, n_train, epochs, n_eval, time_limit):
     N.train(net, data, epochs=1, lr=1e-3)  # warm-up epoch (first launches, allocations)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
-    hist = N.train(net, data, epochs=epochs, lr=1e-3, seed=1)
+    hist = N.train(net, data, epochs=epochs, lr=2e-3, seed=1, lr_final=1e-4)
     torch.cuda.synchronize(device)
     t_train = time.perf_counter() - t0
     samples = epochs * (n_train // batch) * batch

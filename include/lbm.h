@@ -55,7 +55,7 @@ extern "C" {
 typedef enum lbm_status {
     LBM_OK = 0,
     LBM_ERR_INVALID_ARG = 1, /* a size, pointer or parameter is out of range */
-    LBM_ERR_UNSUPPORTED = 2, /* a valid request this build does not implement */
+    LBM_ERR_UNSUPPORTED = 2, /* a valid request the library does not implement */
     LBM_ERR_OOM = 3,         /* a caller-provided buffer is too small */
     LBM_ERR_CUDA = 4,        /* a CUDA runtime call failed */
     LBM_ERR_NONFINITE = 5,   /* a loss or gradient came out NaN or Inf */

@@ -6,7 +6,7 @@ and inference as the starting point of the gradient inversion.
 The network (a 4-level U-Net, see the header) reads the observed steady
 velocity field and the obstacle mask of a lattice and predicts the inlet
 density profile delta(y) / 1e-3; the zero-initialised inversion is both the
-fallback and the judge of its error (``evaluate``)."""
+fallback and the yardstick of its error (``evaluate``)."""
 from __future__ import annotations
 
 import ctypes as C
@@ -204,20 +204,26 @@ def _batch_velocity(b, f, dev):
     return out
 
 
-def train(net: UNet, data: Dataset, epochs: int, lr: float = 1e-3, seed: int = 0, log=None):
-    """Adam over shuffled minibatches of the network's batch size; returns the loss history."""
+def train(net: UNet, data: Dataset, epochs: int, lr: float = 1e-3, seed: int = 0, log=None, lr_final=None):
+    """Adam over shuffled minibatches of the network's batch size, the learning
+    rate decaying from lr to lr_final (cosine over the epochs; constant if
+    lr_final is None); returns the loss history."""
+    import math
+
     B = net.desc.batch
     n = (data.x.shape[0] // B) * B
     rng = np.random.Generator(np.random.PCG64(seed))
     hist = []
     for ep in range(epochs):
+        lr_ep = lr if lr_final is None or epochs < 2 else (
+            lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * ep / (epochs - 1))))
         order = torch.as_tensor(rng.permutation(data.x.shape[0])[:n], device=data.x.device)
         tot = 0.0
         for i in range(0, n, B):
             idx = order[i:i + B]
             x = data.x[idx].contiguous()
             t = data.target[idx].contiguous()
-            tot += float(net.train_step(x, t, lr).item())
+            tot += float(net.train_step(x, t, lr_ep).item())
         hist.append(tot / (n // B))
         if log:
             log(f"epoch {ep}: loss {hist[-1]:.4g}")
