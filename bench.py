@@ -301,6 +301,8 @@ def run_native(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_steps)
         cpu["single_thread"] = cpu_baseline(max(20, args.cpu_sample_steps // 4), threads=1)["value"]
+        cpu["cpu_model"] = cpu_model()
+        cpu["other_workloads"] = cpu_other_workloads(cpu["cores"])
 
     rel_err = float(np.linalg.norm((P["rho_in"].cpu().numpy() - wl.rho_out) - P["delta_true"]) /
                     np.linalg.norm(P["delta_true"]))
@@ -639,6 +641,7 @@ def kernel_rooflines(device, hbm_peak, name, n_launch, layout=None):
         tr = HBM_TRAFFIC.get((name, s.layout), {}).get(kern)
         out[kern] = {"bound": "hbm", "kernel": f"{kern} on {name} ({s.layout} layout)", "achieved": round(ach, 1),
                      "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+                     "frac_of_nominal_8tbs": round(ach / 8000.0, 4),
                      "traffic": round(tr) if tr else None, "bytes_per_launch": byts,
                      "us_per_launch": round(t * 1e6, 2), "fluid_nodes": nf, "nodes": N,
                      "glups_fluid": round(nf / t / 1e9, 2)}
@@ -668,6 +671,44 @@ def cpu_baseline(sample_steps, threads=None):
     return {"value": round(wl.nodes * sample_steps / dt / 1e6, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{WORKLOAD} gradient over the first {sample_steps} of 20000 time steps "
                       f"({dt:.1f} s, FP64 C; per-node loops on {cores} OpenMP threads)"}
+
+
+def cpu_model() -> str:
+    """The host CPU as the kernel reports it (model name, or the Arm implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model name"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    parts = {l.split(":", 1)[0].strip(): l.split(":", 1)[1].strip() for l in info.splitlines() if ":" in l}
+    return f"Arm implementer {parts.get('CPU implementer', '?')} part {parts.get('CPU part', '?')}"
+
+
+def cpu_other_workloads(threads):
+    """The oracle's full gradient on the 64x32 FP64 channel (T = 1000) and on a
+    bounded sample of the 128x64x64 D3Q19 packing (the first 10 of its 10000
+    steps), on `threads` OpenMP threads: MLUPS as nodes x steps / s."""
+    from oracle import oracle as O
+    from paper_2310_00810_gb300 import workloads as W
+
+    O.set_threads(threads)
+    out = {}
+    c1 = W.WORKLOADS["channel64x32"]
+    m1, _ = O.geometry(9, c1.nx, c1.ny, kind=O.GEOM_CHANNEL)
+    t0 = time.perf_counter()
+    O.gradient(9, m1, 1.001, 1.0, c1.tau, c1.steps, np.zeros((2, c1.ny, c1.nx)), ckpt_stride=32)
+    out["channel64x32_full_gradient_mlups"] = round(c1.nodes * c1.steps / (time.perf_counter() - t0) / 1e6, 3)
+    c3 = W.WORKLOADS["spheres128x64x64"]
+    m3, _ = O.geometry(19, c3.nx, c3.ny, c3.nz, kind=O.GEOM_SPHERES, seed=c3.seed, r_min=c3.r_min, r_max=c3.r_max,
+                       porosity=c3.porosity)
+    t0 = time.perf_counter()
+    O.gradient(19, m3, 1.001, 1.0, c3.tau, 10, np.zeros((3, c3.nz, c3.ny, c3.nx)), ckpt_stride=3)
+    out["spheres128x64x64_gradient_sample_mlups"] = round(c3.nodes * 10 / (time.perf_counter() - t0) / 1e6, 3)
+    O.set_threads(1)
+    return out
 
 
 def run_reference(args):
