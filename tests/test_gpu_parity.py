@@ -303,3 +303,26 @@ def test_overlapped_reverse_sweep_is_bitwise_the_serial_one(q, layout):
         g_in, g_tau = s.adjoint(dev(rin), dev([0.8]), 1.0, lam)
         out.append((g_in.cpu().numpy(), g_tau.item()))
     assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_compact_bind_checks_the_fluid_count_and_switches_back():
+    """lbm_compact_bind rejects a fluid count that is not the link array's;
+    switching a solver to the compact layout and back gives the same forward."""
+    nx, ny, nz, g = _state_case(19, 4, 61)
+    s = lbm.Solver(19, nx, ny, nz, precision=4, n_steps=20, geometry=g, layout="dense")
+    nf = int(s.info[3].item())
+    tables = torch.empty(lbm.lbm_compact_size(s.plan, nf + 1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_compact_bind(s.plan, nf + 1, tables, s.stream)
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    rin, tau = dev([1.001]), dev([0.8])
+    f_dense = s.forward(rin, tau, 1.0).clone()
+    s.set_layout("compact")
+    assert s.layout == "compact"
+    f_cmp = s.forward(rin, tau, 1.0).clone()
+    s.set_layout("dense")
+    f_back = s.forward(rin, tau, 1.0)
+    fl = ~s.mask_field.bool()
+    assert torch.allclose(f_dense[:, fl], f_cmp[:, fl], rtol=0, atol=1e-8)  # same arithmetic per node
+    assert torch.equal(f_dense, f_back)
+    assert torch.count_nonzero(f_cmp[:, ~fl]).item() == 0
