@@ -19,9 +19,13 @@
  *   grain nodes and at the walls y = -1/2, ny - 1/2 (and z = -1/2, nz - 1/2).
  * Readings of garbled or silent passages (see the design notes): sums run
  * over i = 0..Q-1; the BGK sign is -(f - f^eq)/tau; c_s^2 = 1/3; u_w in
- * Eq. 6 is the boundary node's own velocity at time t; a link that crosses
- * a wall plane and a pressure plane at once bounces back; solid nodes carry
- * no populations.
+ * Eq. 6 is the boundary node's own velocity at time t (or, as an option,
+ * that velocity extrapolated to the pressure plane: set_abb_velocity); a
+ * link that crosses a wall plane and a pressure plane at once bounces back;
+ * solid nodes carry no populations.
+ *
+ * Density probes (an optional second loss term): w sum_p (rho(x_p) - rho_p)^2
+ * over a list of probe nodes, with its seed dL/df_k = 2 w (rho - rho_p).
  *
  * Loss (Eq. 7, Eq. 15, and the compute_loss kernel of section 2.2), taken at
  * the final step only; default is the vector mismatch sum |u - u_t|^2,
@@ -219,6 +223,31 @@ static real_t inlet_rho(const real_t* rho_in, int profile, const domain* D, int 
     return profile ? rho_in[(long)z * D->ny + y] : rho_in[0];
 }
 
+/* Where u in Eq. 6 is taken.  The paper writes the boundary term with a bare
+ * u.  UW_NODE: the boundary node's own velocity at time t.  UW_EXTRAP: that
+ * velocity extrapolated linearly to the pressure plane half a link outside
+ * the node, u_w = u(x_b) + (u(x_b) - u(x_b + e)) / 2 with x_b + e the next
+ * node inward (x = 1 for the inlet node, nx - 2 for the outlet node); where
+ * that node is solid, u_w = u(x_b). */
+enum { UW_NODE = 0, UW_EXTRAP = 1 };
+static int g_uw_mode = UW_NODE;
+
+int SYM(set_abb_velocity)(int mode)
+{
+    if (mode != UW_NODE && mode != UW_EXTRAP) return -1;
+    g_uw_mode = mode;
+    return 0;
+}
+
+/* The inward neighbour whose velocity enters u_w at boundary node n (at x),
+ * or -1 when u_w is the node's own velocity. */
+static long wall_partner(const domain* D, int x, long n)
+{
+    if (g_uw_mode != UW_EXTRAP) return -1;
+    long m = x == 0 ? n + 1 : n - 1;
+    return is_solid(D, m) ? -1 : m;
+}
+
 /* --------------------------------------------------------- collision */
 
 /* BGK collision alone (Eq. 4-5) at every node of an unstructured array of
@@ -295,6 +324,11 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
                     continue;
                 }
                 real_t u[3] = {uvel[n], uvel[N + n], uvel[2 * N + n]};
+                if (x == 0 || x == nx - 1) {
+                    long m = wall_partner(&D, x, n);
+                    if (m >= 0)
+                        for (int a = 0; a < 3; ++a) u[a] = 1.5 * u[a] - 0.5 * uvel[(long)a * N + m];
+                }
                 for (int i = 0; i < q; ++i) {
                     long s = -1;
                     int cls = classify(&D, &L, x, y, z, i, &s);
@@ -438,6 +472,34 @@ int SYM(loss)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
     return 0;
 }
 
+/* Density probes, a second loss term for the joint inversion of the head and
+ * tau (the Stokes-regime velocity fixes only their ratio):
+ *   L_p = w sum_p (rho(x_p) - rho_p)^2     (p = 0..n_probe-1, x_p a dense node index)
+ * A solid probe node contributes nothing.  If lam != NULL the seed
+ * dL_p/df_k(x_p) = 2 w (rho - rho_p) (Eq. 1: drho/df_k = 1) is ADDED to lam. */
+int SYM(probe_loss)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* f, long n_probe,
+                    const int64_t* node, const double* rho_target, double weight, real_t* loss_out, real_t* lam)
+{
+    lattice L;
+    if (lattice_make(q, &L)) return -1;
+    domain D = {nx, ny, nz, (long)nx * ny * nz, mask};
+    long N = D.n;
+    real_t total = 0;
+    for (long p = 0; p < n_probe; ++p) {
+        long n = (long)node[p];
+        if (n < 0 || n >= N) return -3;
+        if (is_solid(&D, n)) continue;
+        real_t rho, u[3];
+        moments(&L, f, N, n, &rho, u);
+        real_t e = rho - rho_target[p];
+        total += weight * e * e;
+        if (lam)
+            for (int k = 0; k < q; ++k) lam[(long)k * N + n] += 2.0 * weight * e;
+    }
+    *loss_out = total;
+    return 0;
+}
+
 #ifndef ORC_COMPLEX
 /* --------------------------------------------------------- link words */
 
@@ -501,9 +563,11 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
 
     /* 1. transpose of streaming + boundaries.  Pull streaming with its
      * boundary links is a permutation of the (direction, node) slots, so each
-     * mu slot and each node's ubar receive from one node only and nodes can be
-     * shared among threads.  The inlet terms (several nodes feed the single
-     * head) go to gin[n] first and are added in node order afterwards. */
+     * mu slot receives from one node only; a node's ubar receives from itself
+     * and, with the extrapolated u_w, from the boundary node of its own row,
+     * so rows can be shared among threads.  The inlet terms (several nodes
+     * feed the single head) go to gin[n] first and are added in node order
+     * afterwards. */
     double* gin = (double*)calloc((size_t)N, sizeof(double));
     if (!gin) {
         free(mu);
@@ -518,6 +582,16 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
                 if (is_solid(&D, n)) continue;
                 double rho, u[3];
                 moments(&L, f_t, N, n, &rho, u);
+                /* u_w = k_self u(n) + k_part u(m) (Eq. 6 and set_abb_velocity) */
+                long m = (x == 0 || x == nx - 1) ? wall_partner(&D, x, n) : -1;
+                double k_self = 1.0, k_part = 0.0;
+                if (m >= 0) {
+                    double rho_m, u_m[3];
+                    moments(&L, f_t, N, m, &rho_m, u_m);
+                    for (int a = 0; a < 3; ++a) u[a] = 1.5 * u[a] - 0.5 * u_m[a];
+                    k_self = 1.5;
+                    k_part = -0.5;
+                }
                 for (int i = 0; i < q; ++i) {
                     long s = -1;
                     int cls = classify(&D, &L, x, y, z, i, &s);
@@ -534,9 +608,12 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
                             double d_rw = 2.0 * L.w[i] * (1.0 + cu * cu * INV_2CS4 - uu * INV_2CS2);
                             gin[n] += lam * d_rw;
                         }
-                        for (int a = 0; a < L.d; ++a)
-                            ubar[(long)a * N + n] +=
+                        for (int a = 0; a < L.d; ++a) {
+                            double du_w =
                                 lam * 2.0 * L.w[i] * rw * (2.0 * INV_2CS4 * cu * L.c[i][a] - 2.0 * INV_2CS2 * u[a]);
+                            ubar[(long)a * N + n] += k_self * du_w;
+                            if (m >= 0) ubar[(long)a * N + m] += k_part * du_w;
+                        }
                     }
                 }
             }
@@ -602,7 +679,8 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
  * operations).  f0 = NULL starts from rest.  fT_out (optional) gets f^T. */
 int orc_gradient(int q, int nx, int ny, int nz, const uint8_t* mask, const double* rho_in, int inlet_profile,
                  const double* rho_out, const double* tau, int T, const double* f0, const double* u_target,
-                 const uint8_t* roi, int loss_kind, int loss_norm, int ckpt_stride, double* loss_out,
+                 const uint8_t* roi, int loss_kind, int loss_norm, long n_probe, const int64_t* probe_node,
+                 const double* probe_rho, double probe_weight, int ckpt_stride, double* loss_out,
                  double* g_rho_in, double* g_tau, double* fT_out)
 {
     lattice L;
@@ -640,6 +718,12 @@ int orc_gradient(int q, int nx, int ny, int nz, const uint8_t* mask, const doubl
 
     /* loss and its seed lam^T = dL/df^T */
     if ((rc = orc_loss(q, nx, ny, nz, mask, a, u_target, roi, loss_kind, loss_norm, loss_out, lam))) goto done;
+    if (n_probe > 0) {
+        double lp = 0;
+        if ((rc = orc_probe_loss(q, nx, ny, nz, mask, a, n_probe, probe_node, probe_rho, probe_weight, &lp, lam)))
+            goto done;
+        *loss_out += lp;
+    }
 
     /* reverse sweep, one segment at a time, last segment first */
     for (int i = 0; i < n_in; ++i) g_rho_in[i] = 0;

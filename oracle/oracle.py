@@ -32,6 +32,7 @@ _libs: dict = {}
 LOSS_VEC, LOSS_NORM = 0, 1
 NORM_SUM, NORM_MEAN_FLUID = 0, 1
 GEOM_CHANNEL, GEOM_DISKS, GEOM_SPHERES = 0, 1, 2
+UW_NODE, UW_EXTRAP = 0, 1
 
 
 def build(force: bool = False) -> None:
@@ -79,6 +80,31 @@ def _dims(q: int, shape) -> tuple[int, int, int]:
 def set_threads(n: int) -> int:
     """OpenMP threads for the per-node loops (results do not depend on it)."""
     return int(_lib().orc_set_threads(int(n)))
+
+
+def set_abb_velocity(mode: int) -> None:
+    """Where Eq. 6 takes its velocity: UW_NODE (the boundary node's own, the
+    default) or UW_EXTRAP (extrapolated to the pressure plane).  Applies to
+    every later call, in both the real and the complex-step builds."""
+    for cs in (False, True):
+        lib = _lib(cs)
+        fn = lib.orc_cs_set_abb_velocity if cs else lib.orc_set_abb_velocity
+        _check(fn(int(mode)), "set_abb_velocity")
+
+
+class abb_velocity:
+    """``with abb_velocity(UW_EXTRAP): ...`` sets the Eq. 6 velocity for the block."""
+
+    def __init__(self, mode: int):
+        self.mode = mode
+
+    def __enter__(self):
+        set_abb_velocity(self.mode)
+        return self
+
+    def __exit__(self, *exc):
+        set_abb_velocity(UW_NODE)
+        return False
 
 
 def lattice(q: int):
@@ -211,6 +237,27 @@ def loss(q, mask, f, u_target, roi=None, kind=LOSS_VEC, norm=NORM_SUM, seed=True
     return (out[0], lam) if seed else out[0]
 
 
+def probe_loss(q, mask, f, nodes, rho_target, weight=1.0, complex_step=False):
+    """Density-probe loss w sum_p (rho(x_p) - rho_p)^2 and its seed dL/df
+    (nonzero only at the probe nodes); nodes are dense node indices."""
+    dt = np.complex128 if complex_step else np.float64
+    lib = _lib(complex_step)
+    fn = lib.orc_cs_probe_loss if complex_step else lib.orc_probe_loss
+    fn.argtypes = [C.c_int] * 4 + [C.c_void_p, C.c_void_p, C.c_long, C.c_void_p, C.c_void_p, C.c_double,
+                                   C.c_void_p, C.c_void_p]
+    nx, ny, nz = _dims(q, mask.shape)
+    m = np.ascontiguousarray(mask, np.uint8)
+    fi = np.ascontiguousarray(f, dt)
+    idx = np.ascontiguousarray(nodes, np.int64)
+    rt = np.ascontiguousarray(rho_target, np.float64)
+    assert idx.shape == rt.shape
+    out = np.zeros(1, dt)
+    lam = np.zeros_like(fi)
+    _check(fn(q, nx, ny, nz, _p(m), _p(fi), idx.size, _p(idx), _p(rt), float(weight), _p(out), _p(lam)),
+           "probe_loss")
+    return out[0], lam
+
+
 def adjoint_step(q, mask, f_t, lam_next, rho_in, rho_out, tau):
     """One reverse step: returns (lam_t, dL/drho_in contribution, dL/domega contribution)."""
     nx, ny, nz = _dims(q, mask.shape)
@@ -228,8 +275,9 @@ def adjoint_step(q, mask, f_t, lam_next, rho_in, rho_out, tau):
 
 
 def gradient(q, mask, rho_in, rho_out, tau, T, u_target, roi=None, kind=LOSS_VEC, norm=NORM_SUM, ckpt_stride=0,
-             f0=None, return_fT=False):
-    """Loss and gradients of the final-step loss: (L, dL/drho_in, dL/dtau[, f^T])."""
+             f0=None, return_fT=False, probes=None):
+    """Loss and gradients of the final-step loss: (L, dL/drho_in, dL/dtau[, f^T]).
+    probes = (nodes, rho_target, weight) adds the density-probe term (probe_loss)."""
     nx, ny, nz = _dims(q, mask.shape)
     m = np.ascontiguousarray(mask, np.uint8)
     rin, rout, t = _real_args(rho_in, rho_out, tau, np.float64)
@@ -241,8 +289,15 @@ def gradient(q, mask, rho_in, rho_out, tau, T, u_target, roi=None, kind=LOSS_VEC
     g_in = np.zeros(rin.size)
     g_tau = np.zeros(1)
     fT = np.empty((q,) + m.shape) if return_fT else None
+    if probes is None:
+        pn, pr, pw = np.zeros(0, np.int64), np.zeros(0), 0.0
+    else:
+        pn, pr = np.ascontiguousarray(probes[0], np.int64), np.ascontiguousarray(probes[1], np.float64)
+        pw = float(probes[2])
+        assert pn.shape == pr.shape
     _check(_lib().orc_gradient(q, nx, ny, nz, _p(m), _p(rin), prof, _p(rout), _p(t), int(T), _p(f0c), _p(ut), _p(r),
-                               kind, norm, int(ckpt_stride), _p(L), _p(g_in), _p(g_tau), _p(fT)), "gradient")
+                               kind, norm, C.c_long(pn.size), _p(pn), _p(pr), C.c_double(pw), int(ckpt_stride),
+                               _p(L), _p(g_in), _p(g_tau), _p(fT)), "gradient")
     g = g_in if prof else g_in[0]
     return (L[0], g, g_tau[0], fT) if return_fT else (L[0], g, g_tau[0])
 
