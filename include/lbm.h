@@ -127,6 +127,23 @@ typedef struct lbm_kernel_choice {
 LBM_API lbm_status lbm_plan_set_kernels(lbm_plan* plan, const lbm_kernel_choice* choice);
 LBM_API lbm_status lbm_plan_get_kernels(const lbm_plan* plan, lbm_kernel_choice* choice);
 
+/* Where Eq. 6 (section 2.1, the anti-bounce-back pressure boundary) takes
+ * the velocity of its quadratic term; the paper writes it as a bare u.
+ *   LBM_ABB_U_NODE    the boundary node's own velocity at time t (default)
+ *   LBM_ABB_U_EXTRAP  that velocity extrapolated linearly to the pressure
+ *                     plane half a link outside the node:
+ *                     u_w = u(x_b) + (u(x_b) - u(x_b + e)) / 2, x_b + e the
+ *                     next node inward; where that node is solid, u_w = u(x_b)
+ * lbm_forward, lbm_step and lbm_adjoint follow the setting.  With
+ * LBM_ABB_U_EXTRAP the dense layout runs the one-node-per-thread kernels (no
+ * TMA, register-vector or persistent kernels) and each adjoint step is
+ * followed by one short per-row pass; the fluid-only layout keeps its
+ * kernels.  Batches (lbm_batch_*) use the node velocity.  Cached CUDA graphs
+ * are dropped on a change.  Errors: INVALID_ARG for an unknown mode. */
+enum { LBM_ABB_U_NODE = 0, LBM_ABB_U_EXTRAP = 1 };
+LBM_API lbm_status lbm_set_abb_velocity(lbm_plan* plan, int32_t mode);
+LBM_API lbm_status lbm_get_abb_velocity(const lbm_plan* plan, int32_t* mode);
+
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
  * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and two
  * segment buffers, adjoint ping-pong states and FP64 reduction slots. */
@@ -241,6 +258,28 @@ LBM_API lbm_status lbm_loss_grad(lbm_plan* plan, const void* d_f, const double* 
 #define LBM_NOALLOC_MAX_BLOCKS 65536
 LBM_API lbm_status lbm_loss_grad_noalloc(lbm_plan* plan, const void* d_f, const double* d_u_target,
                                          const uint8_t* d_roi, double* d_loss, void* d_lambda, void* stream);
+
+/* Density probes: adds the term w sum_p (rho(x_p) - rho_p)^2 to the loss
+ * and its seed 2 w (rho(x_p) - rho_p) to every direction of lambda^T at x_p
+ * (drho/df_k = 1, Eq. 1).  A second observation for the joint inversion of
+ * the inlet head and tau (section 3.3), which the steady velocity alone
+ * fixes only through their ratio in the Stokes regime.  Call it after
+ * lbm_loss_grad on the same d_loss / d_lambda.
+ *  d_f           f^T (shifted, plan precision), dense
+ *  n_probe       number of probes (0: nothing to add)
+ *  d_probe_node  int64[n_probe] dense node indices (z ny + y) nx + x
+ *  d_rho_target  double[n_probe] observed densities
+ *  weight        w (finite)
+ *  d_loss        double[1] in/out: the term is added
+ *  d_lambda      plan precision, Q N values, in/out: the seeds are added
+ * A solid probe node contributes nothing.  A node listed twice gets both
+ * seeds, added atomically (their order, so the last bit, may vary between
+ * runs); distinct nodes give deterministic results.  An out-of-range node
+ * latches LBM_ERR_INVALID_ARG in the status word and is skipped; a non-finite
+ * loss latches LBM_ERR_NONFINITE. */
+LBM_API lbm_status lbm_probe_loss_grad(lbm_plan* plan, const void* d_f, int64_t n_probe, const int64_t* d_probe_node,
+                                       const double* d_rho_target, double weight, double* d_loss, void* d_lambda,
+                                       void* d_ws, void* stream);
 
 /* Reverse sweep from lambda^T to t = 0 through the checkpoints left in d_ws
  * by the last lbm_forward with the same parameters: recompute each segment,

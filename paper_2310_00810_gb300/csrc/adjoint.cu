@@ -21,6 +21,8 @@
 //      accumulated in place across steps: fixed order, no atomics);
 //      dL/drho_w(y, z) += sum over Eq. 6 inlet links of lambda_i 2 w_i (1 + 4.5 (c_i.u)^2 - 1.5 u.u)
 //      (one owner thread per inlet node, accumulated in place across steps).
+// With the extrapolated Eq. 6 velocity a second, per-row pass adds what the
+// extrapolation changes (k_adjoint_uw).
 #include "device.cuh"
 
 namespace lbm {
@@ -125,6 +127,63 @@ __global__ void __launch_bounds__(kStepThreads)
     if (tid == 0) partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] += bs;
 }
 
+// Reverse of the extrapolated Eq. 6 velocity (Bc::uw_extrap), run after the
+// adjoint step: one thread per row adds adjoint_uw_delta at the row's inlet
+// node and its inward neighbour, then at the outlet node and its neighbour
+// (one thread for both sides, so the two never race on a short row).  A side
+// whose boundary node or inward neighbour is solid keeps the node velocity
+// and needs nothing.  Not used at t = 0: at rest u = u_w = 0 and every delta
+// vanishes.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kStepThreads)
+    k_adjoint_uw(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Geo g, Bc bc,
+                 double* __restrict__ grad_acc)
+{
+    pdl_enter();
+    using L = Lattice<Q>;
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (long long)g.ny * g.nz) return;
+    const int y = (int)(row % g.ny), z = (int)(row / g.ny);
+    const long long N = g.N;
+    for (int side = 0; side < 2; ++side) {
+        const bool xin = side == 0;
+        const int xb = xin ? 0 : g.nx - 1, xe = xin ? 1 : g.nx - 2;
+        const long long nb = row * g.nx + xb, ne = row * g.nx + xe;
+        const uint32_t lb = g.link[nb];
+        if ((lb & kLinkSolid) || ((lb >> inward_dir<Q>(xin)) & 1u)) continue;
+        T fb[Q], fe[Q], li[Q];
+        pull<Q, T>(fb, gprev, nb, xb, y, z, lb, g, bc);
+        pull<Q, T>(fe, gprev, ne, xe, y, z, g.link[ne], g, bc);
+        uint32_t eq6 = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            const int cx = L::c(i, 0);
+            const bool on = ((cx == 1 && xin) || (cx == -1 && !xin)) && !((lb >> i) & 1u);
+            eq6 |= on ? (1u << i) : 0u;
+            li[i] = on ? lam_in[(long long)i * N + nb] : T(0);
+        }
+        const T rw = T(xin ? (bc.profile ? bc.rho_in[row] : bc.rho_in[0]) : bc.rho_out);
+        T db[Q], de[Q];
+        const double dg = adjoint_uw_delta<Q, T>(fb, fe, li, eq6, rw, db, de);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            lam_out[(long long)k * N + nb] += db[k];
+            lam_out[(long long)k * N + ne] += de[k];
+        }
+        if (xin) grad_acc[row] += dg;
+    }
+}
+
+template <int Q, typename T>
+static void launch_uw(const PlanInfo& p, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
+                      double* grad_acc, cudaStream_t s)
+{
+    const long long rows = (long long)p.geo.ny * p.geo.nz;
+    launch_k(p.pdl, k_adjoint_uw<Q, T>, dim3((unsigned)((rows + kStepThreads - 1) / kStepThreads)), dim3(kStepThreads),
+             0, s, static_cast<const T*>(gprev), static_cast<const T*>(lam_in), static_cast<T*>(lam_out), p.geo, bc,
+             grad_acc);
+}
+
 template <int Q, typename T>
 static void launch(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
                    const double* tau, double* grad_acc, double* partial, cudaStream_t s)
@@ -142,6 +201,25 @@ lbm_status adjoint_launch(const PlanInfo& plan, int t_is_zero, const void* gprev
                           const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
     if (plan.cmp.nf) return adjoint_launch_cmp(plan, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+    if (bc.uw_extrap) {
+        // the extrapolated u_w runs on the one-node-per-thread kernels plus its reverse pass
+        const PlanInfo p = with_family(plan, LBM_FAMILY_SCALAR);
+        if (p.q == 9 && p.prec == 4) launch<9, float>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+        else if (p.q == 9 && p.prec == 8)
+            launch<9, double>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+        else if (p.q == 19 && p.prec == 4)
+            launch<19, float>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+        else if (p.q == 19 && p.prec == 8)
+            launch<19, double>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
+        else return LBM_ERR_UNSUPPORTED;
+        if (!t_is_zero) {
+            if (p.q == 9 && p.prec == 4) launch_uw<9, float>(p, gprev, lam_in, lam_out, bc, grad_acc, s);
+            else if (p.q == 9) launch_uw<9, double>(p, gprev, lam_in, lam_out, bc, grad_acc, s);
+            else if (p.prec == 4) launch_uw<19, float>(p, gprev, lam_in, lam_out, bc, grad_acc, s);
+            else launch_uw<19, double>(p, gprev, lam_in, lam_out, bc, grad_acc, s);
+        }
+        return cuda_status(cudaGetLastError());
+    }
     const PlanInfo p = with_family(plan, plan.adj_family);
     if (adjoint_launch_tma(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s))
         return cuda_status(cudaGetLastError());

@@ -124,6 +124,7 @@ Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
     bc.profile = p->info.n_in > 1 ? 1 : 0;
     bc.rho_out = rho_out;
     bc.status = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + p->ws.status);
+    bc.uw_extrap = p->info.uw_extrap;
     return bc;
 }
 
@@ -167,6 +168,7 @@ void drop_graphs(lbm_plan* p)
 void set_dense(lbm_plan* p)
 {
     p->info.cmp = Cmp{0, nullptr, nullptr};
+    p->info.cmp_map = nullptr;
     p->info.state_bytes = p->dense_state_bytes;
     p->info.n_partial = p->dense_n_partial;
     layout(p);
@@ -353,6 +355,21 @@ lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
     return LBM_OK;
 }
 
+lbm_status lbm_set_abb_velocity(lbm_plan* p, int32_t mode)
+{
+    if (!p || (mode != LBM_ABB_U_NODE && mode != LBM_ABB_U_EXTRAP)) return LBM_ERR_INVALID_ARG;
+    p->info.uw_extrap = mode == LBM_ABB_U_EXTRAP ? 1 : 0;
+    drop_graphs(p);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_abb_velocity(const lbm_plan* p, int32_t* mode)
+{
+    if (!p || !mode) return LBM_ERR_INVALID_ARG;
+    *mode = p->info.uw_extrap ? LBM_ABB_U_EXTRAP : LBM_ABB_U_NODE;
+    return LBM_OK;
+}
+
 lbm_status lbm_workspace_size(const lbm_plan* p, size_t* bytes_out)
 {
     if (!p || !bytes_out) return LBM_ERR_INVALID_ARG;
@@ -408,8 +425,10 @@ lbm_status lbm_compact_bind(lbm_plan* p, int64_t n_fluid, void* d_tables, void* 
     }
     if (!d_tables || !aligned256(d_tables)) return LBM_ERR_INVALID_ARG;
     Cmp c{0, nullptr, nullptr};
-    LBM_TRY(compact_build(p->info, n_fluid, d_tables, &c, static_cast<cudaStream_t>(stream)));
+    const int32_t* cmap = nullptr;
+    LBM_TRY(compact_build(p->info, n_fluid, d_tables, &c, &cmap, static_cast<cudaStream_t>(stream)));
     p->info.cmp = c;
+    p->info.cmp_map = cmap;
     p->info.state_bytes = (size_t)p->info.q * (size_t)n_fluid * (size_t)p->info.prec;
     p->info.n_partial = std::max(p->dense_n_partial, (int)((n_fluid + 31) / 32));  // one slot per warp
     layout(p);
@@ -522,6 +541,18 @@ lbm_status lbm_loss_grad_noalloc(lbm_plan* p, const void* d_f, const double* d_u
     if (!d_f || !d_u_target || !d_loss || !d_lambda) return LBM_ERR_INVALID_ARG;
     return loss_launch_noalloc(p->info, d_f, d_u_target, d_roi, p->desc.loss_kind, p->desc.loss_norm, d_loss,
                                d_lambda, static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_probe_loss_grad(lbm_plan* p, const void* d_f, int64_t n_probe, const int64_t* d_probe_node,
+                               const double* d_rho_target, double weight, double* d_loss, void* d_lambda, void* d_ws,
+                               void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    if (n_probe < 0 || !d_f || !d_loss || !d_lambda || !d_ws || !std::isfinite(weight)) return LBM_ERR_INVALID_ARG;
+    if (n_probe > 0 && (!d_probe_node || !d_rho_target)) return LBM_ERR_INVALID_ARG;
+    p->last_ws = d_ws;
+    return probe_launch(p->info, d_f, n_probe, d_probe_node, d_rho_target, weight, d_loss, d_lambda,
+                        reinterpret_cast<uint32_t*>(bytes(d_ws) + p->ws.status), static_cast<cudaStream_t>(stream));
 }
 
 lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,

@@ -41,6 +41,7 @@ struct Geo {
 struct Bc {
     const double* rho_in;  // device: 1 or ny*nz entries
     int profile;           // 1: rho_in[z*ny + y], 0: rho_in[0]
+    int uw_extrap = 0;     // 1: Eq. 6 takes u_w extrapolated to the pressure plane (LBM_ABB_U_EXTRAP)
     double rho_out;
     uint32_t* status;      // device status word (bounded waits latch LBM_ERR_TIMEOUT here)
 };
@@ -74,11 +75,13 @@ struct PlanInfo {
     int pdl;          // 1: launch the sweep kernels with programmatic dependent launch
     int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes
     int overlap;      // 1: reverse sweep recomputes the next segment on a second stream during the adjoint steps
+    int uw_extrap;    // 1: Eq. 6 with the extrapolated wall velocity (one-node-per-thread or fluid-only kernels)
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     size_t persist_max_bytes;
     int tma_min_tiles;  // smallest tile count for which the TMA kernels are used
     size_t state_bytes;   // bytes of one internal state (Q N, or Q nf in the compact layout)
     Cmp cmp;
+    const int32_t* cmp_map;  // cmap[n]: compact index of dense node n, or -1 for a solid node (compact layout)
 };
 
 // Grid barrier words of the persistent sweeps (in the status section).
@@ -212,12 +215,17 @@ inline PlanInfo with_family(const PlanInfo& p, int family)
 }
 
 size_t compact_table_bytes(const PlanInfo& p, long long nf);
-lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, cudaStream_t s);
+lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, const int32_t** cmap_out,
+                         cudaStream_t s);
 lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* dst, bool dense_in, bool dense_out,
                            const Bc& bc, const double* tau, cudaStream_t s);
 lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,
                               const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s);
 lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s);
+
+lbm_status probe_launch(const PlanInfo& p, const void* f, long long n_probe, const int64_t* node,
+                        const double* rho_target, double weight, double* d_loss, void* lambda, uint32_t* status,
+                        cudaStream_t s);
 
 bool persist_ok(const PlanInfo& p);
 lbm_status forward_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau, cudaStream_t s);

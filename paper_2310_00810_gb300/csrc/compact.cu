@@ -226,8 +226,12 @@ __device__ __forceinline__ void pull_cmp(T (&v)[Q], const T* __restrict__ src, l
         for (int i = 0; i < Q; ++i) loc[i] = src[(long long)i * NF + k];
         T drho, rho, u[3];
         moments<Q, T>(loc, drho, rho, u);
-        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const Side sd = side_of(c.idx, k, g);
+        if (bc.uw_extrap) {
+            const int32_t ke = code[inward_dir<Q>(sd.xin)];
+            if (ke >= 0) extrapolate_wall_velocity<Q, T>(u, src, NF, ke);
+        }
+        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const double rw = sd.xin ? (bc.profile ? bc.rho_in[sd.row] : bc.rho_in[0]) : bc.rho_out;
         const T drw = T(rw - 1.0), rwT = T(rw);
         v[0] = loc[0];
@@ -497,6 +501,50 @@ __global__ void __launch_bounds__(kCmpThreads, 4)
     if ((threadIdx.x & 31) == 0 && k < c.nf) partial[k >> 5] += (double)dw;  // lane 0: k = first node of the warp
 }
 
+// Reverse of the extrapolated Eq. 6 velocity in the compact layout: the
+// per-row pass of adjoint.cu (k_adjoint_uw), with the boundary node found
+// through cmap and its inward neighbour through its own table entry.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kCmpThreads)
+    k_adjoint_uw_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c,
+                     const int32_t* __restrict__ cmap, Geo g, Bc bc, double* __restrict__ grad_acc)
+{
+    pdl_enter();
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (long long)g.ny * g.nz) return;
+    const size_t NF = (size_t)c.nf;
+    for (int side = 0; side < 2; ++side) {
+        const bool xin = side == 0;
+        const int32_t kb = cmap[row * g.nx + (xin ? 0 : g.nx - 1)];
+        if (kb < 0) continue;
+        int32_t cb[Q], ce[Q];
+        const bool bb = load_codes<Q>(cb, c, kb);
+        const int32_t ke = cb[inward_dir<Q>(xin)];
+        if (ke < 0) continue;  // inward neighbour solid: u_w is the node's own velocity
+        const bool be = load_codes<Q>(ce, c, ke);
+        T fb[Q], fe[Q], li[Q];
+        pull_cmp<Q, T>(fb, gprev, kb, c.nf, cb, bb, c, g, bc);
+        pull_cmp<Q, T>(fe, gprev, ke, c.nf, ce, be, c, g, bc);
+        uint32_t eq6 = 0;
+        li[0] = T(0);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const bool on = cb[i] == kCmpABB;
+            eq6 |= on ? (1u << i) : 0u;
+            li[i] = on ? lam_in[(size_t)i * NF + kb] : T(0);
+        }
+        const T rw = T(xin ? (bc.profile ? bc.rho_in[row] : bc.rho_in[0]) : bc.rho_out);
+        T db[Q], de[Q];
+        const double dg = adjoint_uw_delta<Q, T>(fb, fe, li, eq6, rw, db, de);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            lam_out[(size_t)k * NF + kb] += db[k];
+            lam_out[(size_t)k * NF + ke] += de[k];
+        }
+        if (xin) grad_acc[row] += dg;
+    }
+}
+
 // CTAs of `kernel` that fit on the GPU at once (the grid of a grid-stride launch).
 template <class K>
 unsigned resident_ctas(K kernel)
@@ -568,13 +616,19 @@ void launch_adjoint(const PlanInfo& p, int t0, const void* gprev, const void* la
     else
         launch_k(p.pdl, k_adjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
                  partial);
+    if (bc.uw_extrap && !t0) {  // at t = 0 the fluid is at rest and the pass adds nothing
+        const long long rows = (long long)p.geo.ny * p.geo.nz;
+        launch_k(p.pdl, k_adjoint_uw_cmp<Q, T>, dim3((unsigned)((rows + kCmpThreads - 1) / kCmpThreads)), block, 0, s,
+                 gp, li, lo, p.cmp, p.cmp_map, p.geo, bc, grad_acc);
+    }
 }
 
 }  // namespace
 
 size_t compact_table_bytes(const PlanInfo& p, long long nf) { return table_layout(p, nf).bytes; }
 
-lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, cudaStream_t s)
+lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, const int32_t** cmap_out,
+                         cudaStream_t s)
 {
     const TableLayout t = table_layout(p, nf);
     unsigned char* base = static_cast<unsigned char*>(tables);
@@ -601,6 +655,7 @@ lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out
     out->nf = nf;
     out->idx = idx;
     out->nbr = nbr;
+    *cmap_out = cmap;
     return LBM_OK;
 }
 

@@ -61,6 +61,84 @@ __device__ __forceinline__ void collide(T (&v)[Q], T omega)
     }
 }
 
+// Eq. 6 with the wall velocity extrapolated to the pressure plane half a
+// link outside the boundary node (Bc::uw_extrap): u_w = u(x_b) + (u(x_b) -
+// u(x_b + e)) / 2, with x_b + e the inward neighbour, whose velocity comes from
+// its post-collision populations (collision keeps u).  `nb` indexes the
+// neighbour in a state of `stride` nodes per direction.
+template <int Q, typename T>
+__device__ __forceinline__ void extrapolate_wall_velocity(T (&u)[3], const T* __restrict__ src, long long stride,
+                                                          long long nb)
+{
+    T v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = src[(long long)i * stride + nb];
+    T drho, rho, ue[3];
+    moments<Q, T>(v, drho, rho, ue);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = T(1.5) * u[a] - T(0.5) * ue[a];
+}
+
+// The direction whose link starts at the inward neighbour of a boundary node:
+// c = (-1, 0, 0) at the inlet (x - c = x + 1), (+1, 0, 0) at the outlet.
+template <int Q>
+__host__ __device__ constexpr int inward_dir(bool xin)
+{
+    return xin ? Lattice<Q>::opp(1) : 1;
+}
+
+// Reverse of the extrapolated u_w at one boundary node x_b with inward
+// neighbour x_e.  The adjoint kernels take u_w as the node's own velocity u;
+// this returns what the extrapolation changes: the velocity terms of x_b
+// become 1.5 G(u_w) instead of G(u), x_e gains -0.5 G(u_w), and the inlet
+// gradient changes by the difference of d(Eq. 6)/drho_w.  With
+// G_a(v) = sum over the node's Eq. 6 links i of lambda_i 2 w_i rho_w (9 (c_i.v) c_ia - 3 v_a),
+// the deltas are  d_b[k] = sum_a (1.5 G_a(u_w) - G_a(u)) (c_ka - u_a) / rho(x_b)
+// and d_e[k] = sum_a (-0.5 G_a(u_w)) (c_ka - u_e,a) / rho(x_e).
+// fb, fe: f^t at x_b and x_e; li[i]: lambda^{t+1}_i(x_b) for the Eq. 6 links
+// (bit i of eq6); returns the change of dL/drho_w.
+template <int Q, typename T>
+__device__ __forceinline__ double adjoint_uw_delta(const T (&fb)[Q], const T (&fe)[Q], const T (&li)[Q],
+                                                   uint32_t eq6, T rw, T (&db)[Q], T (&de)[Q])
+{
+    using L = Lattice<Q>;
+    T drb, rhob, ub[3], dre, rhoe, ue[3];
+    moments<Q, T>(fb, drb, rhob, ub);
+    moments<Q, T>(fe, dre, rhoe, ue);
+    T uw[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) uw[a] = T(1.5) * ub[a] - T(0.5) * ue[a];
+    const T uub = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+    const T uuw = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+    T Gw[3] = {T(0), T(0), T(0)}, Gu[3] = {T(0), T(0), T(0)};
+    double dgrw = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        if (!((eq6 >> i) & 1u)) continue;
+        const T two_w = T(2.0 * L::w(i));
+        const T cw = cdot<Q, T>(i, uw), cb = cdot<Q, T>(i, ub);
+        dgrw += (double)(li[i] * two_w * (T(4.5) * (cw * cw - cb * cb) - T(1.5) * (uuw - uub)));
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+            Gw[a] += li[i] * two_w * rw * (T(9) * cw * T(L::c(i, a)) - T(3) * uw[a]);
+            Gu[a] += li[i] * two_w * rw * (T(9) * cb * T(L::c(i, a)) - T(3) * ub[a]);
+        }
+    }
+    const T invb = T(1) / rhob, inve = T(1) / rhoe;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        T sb = 0, se = 0;
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) {
+            sb += (T(1.5) * Gw[a] - Gu[a]) * (T(L::c(k, a)) - ub[a]);
+            se += T(-0.5) * Gw[a] * (T(L::c(k, a)) - ue[a]);
+        }
+        db[k] = sb * invb;
+        de[k] = se * inve;
+    }
+    return dgrw;
+}
+
 // Pull with boundaries: fills v with what node n (at x, y, z) receives.
 template <int Q, typename T>
 __device__ __forceinline__ void pull(T (&v)[Q], const T* __restrict__ src, long long n, int x, int y, int z,
@@ -76,6 +154,8 @@ __device__ __forceinline__ void pull(T (&v)[Q], const T* __restrict__ src, long 
         for (int i = 0; i < Q; ++i) loc[i] = src[(long long)i * N + n];
         T drho, rho, u[3];
         moments<Q, T>(loc, drho, rho, u);
+        if (bc.uw_extrap && !((lw >> inward_dir<Q>(xin)) & 1u))
+            extrapolate_wall_velocity<Q, T>(u, src, N, xin ? n + 1 : n - 1);
         const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const double rw = xin ? (bc.profile ? bc.rho_in[(long long)z * g.ny + y] : bc.rho_in[0]) : bc.rho_out;
         const T drw = T(rw - 1.0), rwT = T(rw);

@@ -102,6 +102,67 @@ __global__ void __launch_bounds__(kStepThreads)
     if (threadIdx.x == 0) partial[((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = bs;
 }
 
+// Density probes, a second loss term (w sum_p (rho(x_p) - rho_p)^2) for the
+// joint inversion of the head and tau, whose velocity field alone fixes only
+// their ratio in the Stokes regime.  Adds the term to *d_loss and its seed
+// 2 w (rho(x_p) - rho_p) to every direction of lambda^T at x_p (drho/df_k = 1,
+// Eq. 1).  One block: the loss is summed in a fixed order; a node listed twice
+// gets both seeds through atomics (their order, so the last bit, may vary).
+// An out-of-range node latches LBM_ERR_INVALID_ARG and is skipped; a solid
+// node contributes nothing.
+template <int Q, typename T>
+__global__ void __launch_bounds__(kReduceThreads)
+    k_probe_loss(const T* __restrict__ f, Geo g, long long n_probe, const int64_t* __restrict__ node,
+                 const double* __restrict__ rho_t, double w, double* __restrict__ d_loss, T* __restrict__ lam,
+                 uint32_t* __restrict__ status)
+{
+    const long long N = g.N;
+    double term = 0.0;
+    for (long long p = threadIdx.x; p < n_probe; p += blockDim.x) {
+        const long long n = node[p];
+        if (n < 0 || n >= N) {
+            atomicOr(status, 1u << LBM_ERR_INVALID_ARG);
+            continue;
+        }
+        if (g.link[n] & kLinkSolid) continue;
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) s += f[(long long)i * N + n];
+        const double e = (1.0 + (double)s) - rho_t[p];
+        term += w * e * e;
+        const T seed = T(2.0 * w * e);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) atomicAdd(lam + (long long)k * N + n, seed);
+    }
+    const double bs = block_sum(term, threadIdx.x, blockDim.x);
+    if (threadIdx.x == 0) {
+        *d_loss += bs;
+        if (!isfinite(*d_loss)) atomicOr(status, 1u << LBM_ERR_NONFINITE);
+    }
+}
+
+lbm_status probe_launch(const PlanInfo& p, const void* f, long long n_probe, const int64_t* node,
+                        const double* rho_target, double weight, double* d_loss, void* lambda, uint32_t* status,
+                        cudaStream_t s)
+{
+    const dim3 grid(1), block(kReduceThreads);
+    if (p.q == 9 && p.prec == 4)
+        k_probe_loss<9, float><<<grid, block, 0, s>>>(static_cast<const float*>(f), p.geo, n_probe, node, rho_target,
+                                                      weight, d_loss, static_cast<float*>(lambda), status);
+    else if (p.q == 9)
+        k_probe_loss<9, double><<<grid, block, 0, s>>>(static_cast<const double*>(f), p.geo, n_probe, node,
+                                                       rho_target, weight, d_loss, static_cast<double*>(lambda),
+                                                       status);
+    else if (p.prec == 4)
+        k_probe_loss<19, float><<<grid, block, 0, s>>>(static_cast<const float*>(f), p.geo, n_probe, node, rho_target,
+                                                       weight, d_loss, static_cast<float*>(lambda), status);
+    else
+        k_probe_loss<19, double><<<grid, block, 0, s>>>(static_cast<const double*>(f), p.geo, n_probe, node,
+                                                        rho_target, weight, d_loss, static_cast<double*>(lambda),
+                                                        status);
+    return cuda_status(cudaGetLastError());
+}
+
 __global__ void k_loss_final(const double* __restrict__ partial, int nb, double* __restrict__ d_loss,
                              uint32_t* __restrict__ status)
 {

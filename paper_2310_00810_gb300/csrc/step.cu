@@ -19,7 +19,8 @@
 //   x - c_i beyond the plane x = -1/2 / nx - 1/2 (and not a wall link)
 //        -> -g_opp(i)(x) + 2 w_i (rho_w (1 + 4.5 (c_i.u_w)^2 - 1.5 u_w.u_w) - 1)   (Eq. 6,
 //           shifted; u_w is the node's own velocity at time t, from its
-//           post-collision populations, which collision does not change)
+//           post-collision populations, which collision does not change, or
+//           with Bc::uw_extrap that velocity extrapolated to the plane)
 //   otherwise                                  ->  g_i(x - c_i)
 #include "device.cuh"
 
@@ -66,7 +67,8 @@ lbm_status step_launch(const PlanInfo& plan, int mode, const void* src, void* ds
                        cudaStream_t s)
 {
     if (plan.cmp.nf) return step_launch_cmp(plan, mode, src, dst, false, false, bc, tau, s);
-    const PlanInfo p = with_family(plan, plan.step_family);
+    // the extrapolated Eq. 6 velocity is implemented by the one-node-per-thread kernels
+    const PlanInfo p = with_family(plan, bc.uw_extrap ? LBM_FAMILY_SCALAR : plan.step_family);
     if (step_launch_tma(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (step_launch_vec(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (p.q == 9 && p.prec == 4) launch<9, float>(p, mode, src, dst, bc, tau, s);

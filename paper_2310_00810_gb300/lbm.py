@@ -27,11 +27,12 @@ LBM_GEOM_CHANNEL, LBM_GEOM_DISKS, LBM_GEOM_SPHERES, LBM_GEOM_MASK = 0, 1, 2, 3
 LBM_LINK_SOLID = 0x80000000
 
 LBM_FAMILY_AUTO, LBM_FAMILY_SCALAR, LBM_FAMILY_VEC, LBM_FAMILY_TMA = 0, 1, 2, 3
+LBM_ABB_U_NODE, LBM_ABB_U_EXTRAP = 0, 1
 
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
-    "lbm_compact_size", "lbm_compact_bind",
-    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
+    "lbm_compact_size", "lbm_compact_bind", "lbm_set_abb_velocity", "lbm_get_abb_velocity",
+    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_probe_loss_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
     "unet_param_layout", "unet_workspace_size", "unet_pack_input", "unet_prepare_weights", "unet_forward",
@@ -91,6 +92,9 @@ def load():
                 "lbm_bind_geometry": [vp, vp],
                 "lbm_compact_size": [vp, C.c_int64, C.POINTER(C.c_size_t)],
                 "lbm_compact_bind": [vp, C.c_int64, vp, vp],
+                "lbm_set_abb_velocity": [vp, i32],
+                "lbm_get_abb_velocity": [vp, C.POINTER(C.c_int32)],
+                "lbm_probe_loss_grad": [vp, vp, C.c_int64, vp, vp, f64, vp, vp, vp, vp],
                 "lbm_forward": [vp, vp, vp, f64, vp, vp, vp],
                 "lbm_step": [vp, vp, vp, f64, vp, vp, i32, vp, vp],
                 "lbm_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
@@ -243,6 +247,16 @@ def lbm_compact_bind(plan: Plan, n_fluid: int, tables, stream=None) -> None:
     plan._tables = tables  # the plan reads the tables while it is bound to them
 
 
+def lbm_set_abb_velocity(plan: Plan, mode: int) -> None:
+    _check(load().lbm_set_abb_velocity(plan.handle, int(mode)), "lbm_set_abb_velocity")
+
+
+def lbm_get_abb_velocity(plan: Plan) -> int:
+    m = C.c_int32()
+    _check(load().lbm_get_abb_velocity(plan.handle, C.byref(m)), "lbm_get_abb_velocity")
+    return m.value
+
+
 def lbm_forward(plan: Plan, rho_in, tau, rho_out: float, f, ws, stream=None) -> None:
     _check(load().lbm_forward(plan.handle, _ptr(rho_in, torch.float64, plan.n_in), _ptr(tau, torch.float64, 1),
                               float(rho_out), _ptr(f, plan.dtype, plan.q * plan.N), _ptr(ws, torch.uint8),
@@ -279,6 +293,15 @@ def lbm_loss_grad_noalloc(plan: Plan, f, u_target, roi, loss, lam, stream=None) 
                                         _ptr(roi, torch.uint8, plan.N), _ptr(loss, torch.float64, 1),
                                         _ptr(lam, plan.dtype, plan.q * plan.N), _stream(stream)),
            "lbm_loss_grad_noalloc")
+
+
+def lbm_probe_loss_grad(plan: Plan, f, nodes, rho_target, weight: float, loss, lam, ws, stream=None) -> None:
+    n = 0 if nodes is None else int(nodes.numel())
+    _check(load().lbm_probe_loss_grad(plan.handle, _ptr(f, plan.dtype, plan.q * plan.N), n,
+                                      _ptr(nodes, torch.int64, n) if n else None,
+                                      _ptr(rho_target, torch.float64, n) if n else None, float(weight),
+                                      _ptr(loss, torch.float64, 1), _ptr(lam, plan.dtype, plan.q * plan.N),
+                                      _ptr(ws, torch.uint8), _stream(stream)), "lbm_probe_loss_grad")
 
 
 def lbm_adjoint(plan: Plan, rho_in, tau, rho_out: float, lam, grad_rho_in, grad_tau, ws, stream=None) -> None:
@@ -410,6 +433,15 @@ class Solver:
         lam = self.new_state() if lam is None else lam
         self.run(lambda: lbm_loss_grad(self.plan, f, u_target, roi, loss, lam, self.ws))
         return loss, lam
+
+    def probe_loss_grad(self, f, nodes, rho_target, weight, loss, lam):
+        """Adds the density-probe term to loss and its seed to lam (after loss_grad)."""
+        self.run(lambda: lbm_probe_loss_grad(self.plan, f, nodes, rho_target, weight, loss, lam, self.ws))
+        return loss, lam
+
+    def set_abb_velocity(self, mode: int) -> None:
+        """LBM_ABB_U_NODE (default) or LBM_ABB_U_EXTRAP: where Eq. 6 takes its velocity."""
+        lbm_set_abb_velocity(self.plan, mode)
 
     def adjoint(self, rho_in, tau, rho_out, lam, g_in=None, g_tau=None):
         g_in = torch.zeros(self.plan.n_in, dtype=torch.float64, device=self.device) if g_in is None else g_in
