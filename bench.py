@@ -391,6 +391,23 @@ def c3_leg(device, time_limit):
     f_hat = s.forward(dv([wl.rho_out + d_hat]), dv([res.tau]), wl.rho_out)
     k_hat, _ = s.darcy(f_hat, dv([wl.rho_out + d_hat]), dv([res.tau]), wl.rho_out)
     k_ck = carman_kozeny(porosity, 2.0 * wl.r_max)
+    # the same inversion with density probes added to the loss: 16 fluid nodes on each of the
+    # sections x = 16, 48, 80, 112 observe rho (weight 10: both terms of similar size at the start)
+    rho_field, _ = s.macroscopic(f)
+    m = s.mask_field.cpu().numpy()
+    nodes = []
+    for xs in (16, 48, 80, 112):
+        fl = np.flatnonzero(m[:, :, xs].reshape(-1) == 0)
+        pick = fl[np.linspace(0, fl.size - 1, 16).astype(np.int64)]
+        zz, yy = np.unravel_index(pick, m.shape[:2])
+        nodes += list((zz * wl.ny + yy) * wl.nx + xs)
+    nodes_t = torch.as_tensor(np.array(nodes, np.int64), device=device)
+    rho_t = rho_field.reshape(-1)[nodes_t].contiguous()
+    inv_p = I.Inversion(s, u_target.contiguous(), wl.rho_out, tau0=1.0, invert_tau=True, probes=(nodes_t, rho_t, 10.0))
+    res_p = inv_p.run_lbfgs(max_evals=400, tol=1e-3, truth_delta=delta_true, truth_tau=tau_true, time_limit=time_limit)
+    with_probes = {"probes": "64 fluid nodes on x = 16, 48, 80, 112, weight 10", "seconds": round(res_p.seconds, 2),
+                   "converged": bool(res_p.converged), "gradient_evaluations": inv_p.evaluations,
+                   "rel_err_delta": res_p.rel_err_inlet, "rel_err_nu": res_p.rel_err_nu}
     out = {"workload": "spheres128x64x64: D3Q19 BGK FP32 128x64x64 duct, Boolean spheres r 6, "
                        f"porosity {porosity:.4f} (target 0.45), T={wl.steps}, constant head + tau",
            "kernels": tuned["choice"], "layout": tuned.get("layout", "dense"),
@@ -401,8 +418,9 @@ def c3_leg(device, time_limit):
            "method": "L-BFGS on (delta / 1e-3, (tau - 0.5) / 0.1)", "start": "delta = 0, tau = 1.0",
            "darcy_k_truth": float(k_true.item()), "darcy_k_recovered": float(k_hat.item()),
            "darcy_k_rel_err": abs(float(k_hat.item()) - float(k_true.item())) / float(k_true.item()),
-           "carman_kozeny_k": k_ck, "k_over_k_ck": float(k_true.item()) / k_ck, "time_limit_s": time_limit}
-    del s, inv
+           "carman_kozeny_k": k_ck, "k_over_k_ck": float(k_true.item()) / k_ck, "time_limit_s": time_limit,
+           "with_density_probes": with_probes}
+    del s, inv, inv_p
     torch.cuda.empty_cache()
     return out
 

@@ -52,12 +52,14 @@ class Inversion:
     optionally, tau, against a target velocity field."""
 
     def __init__(self, solver: lbm.Solver, u_target, rho_out: float, theta0=None, tau0: float = 0.8,
-                 invert_tau: bool = False, lr: float = 0.02, lr_tau: float = 0.01, roi=None):
+                 invert_tau: bool = False, lr: float = 0.02, lr_tau: float = 0.01, roi=None, probes=None):
         p = solver.plan
         dev = solver.device
         self.s, self.rho_out, self.invert_tau = solver, float(rho_out), invert_tau
         self.u_target = u_target.contiguous()
         self.roi = roi
+        # probes = (node indices int64, observed densities float64, weight): the density-probe loss term
+        self.probes = probes
         self.lr, self.lr_tau = lr, lr_tau
         t0 = np.zeros(p.n_in) if theta0 is None else np.broadcast_to(np.asarray(theta0, np.float64), (p.n_in,))
         self.theta = torch.tensor(np.array(t0), dtype=torch.float64, device=dev)
@@ -76,11 +78,18 @@ class Inversion:
         self.g_tau = torch.zeros(1, dtype=torch.float64, device=dev)
         self.t = 0
 
+    def _loss_and_seed(self):
+        s, p, st = self.s, self.s.plan, self.s.stream
+        lbm.lbm_loss_grad(p, self.f, self.u_target, self.roi, self.loss, self.lam, s.ws, st)
+        if self.probes is not None:
+            nodes, rho_t, w = self.probes
+            lbm.lbm_probe_loss_grad(p, self.f, nodes, rho_t, w, self.loss, self.lam, s.ws, st)
+
     def enqueue_iteration(self):
         """One gradient evaluation and the Adam updates, enqueued on the solver's stream."""
         s, p, st = self.s, self.s.plan, self.s.stream
         lbm.lbm_forward(p, self.rho_in, self.tau, self.rho_out, self.f, s.ws, st)
-        lbm.lbm_loss_grad(p, self.f, self.u_target, self.roi, self.loss, self.lam, s.ws, st)
+        self._loss_and_seed()
         lbm.lbm_adjoint(p, self.rho_in, self.tau, self.rho_out, self.lam, self.g_in, self.g_tau, s.ws, st)
         self.t += 1
         lbm.lbm_adam_step(self.theta, self.m, self.v, self.g_in, self.rho_in, self.rho_out, INLET_SCALE, self.t,
@@ -134,7 +143,7 @@ class Inversion:
             self.rho_in.copy_(torch.from_numpy(rho), non_blocking=False)
             self.tau.fill_(tau)
         lbm.lbm_forward(p, self.rho_in, self.tau, self.rho_out, self.f, s.ws, st)
-        lbm.lbm_loss_grad(p, self.f, self.u_target, self.roi, self.loss, self.lam, s.ws, st)
+        self._loss_and_seed()
         lbm.lbm_adjoint(p, self.rho_in, self.tau, self.rho_out, self.lam, self.g_in, self.g_tau, s.ws, st)
         st.synchronize()
         g = self.g_in.cpu().numpy() * INLET_SCALE
