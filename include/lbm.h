@@ -281,6 +281,31 @@ LBM_API lbm_status lbm_probe_loss_grad(lbm_plan* plan, const void* d_f, int64_t 
                                        const double* d_rho_target, double weight, double* d_loss, void* d_lambda,
                                        void* d_ws, void* stream);
 
+/* Cubic-spline inlet profiles (section 3.1.3: the multi-parameter inversion
+ * imposes the inlet pressure as a cubic spline through a few inlet
+ * densities).  Knot values c[Kz][Ky] give
+ *   rho_in[z ny + y] = rho_out + sum_{b,a} Bz[z][b] By[y][a] c[b][a],
+ * By (Bz) the natural cubic spline basis over the rows (layers): column a is
+ * the spline through the a-th unit knot vector, knots evenly spaced at
+ * t_a = a (n - 1) / (K - 1), zero second derivative at both ends; K = 1 is a
+ * constant.  D2Q9 plans use Kz = 1 and Bz = {1}.
+ * lbm_spline_basis: host function, writes h_basis[n][n_knots] (row-major).
+ *   Errors: INVALID_ARG unless 1 <= n_knots <= n <= 2^20.
+ * lbm_spline_profile: d_by double[ny][ky], d_bz double[nz][kz], d_knots
+ *   double[kz][ky] -> d_rho_in double[ny nz].
+ * lbm_spline_grad: d_grad_rho_in double[ny nz] (from lbm_adjoint) ->
+ *   d_grad_knots double[kz][ky] = Bz^T G By, each entry summed in a fixed
+ *   order (deterministic).
+ * Both need a plan with LBM_INLET_PROFILE and 1 <= ky <= ny, 1 <= kz <= nz
+ * (else INVALID_ARG); asynchronous on the stream. */
+LBM_API lbm_status lbm_spline_basis(int32_t n_knots, int32_t n, double* h_basis);
+LBM_API lbm_status lbm_spline_profile(const lbm_plan* plan, int32_t ky, int32_t kz, const double* d_by,
+                                      const double* d_bz, const double* d_knots, double rho_out, double* d_rho_in,
+                                      void* stream);
+LBM_API lbm_status lbm_spline_grad(const lbm_plan* plan, int32_t ky, int32_t kz, const double* d_by,
+                                   const double* d_bz, const double* d_grad_rho_in, double* d_grad_knots,
+                                   void* stream);
+
 /* Reverse sweep from lambda^T to t = 0 through the checkpoints left in d_ws
  * by the last lbm_forward with the same parameters: recompute each segment,
  * then run the adjoint step backwards through it.

@@ -555,6 +555,35 @@ lbm_status lbm_probe_loss_grad(lbm_plan* p, const void* d_f, int64_t n_probe, co
                         reinterpret_cast<uint32_t*>(bytes(d_ws) + p->ws.status), static_cast<cudaStream_t>(stream));
 }
 
+lbm_status lbm_spline_basis(int32_t n_knots, int32_t n, double* h_basis)
+{
+    if (!h_basis || n < 1 || n_knots < 1 || n_knots > n || n > (1 << 20)) return LBM_ERR_INVALID_ARG;
+    spline_basis_host(n_knots, n, h_basis);
+    return LBM_OK;
+}
+
+static bool spline_args_ok(const lbm_plan* p, int32_t ky, int32_t kz)
+{
+    return p && p->desc.inlet_kind == LBM_INLET_PROFILE && ky >= 1 && kz >= 1 && ky <= p->info.geo.ny &&
+           kz <= p->info.geo.nz;
+}
+
+lbm_status lbm_spline_profile(const lbm_plan* p, int32_t ky, int32_t kz, const double* d_by, const double* d_bz,
+                              const double* d_knots, double rho_out, double* d_rho_in, void* stream)
+{
+    if (!spline_args_ok(p, ky, kz) || !d_by || !d_bz || !d_knots || !d_rho_in) return LBM_ERR_INVALID_ARG;
+    return spline_profile_launch(p->info, ky, kz, d_by, d_bz, d_knots, rho_out, d_rho_in,
+                                 static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_spline_grad(const lbm_plan* p, int32_t ky, int32_t kz, const double* d_by, const double* d_bz,
+                           const double* d_grad_rho_in, double* d_grad_knots, void* stream)
+{
+    if (!spline_args_ok(p, ky, kz) || !d_by || !d_bz || !d_grad_rho_in || !d_grad_knots) return LBM_ERR_INVALID_ARG;
+    return spline_grad_launch(p->info, ky, kz, d_by, d_bz, d_grad_rho_in, d_grad_knots,
+                              static_cast<cudaStream_t>(stream));
+}
+
 lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
                        const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream)
 {

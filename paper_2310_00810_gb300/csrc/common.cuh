@@ -227,6 +227,12 @@ lbm_status probe_launch(const PlanInfo& p, const void* f, long long n_probe, con
                         const double* rho_target, double weight, double* d_loss, void* lambda, uint32_t* status,
                         cudaStream_t s);
 
+void spline_basis_host(int K, int n, double* basis);
+lbm_status spline_profile_launch(const PlanInfo& p, int ky, int kz, const double* by, const double* bz,
+                                 const double* c, double rho_out, double* rho_in, cudaStream_t s);
+lbm_status spline_grad_launch(const PlanInfo& p, int ky, int kz, const double* by, const double* bz,
+                              const double* g, double* gc, cudaStream_t s);
+
 bool persist_ok(const PlanInfo& p);
 lbm_status forward_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau, cudaStream_t s);
 lbm_status reverse_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau,

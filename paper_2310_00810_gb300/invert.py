@@ -52,9 +52,19 @@ class Inversion:
     optionally, tau, against a target velocity field."""
 
     def __init__(self, solver: lbm.Solver, u_target, rho_out: float, theta0=None, tau0: float = 0.8,
-                 invert_tau: bool = False, lr: float = 0.02, lr_tau: float = 0.01, roi=None, probes=None):
+                 invert_tau: bool = False, lr: float = 0.02, lr_tau: float = 0.01, roi=None, probes=None,
+                 spline=None):
         p = solver.plan
         dev = solver.device
+        # spline = (Ky, Kz): run_lbfgs inverts the knot values of a cubic-spline profile
+        # (lbm_spline_profile / lbm_spline_grad) instead of one density per inlet node
+        self.spline = None
+        if spline is not None:
+            ky, kz = int(spline[0]), int(spline[1])
+            by, bz = lbm.lbm_spline_basis(ky, p.ny), lbm.lbm_spline_basis(kz, p.nz)
+            self.spline = (torch.as_tensor(by, device=dev), torch.as_tensor(bz, device=dev), np.kron(bz, by))
+            self.knots = torch.zeros(ky * kz, dtype=torch.float64, device=dev)
+            self.g_knots = torch.zeros(ky * kz, dtype=torch.float64, device=dev)
         self.s, self.rho_out, self.invert_tau = solver, float(rho_out), invert_tau
         self.u_target = u_target.contiguous()
         self.roi = roi
@@ -136,32 +146,45 @@ class Inversion:
     def _evaluate(self, x: np.ndarray):
         """Loss and gradient with respect to the scaled parameters x (one gradient evaluation)."""
         s, p, st = self.s, self.s.plan, self.s.stream
-        n = p.n_in
-        rho = self.rho_out + INLET_SCALE * x[:n]
+        n = self._n_par()
         tau = TAU_OFFSET + TAU_SCALE * x[n] if self.invert_tau else float(self.tau_fixed)
         with torch.cuda.stream(st):
-            self.rho_in.copy_(torch.from_numpy(rho), non_blocking=False)
+            if self.spline is None:
+                self.rho_in.copy_(torch.from_numpy(self.rho_out + INLET_SCALE * x[:n]), non_blocking=False)
+            else:
+                self.knots.copy_(torch.from_numpy(INLET_SCALE * x[:n]), non_blocking=False)
             self.tau.fill_(tau)
+        if self.spline is not None:
+            lbm.lbm_spline_profile(p, self.spline[0], self.spline[1], self.knots, self.rho_out, self.rho_in, st)
         lbm.lbm_forward(p, self.rho_in, self.tau, self.rho_out, self.f, s.ws, st)
         self._loss_and_seed()
         lbm.lbm_adjoint(p, self.rho_in, self.tau, self.rho_out, self.lam, self.g_in, self.g_tau, s.ws, st)
+        if self.spline is not None:
+            lbm.lbm_spline_grad(p, self.spline[0], self.spline[1], self.g_in, self.g_knots, st)
         st.synchronize()
-        g = self.g_in.cpu().numpy() * INLET_SCALE
+        g = (self.g_in if self.spline is None else self.g_knots).cpu().numpy() * INLET_SCALE
         if self.invert_tau:
             g = np.concatenate([g, self.g_tau.cpu().numpy() * TAU_SCALE])
         return float(self.loss.cpu().item()), g
+
+    def _n_par(self) -> int:
+        return self.s.plan.n_in if self.spline is None else int(self.knots.numel())
+
+    def _delta(self, x_in: np.ndarray) -> np.ndarray:
+        """delta = rho_in - rho_out per inlet node for the inlet parameters x_in."""
+        return INLET_SCALE * (x_in if self.spline is None else self.spline[2] @ x_in)
 
     def run_lbfgs(self, max_evals: int = 400, tol: float = 1e-3, truth_delta=None, truth_tau=None,
                   memory: int = 20, time_limit: float | None = None) -> InversionResult:
         """L-BFGS on the scaled parameters until the relative error on delta
         (and nu) is <= tol, or max_evals gradient evaluations / time_limit."""
         p = self.s.plan
-        n = p.n_in
+        n = self._n_par()
         self.tau_fixed = float(self.tau.cpu().item())
-        x = self.theta.cpu().numpy().copy()
+        x = self.theta.cpu().numpy().copy() if self.spline is None else np.zeros(n)
         if self.invert_tau:
             x = np.concatenate([x, self.theta_tau.cpu().numpy()])
-        td = None if truth_delta is None else np.broadcast_to(np.asarray(truth_delta, np.float64), (n,))
+        td = None if truth_delta is None else np.broadcast_to(np.asarray(truth_delta, np.float64), (p.n_in,))
         nu_true = None if truth_tau is None else (truth_tau - 0.5) / 3.0
         torch.cuda.synchronize(self.s.device)
         t_start = time.perf_counter()
@@ -211,7 +234,7 @@ class Inversion:
             x, f, g = x + sv, f1, g1
             losses.append(f)
             if td is not None:
-                e_in = float(np.linalg.norm(INLET_SCALE * x[:n] - td) / np.linalg.norm(td))
+                e_in = float(np.linalg.norm(self._delta(x[:n]) - td) / np.linalg.norm(td))
                 if nu_true is not None and self.invert_tau:
                     e_nu = float(abs(TAU_SCALE * x[n] / 3.0 - nu_true) / nu_true)
                 errs.append((e_in, e_nu))
@@ -221,10 +244,10 @@ class Inversion:
             if time_limit is not None and time.perf_counter() - t_start > time_limit:
                 break
         secs = time.perf_counter() - t_start
-        self.theta.copy_(torch.from_numpy(x[:n]))
+        self.theta.copy_(torch.from_numpy(self._delta(x[:n]) / INLET_SCALE))
         if self.invert_tau:
             self.theta_tau.fill_(float(x[n]))
         self.evaluations = evals
-        return InversionResult(it, secs, converged, self.rho_out + INLET_SCALE * x[:n],
+        return InversionResult(it, secs, converged, self.rho_out + self._delta(x[:n]),
                                TAU_OFFSET + TAU_SCALE * x[n] if self.invert_tau else self.tau_fixed, e_in, e_nu,
                                losses, errs)

@@ -32,7 +32,8 @@ LBM_ABB_U_NODE, LBM_ABB_U_EXTRAP = 0, 1
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
     "lbm_compact_size", "lbm_compact_bind", "lbm_set_abb_velocity", "lbm_get_abb_velocity",
-    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_probe_loss_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
+    "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_probe_loss_grad", "lbm_spline_basis",
+    "lbm_spline_profile", "lbm_spline_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
     "unet_param_layout", "unet_workspace_size", "unet_pack_input", "unet_prepare_weights", "unet_forward",
@@ -95,6 +96,9 @@ def load():
                 "lbm_set_abb_velocity": [vp, i32],
                 "lbm_get_abb_velocity": [vp, C.POINTER(C.c_int32)],
                 "lbm_probe_loss_grad": [vp, vp, C.c_int64, vp, vp, f64, vp, vp, vp, vp],
+                "lbm_spline_basis": [i32, i32, vp],
+                "lbm_spline_profile": [vp, i32, i32, vp, vp, vp, f64, vp, vp],
+                "lbm_spline_grad": [vp, i32, i32, vp, vp, vp, vp, vp],
                 "lbm_forward": [vp, vp, vp, f64, vp, vp, vp],
                 "lbm_step": [vp, vp, vp, f64, vp, vp, i32, vp, vp],
                 "lbm_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
@@ -302,6 +306,30 @@ def lbm_probe_loss_grad(plan: Plan, f, nodes, rho_target, weight: float, loss, l
                                       _ptr(rho_target, torch.float64, n) if n else None, float(weight),
                                       _ptr(loss, torch.float64, 1), _ptr(lam, plan.dtype, plan.q * plan.N),
                                       _ptr(ws, torch.uint8), _stream(stream)), "lbm_probe_loss_grad")
+
+
+def lbm_spline_basis(n_knots: int, n: int):
+    """Host basis B[n, n_knots] of the natural cubic spline (a float64 numpy array)."""
+    import numpy as np
+
+    out = np.zeros((int(n), int(n_knots)), np.float64)
+    _check(load().lbm_spline_basis(int(n_knots), int(n), out.ctypes.data_as(C.c_void_p)), "lbm_spline_basis")
+    return out
+
+
+def lbm_spline_profile(plan: Plan, by, bz, knots, rho_out: float, rho_in, stream=None) -> None:
+    ky, kz = by.shape[1], bz.shape[1]
+    _check(load().lbm_spline_profile(plan.handle, ky, kz, _ptr(by, torch.float64, plan.ny * ky),
+                                     _ptr(bz, torch.float64, plan.nz * kz), _ptr(knots, torch.float64, ky * kz),
+                                     float(rho_out), _ptr(rho_in, torch.float64, plan.n_in), _stream(stream)),
+           "lbm_spline_profile")
+
+
+def lbm_spline_grad(plan: Plan, by, bz, grad_rho_in, grad_knots, stream=None) -> None:
+    ky, kz = by.shape[1], bz.shape[1]
+    _check(load().lbm_spline_grad(plan.handle, ky, kz, _ptr(by, torch.float64, plan.ny * ky),
+                                  _ptr(bz, torch.float64, plan.nz * kz), _ptr(grad_rho_in, torch.float64, plan.n_in),
+                                  _ptr(grad_knots, torch.float64, ky * kz), _stream(stream)), "lbm_spline_grad")
 
 
 def lbm_adjoint(plan: Plan, rho_in, tau, rho_out: float, lam, grad_rho_in, grad_tau, ws, stream=None) -> None:

@@ -73,3 +73,17 @@ def test_calls_without_geometry_are_rejected(lib):
     st = lib.lbm_forward(p.handle, None, None, 1.0, None, None, None)
     assert st == lbm.LBM_ERR_INVALID_ARG
     assert lbm.lbm_error_string(lbm.LBM_ERR_NONFINITE) == "non-finite loss or gradient"
+
+
+def test_spline_basis_host_call_matches_the_oracle(lib):
+    """lbm_spline_basis is host code: it runs here, against the spline oracle."""
+    import numpy as np
+
+    from oracle import spline_oracle as S
+
+    for K, n in [(1, 5), (2, 9), (3, 17), (6, 64), (16, 128), (33, 256), (7, 7)]:
+        np.testing.assert_allclose(lbm.lbm_spline_basis(K, n), S.basis(K, n), rtol=0, atol=1e-13)
+    for K, n in [(0, 5), (6, 5), (2, 0)]:
+        with pytest.raises(lbm.LBMError) as e:
+            lbm.lbm_spline_basis(K, n)
+        assert e.value.status == lbm.LBM_ERR_INVALID_ARG
