@@ -32,6 +32,7 @@ from . import lbm
 
 INLET_SCALE = 1e-3
 TAU_OFFSET, TAU_SCALE = 0.5, 0.1
+TAU_MIN_THETA = 0.05  # the L-BFGS steps keep tau >= 0.505
 
 
 @dataclasses.dataclass
@@ -214,16 +215,28 @@ class Inversion:
                 S, Y = [], []
                 d = -g / max(np.linalg.norm(g), 1e-300)
                 d0 = g @ d
-            t = 1.0
+            # the step keeps tau above 1/2 (nu > 0): beyond it the lattice is unstable
+            t_max = np.inf
+            if self.invert_tau and d[n] < 0:
+                t_max = max((x[n] - TAU_MIN_THETA) / -d[n], 0.0)
+            t = min(1.0, t_max)
             f1, g1 = self._evaluate(x + t * d)
             evals += 1
             d1 = g1 @ d
-            if d1 > d0:  # secant step on the directional derivative (exact for a quadratic)
-                t_new = -d0 / (d1 - d0) * t
+            if np.isfinite(f1) and d1 > d0:  # secant step on the directional derivative (exact for a quadratic)
+                t_new = min(-d0 / (d1 - d0) * t, t_max)
                 if abs(t_new - t) > 1e-12 * t and evals < max_evals:
-                    t = t_new
-                    f1, g1 = self._evaluate(x + t * d)
+                    f2, g2 = self._evaluate(x + t_new * d)
                     evals += 1
+                    if np.isfinite(f2) and f2 <= f1:
+                        t, f1, g1 = t_new, f2, g2
+            # halve the step while the loss is non-finite or has grown (not for a quadratic)
+            while not (np.isfinite(f1) and f1 <= f + 1e-6 * abs(f)) and evals < max_evals and t > 1e-6:
+                t *= 0.5
+                f1, g1 = self._evaluate(x + t * d)
+                evals += 1
+            if not np.isfinite(f1):
+                break
             sv, yv = t * d, g1 - g
             if yv @ sv > 0:
                 S.append(sv)
