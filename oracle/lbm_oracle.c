@@ -27,6 +27,14 @@
  * Density probes (an optional second loss term): w sum_p (rho(x_p) - rho_p)^2
  * over a list of probe nodes, with its seed dL/df_k = 2 w (rho - rho_p).
  *
+ * MRT collision (section 3.4, Eq. 16-18; D2Q9 only, an option set by
+ * set_collision): f* = f - M^{-1} S M (f - f^eq), M the moment matrix of
+ * Eq. 18 (rows rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy; the printed
+ * p_xy row |c_x c_y| is read as the orthogonal c_x c_y), m^eq = M f^eq with
+ * f^eq of Eq. 5, S = diag(0, s_e, s_eps, 0, s_q, 0, s_q, 1/tau, 1/tau) (the
+ * conserved moments have m = m^eq, so their rates do not matter).  S = I / tau
+ * is BGK.
+ *
  * Loss (Eq. 7, Eq. 15, and the compute_loss kernel of section 2.2), taken at
  * the final step only; default is the vector mismatch sum |u - u_t|^2,
  * optional is the paper's (|u| - |u_t|)^2.
@@ -248,22 +256,99 @@ static long wall_partner(const domain* D, int x, long n)
     return is_solid(D, m) ? -1 : m;
 }
 
+/* ------------------------------------------------------------- MRT */
+
+enum { COLL_BGK = 0, COLL_MRT = 1 };
+static int g_coll = COLL_BGK;
+static double g_s_e = 1.0, g_s_eps = 1.0, g_s_q = 1.0;
+
+int SYM(set_collision)(int mode, double s_e, double s_eps, double s_q)
+{
+    if (mode != COLL_BGK && mode != COLL_MRT) return -1;
+    g_coll = mode;
+    g_s_e = s_e;
+    g_s_eps = s_eps;
+    g_s_q = s_q;
+    return 0;
+}
+
+/* Row r of the D2Q9 moment matrix at direction j, from its polynomial in c_j
+ * (Gram-Schmidt over the lattice, the construction behind Eq. 18). */
+static double mrt_row(const lattice* L, int r, int j)
+{
+    double cx = L->c[j][0], cy = L->c[j][1], c2 = cx * cx + cy * cy;
+    switch (r) {
+    case 0: return 1.0;
+    case 1: return -4.0 + 3.0 * c2;
+    case 2: return 4.0 - 10.5 * c2 + 4.5 * c2 * c2;
+    case 3: return cx;
+    case 4: return (-5.0 + 3.0 * c2) * cx;
+    case 5: return cy;
+    case 6: return (-5.0 + 3.0 * c2) * cy;
+    case 7: return cx * cx - cy * cy;
+    default: return cx * cy;
+    }
+}
+
+/* Relaxation rate of moment r for omega = 1/tau. */
+static real_t mrt_rate(int r, real_t omega)
+{
+    switch (r) {
+    case 1: return g_s_e;
+    case 2: return g_s_eps;
+    case 4:
+    case 6: return g_s_q;
+    case 7:
+    case 8: return omega;
+    default: return 0.0;
+    }
+}
+
+/* |row r|^2 = sum_j M_rj^2 (M M^T is diagonal, so M^{-1} = M^T diag(1/|row|^2)). */
+static double mrt_norm2(const lattice* L, int r)
+{
+    double s = 0;
+    for (int j = 0; j < 9; ++j) s += mrt_row(L, r, j) * mrt_row(L, r, j);
+    return s;
+}
+
 /* --------------------------------------------------------- collision */
 
-/* BGK collision alone (Eq. 4-5) at every node of an unstructured array of
- * n nodes: f_out_i = f_i - (f_i - f^eq_i(rho, u)) / tau. */
+/* Post-collision populations of one node (BGK, Eq. 4-5, or MRT, Eq. 16). */
+static void collide_node(const lattice* L, const real_t* f, long N, long n, real_t tau, real_t* out, long ostride,
+                         long on)
+{
+    real_t rho, u[3];
+    moments(L, f, N, n, &rho, u);
+    if (g_coll == COLL_MRT && L->q == 9) {
+        real_t d[9], dm[9];
+        for (int j = 0; j < 9; ++j) d[j] = f[(long)j * N + n] - feq(L, j, rho, u);
+        for (int r = 0; r < 9; ++r) {
+            real_t m = 0;
+            for (int j = 0; j < 9; ++j) m += mrt_row(L, r, j) * d[j];
+            dm[r] = mrt_rate(r, 1.0 / tau) * m / mrt_norm2(L, r);
+        }
+        for (int j = 0; j < 9; ++j) {
+            real_t c = 0;
+            for (int r = 0; r < 9; ++r) c += mrt_row(L, r, j) * dm[r];
+            out[(long)j * ostride + on] = f[(long)j * N + n] - c;
+        }
+        return;
+    }
+    for (int i = 0; i < L->q; ++i) {
+        real_t fi = f[(long)i * N + n];
+        out[(long)i * ostride + on] = fi - (fi - feq(L, i, rho, u)) / tau;
+    }
+}
+
+/* The collision alone (BGK, Eq. 4-5: f_out_i = f_i - (f_i - f^eq_i) / tau,
+ * or MRT, Eq. 16) at every node of an unstructured array of n nodes. */
 int SYM(collide)(int q, long n_nodes, const real_t* f_in, real_t* f_out, const real_t* tau)
 {
     lattice L;
     if (lattice_make(q, &L)) return -1;
-    for (long n = 0; n < n_nodes; ++n) {
-        real_t rho, u[3];
-        moments(&L, f_in, n_nodes, n, &rho, u);
-        for (int i = 0; i < q; ++i) {
-            real_t fi = f_in[(long)i * n_nodes + n];
-            f_out[(long)i * n_nodes + n] = fi - (fi - feq(&L, i, rho, u)) / *tau;
-        }
-    }
+    if (g_coll == COLL_MRT && q != 9) return -4;
+    for (long n = 0; n < n_nodes; ++n) collide_node(&L, f_in, n_nodes, n, *tau, f_out, n_nodes, n);
     return 0;
 }
 
@@ -290,6 +375,7 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
 {
     lattice L;
     if (lattice_make(q, &L)) return -1;
+    if (g_coll == COLL_MRT && q != 9) return -4;
     domain D = {nx, ny, nz, (long)nx * ny * nz, mask};
     long N = D.n;
     real_t* fstar = (real_t*)malloc(sizeof(real_t) * (size_t)q * (size_t)N);
@@ -307,10 +393,7 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
         real_t rho, u[3];
         moments(&L, f_in, N, n, &rho, u);
         for (int a = 0; a < 3; ++a) uvel[a * N + n] = u[a];
-        for (int i = 0; i < q; ++i) {
-            real_t fi = f_in[(long)i * N + n];
-            fstar[(long)i * N + n] = fi - (fi - feq(&L, i, rho, u)) / *tau;
-        }
+        collide_node(&L, f_in, N, n, *tau, fstar, N, n);
     }
 
     /* streaming with boundaries (each node writes only its own populations) */
@@ -540,10 +623,12 @@ int orc_links(int q, int nx, int ny, int nz, const uint8_t* mask, uint32_t* link
  *     post-collision population it was copied from (with the sign of Eq. 6
  *     for anti-bounce-back links), and the Eq. 6 source contributes to
  *     rho_w and to the boundary node's u;
- *  2. collision: f*_j = (1 - omega) f_j + omega f^eq_j(rho(f), u(f)),
- *     so dL/df_k = (1 - omega) mu_k + rhobar + sum_a ubar_a (c_ka - u_a)/rho
- *     with rhobar = sum_j mu_j omega df^eq_j/drho and
- *     ubar_a = (Eq. 6 part) + sum_j mu_j omega df^eq_j/du_a. */
+ *  2. collision: f*_j = f_j - sum_k A_jk (f_k - f^eq_k(rho(f), u(f))), with
+ *     A = omega I (BGK) or A = M^{-1} S M (MRT), so with nu = A^T mu
+ *     dL/df_k = mu_k - nu_k + rhobar + sum_a ubar_a (c_ka - u_a)/rho
+ *     with rhobar = sum_j nu_j df^eq_j/drho and
+ *     ubar_a = (Eq. 6 part) + sum_j nu_j df^eq_j/du_a; dL/domega is
+ *     -mu . dA/domega (f - f^eq). */
 int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const double* f_t,
                      const double* lam_next, double* lam_out, const double* rho_in, int inlet_profile,
                      const double* rho_out, const double* tau, double* g_rho_in, double* g_omega)
@@ -645,19 +730,39 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
         moments(&L, f_t, N, n, &rho, u);
         double uu = dot_uu(&L, u);
         double rhobar = 0, ub[3] = {ubar[n], ubar[N + n], ubar[2 * N + n]};
+        double nu[19];
+        if (g_coll == COLL_MRT && q == 9) {
+            /* nu = M^T S D^{-1} M mu; dL/domega from the two stress moments */
+            double mm[9], md[9];
+            for (int r = 0; r < 9; ++r) {
+                mm[r] = md[r] = 0;
+                for (int j = 0; j < 9; ++j) {
+                    mm[r] += mrt_row(&L, r, j) * mu[(long)j * N + n];
+                    md[r] += mrt_row(&L, r, j) * (f_t[(long)j * N + n] - feq(&L, j, rho, u));
+                }
+            }
+            for (int r = 7; r < 9; ++r) gw -= mm[r] * md[r] / mrt_norm2(&L, r);
+            for (int j = 0; j < 9; ++j) {
+                nu[j] = 0;
+                for (int r = 0; r < 9; ++r) nu[j] += mrt_row(&L, r, j) * mrt_rate(r, omega) * mm[r] / mrt_norm2(&L, r);
+            }
+        } else {
+            for (int j = 0; j < q; ++j) {
+                double m = mu[(long)j * N + n];
+                gw += m * (feq(&L, j, rho, u) - f_t[(long)j * N + n]);
+                nu[j] = omega * m;
+            }
+        }
         for (int j = 0; j < q; ++j) {
-            double m = mu[(long)j * N + n];
             double cu = dot_cu(&L, j, u);
             double P = 1.0 + cu * INV_CS2 + cu * cu * INV_2CS4 - uu * INV_2CS2;
-            double fe = L.w[j] * rho * P;
-            gw += m * (fe - f_t[(long)j * N + n]);
-            rhobar += m * omega * L.w[j] * P;
+            rhobar += nu[j] * L.w[j] * P;
             for (int a = 0; a < L.d; ++a)
-                ub[a] += m * omega * L.w[j] * rho *
+                ub[a] += nu[j] * L.w[j] * rho *
                          (INV_CS2 * L.c[j][a] + 2.0 * INV_2CS4 * cu * L.c[j][a] - 2.0 * INV_2CS2 * u[a]);
         }
         for (int k = 0; k < q; ++k) {
-            double s = (1.0 - omega) * mu[(long)k * N + n] + rhobar;
+            double s = mu[(long)k * N + n] - nu[k] + rhobar;
             for (int a = 0; a < L.d; ++a) s += ub[a] * ((double)L.c[k][a] - u[a]) / rho;
             lam_out[(long)k * N + n] = s;
         }

@@ -92,6 +92,35 @@ def set_abb_velocity(mode: int) -> None:
         _check(fn(int(mode)), "set_abb_velocity")
 
 
+COLL_BGK, COLL_MRT = 0, 1
+
+
+def set_collision(mode: int, s_e: float = 1.0, s_eps: float = 1.0, s_q: float = 1.0) -> None:
+    """BGK (default) or the D2Q9 MRT operator of Eq. 16-18 with the free
+    rates s_e, s_eps, s_q (the stress rates are 1/tau); applies to every later
+    call, in both builds."""
+    for cs in (False, True):
+        lib = _lib(cs)
+        fn = lib.orc_cs_set_collision if cs else lib.orc_set_collision
+        fn.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+        _check(fn(int(mode), float(s_e), float(s_eps), float(s_q)), "set_collision")
+
+
+class collision:
+    """``with collision(COLL_MRT, s_e, s_eps, s_q): ...`` sets the operator for the block."""
+
+    def __init__(self, mode: int, s_e: float = 1.0, s_eps: float = 1.0, s_q: float = 1.0):
+        self.args = (mode, s_e, s_eps, s_q)
+
+    def __enter__(self):
+        set_collision(*self.args)
+        return self
+
+    def __exit__(self, *exc):
+        set_collision(COLL_BGK)
+        return False
+
+
 class abb_velocity:
     """``with abb_velocity(UW_EXTRAP): ...`` sets the Eq. 6 velocity for the block."""
 
