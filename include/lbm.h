@@ -144,6 +144,24 @@ enum { LBM_ABB_U_NODE = 0, LBM_ABB_U_EXTRAP = 1 };
 LBM_API lbm_status lbm_set_abb_velocity(lbm_plan* plan, int32_t mode);
 LBM_API lbm_status lbm_get_abb_velocity(const lbm_plan* plan, int32_t* mode);
 
+/* Collision operator.  LBM_COLLISION_BGK (default): Eq. 4-5.
+ * LBM_COLLISION_MRT (section 3.4, Eq. 16-18; D2Q9 plans only): f* = f -
+ * M^{-1} S M (f - f^eq), M the moment matrix of Eq. 18 (rows rho, e,
+ * epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy; the printed p_xy row |c_x c_y| is
+ * read as the orthogonal c_x c_y), m^eq = M f^eq with f^eq of Eq. 5, and
+ * S = diag(-, s_e, s_eps, -, s_q, -, s_q, 1/tau, 1/tau): the stress rates follow
+ * tau (so dL/dtau is the derivative through them alone), the free rates s_e,
+ * s_eps, s_q are fixed here (each in (0, 2); the conserved moments need no
+ * rate).  The dense layout runs the one-node-per-thread kernels while MRT is
+ * set; the fluid-only layout keeps its kernels.  Batches use BGK.  Cached
+ * CUDA graphs are dropped on a change.  Errors: INVALID_ARG for an unknown
+ * mode or a rate outside (0, 2); UNSUPPORTED for MRT on a D3Q19 plan.
+ * lbm_get_collision writes the mode and, if rates != NULL, the three rates
+ * (zeros under BGK). */
+enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_MRT = 1 };
+LBM_API lbm_status lbm_set_collision(lbm_plan* plan, int32_t mode, double s_e, double s_eps, double s_q);
+LBM_API lbm_status lbm_get_collision(const lbm_plan* plan, int32_t* mode, double* rates);
+
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
  * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and two
  * segment buffers, adjoint ping-pong states and FP64 reduction slots. */

@@ -90,33 +90,45 @@ __global__ void __launch_bounds__(kStepThreads)
             }
         }
 
-        // 3. transpose of the collision
-        T A = 0, B[3] = {T(0), T(0), T(0)}, domT = 0;
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            const T cu = cdot<Q, T>(j, u);
-            const T wj = T(L::w(j));
-            const T P = T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
-            const T feq = wj * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
-            domT += mu[j] * (feq - f[j]);
-            A += mu[j] * wj * P;
-#pragma unroll
-            for (int a = 0; a < L::D; ++a)
-                B[a] += mu[j] * wj * rho * (T(3 * L::c(j, a)) + T(9) * cu * T(L::c(j, a)) - T(3) * u[a]);
+        // 3. transpose of the collision (BGK here, MRT in adjoint_collision_mrt)
+        T lamv[Q], domT = 0;
+        bool mrt_done = false;
+        if constexpr (Q == 9) {
+            if (bc.mrt) {
+                domT = adjoint_collision_mrt<T>(f, mu, drho, rho, u, G, omega, mrt_rates(bc.status), lamv);
+                mrt_done = true;
+            }
         }
-        const T inv = T(1) / rho;
-        T Bt[3];
+        if (!mrt_done) {
+            T A = 0, B[3] = {T(0), T(0), T(0)};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) Bt[a] = (omega * B[a] + G[a]) * inv;
-        const T base = omega * A;
-        const T keep = T(1) - omega;
+            for (int j = 0; j < Q; ++j) {
+                const T cu = cdot<Q, T>(j, u);
+                const T wj = T(L::w(j));
+                const T P = T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu;
+                const T feq = wj * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+                domT += mu[j] * (feq - f[j]);
+                A += mu[j] * wj * P;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            T s = keep * mu[k] + base;
+                for (int a = 0; a < L::D; ++a)
+                    B[a] += mu[j] * wj * rho * (T(3 * L::c(j, a)) + T(9) * cu * T(L::c(j, a)) - T(3) * u[a]);
+            }
+            const T inv = T(1) / rho;
+            T Bt[3];
 #pragma unroll
-            for (int a = 0; a < L::D; ++a) s += Bt[a] * (T(L::c(k, a)) - u[a]);
-            lam_out[(long long)k * N + n] = s;
+            for (int a = 0; a < 3; ++a) Bt[a] = (omega * B[a] + G[a]) * inv;
+            const T base = omega * A;
+            const T keep = T(1) - omega;
+#pragma unroll
+            for (int k = 0; k < Q; ++k) {
+                T sk = keep * mu[k] + base;
+#pragma unroll
+                for (int a = 0; a < L::D; ++a) sk += Bt[a] * (T(L::c(k, a)) - u[a]);
+                lamv[k] = sk;
+            }
         }
+#pragma unroll
+        for (int k = 0; k < Q; ++k) lam_out[(long long)k * N + n] = lamv[k];
 
         // 4. parameter gradients
         dom = (double)domT;
@@ -201,8 +213,9 @@ lbm_status adjoint_launch(const PlanInfo& plan, int t_is_zero, const void* gprev
                           const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
     if (plan.cmp.nf) return adjoint_launch_cmp(plan, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
-    if (bc.uw_extrap) {
-        // the extrapolated u_w runs on the one-node-per-thread kernels plus its reverse pass
+    if (bc.uw_extrap || bc.mrt) {
+        // the extrapolated u_w and the MRT collision run on the one-node-per-thread kernels
+        // (plus, for u_w, its reverse pass)
         const PlanInfo p = with_family(plan, LBM_FAMILY_SCALAR);
         if (p.q == 9 && p.prec == 4) launch<9, float>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
         else if (p.q == 9 && p.prec == 8)
@@ -212,7 +225,7 @@ lbm_status adjoint_launch(const PlanInfo& plan, int t_is_zero, const void* gprev
         else if (p.q == 19 && p.prec == 8)
             launch<19, double>(p, t_is_zero, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
         else return LBM_ERR_UNSUPPORTED;
-        if (!t_is_zero) {
+        if (bc.uw_extrap && !t_is_zero) {
             if (p.q == 9 && p.prec == 4) launch_uw<9, float>(p, gprev, lam_in, lam_out, bc, grad_acc, s);
             else if (p.q == 9) launch_uw<9, double>(p, gprev, lam_in, lam_out, bc, grad_acc, s);
             else if (p.prec == 4) launch_uw<19, float>(p, gprev, lam_in, lam_out, bc, grad_acc, s);

@@ -117,6 +117,22 @@ bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 25
 
 unsigned char* bytes(void* ws) { return static_cast<unsigned char*>(ws); }
 
+// The MRT rates into the status section, where the kernels read them (Bc::mrt).
+__global__ void k_write_mrt_rates(uint32_t* status, float s_e, float s_eps, float s_q)
+{
+    float* r = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(status) + kMrtRates);
+    r[0] = s_e;
+    r[1] = s_eps;
+    r[2] = s_q;
+}
+
+lbm_status write_mrt_rates(const lbm_plan* p, const Bc& bc, cudaStream_t s)
+{
+    if (!p->info.mrt) return LBM_OK;
+    k_write_mrt_rates<<<1, 1, 0, s>>>(bc.status, p->info.mrt_rates[0], p->info.mrt_rates[1], p->info.mrt_rates[2]);
+    return cuda_status(cudaGetLastError());
+}
+
 Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
 {
     Bc bc;
@@ -125,6 +141,7 @@ Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
     bc.rho_out = rho_out;
     bc.status = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + p->ws.status);
     bc.uw_extrap = p->info.uw_extrap;
+    bc.mrt = p->info.mrt;
     return bc;
 }
 
@@ -370,6 +387,31 @@ lbm_status lbm_get_abb_velocity(const lbm_plan* p, int32_t* mode)
     return LBM_OK;
 }
 
+lbm_status lbm_set_collision(lbm_plan* p, int32_t mode, double s_e, double s_eps, double s_q)
+{
+    if (!p || (mode != LBM_COLLISION_BGK && mode != LBM_COLLISION_MRT)) return LBM_ERR_INVALID_ARG;
+    if (mode == LBM_COLLISION_MRT) {
+        if (p->info.q != 9) return LBM_ERR_UNSUPPORTED;
+        auto ok = [](double r) { return r > 0.0 && r < 2.0; };
+        if (!ok(s_e) || !ok(s_eps) || !ok(s_q)) return LBM_ERR_INVALID_ARG;
+        p->info.mrt_rates[0] = (float)s_e;
+        p->info.mrt_rates[1] = (float)s_eps;
+        p->info.mrt_rates[2] = (float)s_q;
+    }
+    p->info.mrt = mode == LBM_COLLISION_MRT ? 1 : 0;
+    drop_graphs(p);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_collision(const lbm_plan* p, int32_t* mode, double* rates)
+{
+    if (!p || !mode) return LBM_ERR_INVALID_ARG;
+    *mode = p->info.mrt ? LBM_COLLISION_MRT : LBM_COLLISION_BGK;
+    if (rates)
+        for (int i = 0; i < 3; ++i) rates[i] = p->info.mrt ? (double)p->info.mrt_rates[i] : 0.0;
+    return LBM_OK;
+}
+
 lbm_status lbm_workspace_size(const lbm_plan* p, size_t* bytes_out)
 {
     if (!p || !bytes_out) return LBM_ERR_INVALID_ARG;
@@ -464,6 +506,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         return forward_persist(p->info, a, bc, d_tau, s);
     }
     auto issue = [&](cudaStream_t st_) -> lbm_status {
+        LBM_TRY(write_mrt_rates(p, bc, st_));
         // g^0 = rest
         unsigned char* cur = slot(0);
         if (!cur) cur = ping0;
@@ -498,6 +541,7 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
     auto issue = [&](cudaStream_t st_) -> lbm_status {
+        LBM_TRY(write_mrt_rates(p, bc, st_));
         if (p->info.cmp.nf)
             LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bc, d_tau, st_));
         else
@@ -651,6 +695,7 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LBM_ERR_CUDA;
     }
     auto issue = [&](cudaStream_t st_) -> lbm_status {
+        LBM_TRY(write_mrt_rates(p, bc, st_));
         lam_cur = d_lambda;
         lam_next = 0;
         if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, st_) != cudaSuccess)

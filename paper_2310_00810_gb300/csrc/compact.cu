@@ -296,7 +296,7 @@ __device__ __noinline__ void step_node_eq6(const T* __restrict__ src, T* __restr
     load_codes<Q>(code, c, k);
     T v[Q];
     pull_cmp<Q, T>(v, src, k, c.nf, code, true, c, g, bc);
-    if (MODE != kStreamOnly) collide<Q, T>(v, omega);
+    if (MODE != kStreamOnly) collide_any<Q, T>(v, omega, bc);
     store_node<Q, T, DOUT>(dst, v, k, c, g);
 }
 
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kCmpThreads, 4) k_step_cmp(const T* __restrict
         }
         pull_cmp<Q, T>(v, src, k, c.nf, code, false, c, g, bc);
     }
-    if (MODE != kStreamOnly) collide<Q, T>(v, omega);
+    if (MODE != kStreamOnly) collide_any<Q, T>(v, omega, bc);
     store_node<Q, T, DOUT>(dst, v, k, c, g);
 }
 
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kCmpThreads, MINB) k_step_cmp_gs(const T* __re
             step_node_eq6<Q, T, kStreamCollide, false>(src, dst, k, c, g, bc, omega);
             continue;
         }
-        collide<Q, T>(v, omega);
+        collide_any<Q, T>(v, omega, bc);
         store_node<Q, T, false>(dst, v, k, c, g);
     }
 }
@@ -363,9 +363,18 @@ __global__ void __launch_bounds__(kCmpThreads, MINB) k_step_cmp_gs(const T* __re
 template <int Q, typename T>
 __device__ __forceinline__ T adjoint_collision(const T (&f)[Q], const T (&mu)[Q], T drho, T rho, const T (&u)[3],
                                                const T (&G)[3], T omega, T* __restrict__ lam_out, long long k,
-                                               size_t NF)
+                                               size_t NF, const Bc& bc)
 {
     using L = Lattice<Q>;
+    if constexpr (Q == 9) {
+        if (bc.mrt) {
+            T lam[9];
+            const T dom = adjoint_collision_mrt<T>(f, mu, drho, rho, u, G, omega, mrt_rates(bc.status), lam);
+#pragma unroll
+            for (int kk = 0; kk < 9; ++kk) lam_out[(size_t)kk * NF + k] = lam[kk];
+            return dom;
+        }
+    }
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     T A = 0, B[3] = {T(0), T(0), T(0)}, domT = 0;
 #pragma unroll
@@ -444,7 +453,7 @@ __device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T*
             for (int a = 0; a < L::D; ++a) G[a] += li * two_w * rwT * (T(9) * cu * T(L::c(o, a)) - T(3) * u[a]);
         }
     }
-    const T domT = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF);
+    const T domT = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF, bc);
     // 4. inlet gradient (one owner per inlet node)
     if (sd.xin) grad_acc[sd.row] += grw;
     return domT;
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(kCmpThreads, 4)
             T drho, rho, u[3];
             moments<Q, T>(f, drho, rho, u);
             const T G[3] = {T(0), T(0), T(0)};
-            dom = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF);
+            dom = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF, bc);
         }
     }
     // one FP64 partial per warp (its sum in T), accumulated in place across

@@ -61,6 +61,143 @@ __device__ __forceinline__ void collide(T (&v)[Q], T omega)
     }
 }
 
+// ------------------------------------------------------------- MRT (D2Q9)
+// The moment matrix of the MRT operator (section 3.4, Eq. 18) in this
+// lattice's direction order; rows rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx,
+// p_xy (the printed p_xy row |c_x c_y| read as the orthogonal c_x c_y), and
+// 1 / |row|^2 (the rows are orthogonal: M^{-1} = M^T diag(1 / |row|^2)).
+__host__ __device__ constexpr int mrt_m(int r, int j)
+{
+    constexpr int t[9][9] = {{1, 1, 1, 1, 1, 1, 1, 1, 1},     {-4, -1, -1, -1, -1, 2, 2, 2, 2},
+                             {4, -2, -2, -2, -2, 1, 1, 1, 1},  {0, 1, 0, -1, 0, 1, -1, -1, 1},
+                             {0, -2, 0, 2, 0, 1, -1, -1, 1},   {0, 0, 1, 0, -1, 1, 1, -1, -1},
+                             {0, 0, -2, 0, 2, 1, 1, -1, -1},   {0, 1, -1, 1, -1, 0, 0, 0, 0},
+                             {0, 0, 0, 0, 0, 1, -1, 1, -1}};
+    return t[r][j];
+}
+
+__host__ __device__ constexpr double mrt_inv_norm2(int r)
+{
+    constexpr double t[9] = {1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 6, 1.0 / 12, 1.0 / 6, 1.0 / 12, 1.0 / 4, 1.0 / 4};
+    return t[r];
+}
+
+// Relaxation rate of moment row r: 0 for the conserved rho, j_x, j_y (their
+// m - m^eq vanishes), s_e, s_eps, s_q for the free rows, omega = 1/tau for the
+// stress rows p_xx, p_xy.
+template <typename T>
+__device__ __forceinline__ T mrt_rate(int r, T omega, const T (&s)[3])
+{
+    return r == 1 ? s[0] : r == 2 ? s[1] : (r == 4 || r == 6) ? s[2] : (r >= 7 ? omega : T(0));
+}
+
+// MRT collision (Eq. 16) in place on shifted populations:
+// f* = f - M^{-1} S M (f - f^eq), m^eq = M f^eq with f^eq of Eq. 5.
+template <typename T>
+__device__ __forceinline__ void collide_mrt(T (&v)[9], T omega, const float* __restrict__ rates)
+{
+    using L = Lattice<9>;
+    const T s[3] = {T(rates[0]), T(rates[1]), T(rates[2])};
+    T drho, rho, u[3];
+    moments<9, T>(v, drho, rho, u);
+    const T uu = u[0] * u[0] + u[1] * u[1];
+    T d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T cu = cdot<9, T>(i, u);
+        d[i] = v[i] - T(L::w(i)) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    }
+    T dm[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        T m = 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            if (mrt_m(r, j) != 0) m += T(mrt_m(r, j)) * d[j];
+        dm[r] = mrt_rate<T>(r, omega, s) * m * T(mrt_inv_norm2(r));
+    }
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        T c = 0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+            if (mrt_m(r, j) != 0 && r != 0 && r != 3 && r != 5) c += T(mrt_m(r, j)) * dm[r];
+        v[j] -= c;
+    }
+}
+
+// BGK (Eq. 4-5) or, on D2Q9 plans with Bc::mrt, MRT.
+template <int Q, typename T>
+__device__ __forceinline__ void collide_any(T (&v)[Q], T omega, const Bc& bc)
+{
+    if constexpr (Q == 9) {
+        if (bc.mrt) {
+            collide_mrt<T>(v, omega, mrt_rates(bc.status));
+            return;
+        }
+    }
+    collide<Q, T>(v, omega);
+}
+
+// Transpose of the MRT collision at one node, from f^t (moments drho, rho, u)
+// and mu = dL/df*: with nu = M^T S diag(1/|row|^2) M mu (nu = omega mu for
+// BGK), lambda_k = mu_k - nu_k + A + sum_a (B_a + G_a) (c_ka - u_a) / rho,
+// A = sum_j nu_j w_j P_j, B_a = sum_j nu_j w_j rho (3 c_ja + 9 (c_j.u) c_ja - 3 u_a),
+// G the Eq. 6 velocity terms.  Returns the node's dL/domega term: only the
+// stress rows depend on omega, -sum_{p_xx, p_xy} (M mu)_r (M (f - f^eq))_r / |row_r|^2.
+template <typename T>
+__device__ __forceinline__ T adjoint_collision_mrt(const T (&f)[9], const T (&mu)[9], T drho, T rho,
+                                                   const T (&u)[3], const T (&G)[3], T omega,
+                                                   const float* __restrict__ rates, T (&lam)[9])
+{
+    using L = Lattice<9>;
+    const T s[3] = {T(rates[0]), T(rates[1]), T(rates[2])};
+    const T uu = u[0] * u[0] + u[1] * u[1];
+    T d[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const T cu = cdot<9, T>(i, u);
+        d[i] = f[i] - T(L::w(i)) * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu));
+    }
+    T sm[9], dom = T(0);
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        T mm = 0, md = 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j)
+            if (mrt_m(r, j) != 0) {
+                mm += T(mrt_m(r, j)) * mu[j];
+                md += T(mrt_m(r, j)) * d[j];
+            }
+        if (r >= 7) dom -= mm * md * T(mrt_inv_norm2(r));
+        sm[r] = mrt_rate<T>(r, omega, s) * mm * T(mrt_inv_norm2(r));
+    }
+    T nu[9], A = 0, B[2] = {T(0), T(0)};
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        T c = 0;
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+            if (mrt_m(r, j) != 0 && r != 0 && r != 3 && r != 5) c += T(mrt_m(r, j)) * sm[r];
+        nu[j] = c;
+        const T cu = cdot<9, T>(j, u);
+        const T wj = T(L::w(j));
+        A += c * wj * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+            B[a] += c * wj * rho * (T(3 * L::c(j, a)) + T(9) * cu * T(L::c(j, a)) - T(3) * u[a]);
+    }
+    const T inv = T(1) / rho;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        T sk = mu[k] - nu[k] + A;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) sk += (B[a] + G[a]) * inv * (T(L::c(k, a)) - u[a]);
+        lam[k] = sk;
+    }
+    return dom;
+}
+
 // Eq. 6 with the wall velocity extrapolated to the pressure plane half a
 // link outside the boundary node (Bc::uw_extrap): u_w = u(x_b) + (u(x_b) -
 // u(x_b + e)) / 2, with x_b + e the inward neighbour, whose velocity comes from

@@ -398,7 +398,7 @@ lbm_status reverse_impl(const PlanInfo& p, const PersistArgs& a, const Bc& bc, c
 // Widest row vector every persistent kernel variant of this plan can use.
 bool persist_ok(const PlanInfo& p)
 {
-    return p.use_persist && p.cmp.nf == 0 && !p.uw_extrap && p.geo.nx % 4 == 0 && p.state_bytes <= p.persist_max_bytes;
+    return p.use_persist && p.cmp.nf == 0 && !p.uw_extrap && !p.mrt && p.geo.nx % 4 == 0 && p.state_bytes <= p.persist_max_bytes;
 }
 
 lbm_status forward_persist(const PlanInfo& p, const PersistArgs& a, const Bc& bc, const double* tau, cudaStream_t s)

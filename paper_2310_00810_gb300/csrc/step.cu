@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const T* __restrict__ src
     } else {
         pull<Q, T>(v, src, n, x, y, z, lw, g, bc);
     }
-    if (MODE != kStreamOnly) collide<Q, T>(v, T(1.0 / *tau));
+    if (MODE != kStreamOnly) collide_any<Q, T>(v, T(1.0 / *tau), bc);
 #pragma unroll
     for (int i = 0; i < Q; ++i) dst[(long long)i * g.N + n] = v[i];
 }
@@ -67,8 +67,8 @@ lbm_status step_launch(const PlanInfo& plan, int mode, const void* src, void* ds
                        cudaStream_t s)
 {
     if (plan.cmp.nf) return step_launch_cmp(plan, mode, src, dst, false, false, bc, tau, s);
-    // the extrapolated Eq. 6 velocity is implemented by the one-node-per-thread kernels
-    const PlanInfo p = with_family(plan, bc.uw_extrap ? LBM_FAMILY_SCALAR : plan.step_family);
+    // the extrapolated Eq. 6 velocity and the MRT collision are implemented by the one-node-per-thread kernels
+    const PlanInfo p = with_family(plan, (bc.uw_extrap || bc.mrt) ? LBM_FAMILY_SCALAR : plan.step_family);
     if (step_launch_tma(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (step_launch_vec(p, mode, src, dst, bc, tau, s)) return cuda_status(cudaGetLastError());
     if (p.q == 9 && p.prec == 4) launch<9, float>(p, mode, src, dst, bc, tau, s);

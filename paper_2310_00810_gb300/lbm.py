@@ -28,10 +28,12 @@ LBM_LINK_SOLID = 0x80000000
 
 LBM_FAMILY_AUTO, LBM_FAMILY_SCALAR, LBM_FAMILY_VEC, LBM_FAMILY_TMA = 0, 1, 2, 3
 LBM_ABB_U_NODE, LBM_ABB_U_EXTRAP = 0, 1
+LBM_COLLISION_BGK, LBM_COLLISION_MRT = 0, 1
 
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
     "lbm_compact_size", "lbm_compact_bind", "lbm_set_abb_velocity", "lbm_get_abb_velocity",
+    "lbm_set_collision", "lbm_get_collision",
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_probe_loss_grad", "lbm_spline_basis",
     "lbm_spline_profile", "lbm_spline_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
@@ -94,6 +96,8 @@ def load():
                 "lbm_compact_size": [vp, C.c_int64, C.POINTER(C.c_size_t)],
                 "lbm_compact_bind": [vp, C.c_int64, vp, vp],
                 "lbm_set_abb_velocity": [vp, i32],
+                "lbm_set_collision": [vp, i32, f64, f64, f64],
+                "lbm_get_collision": [vp, C.POINTER(C.c_int32), vp],
                 "lbm_get_abb_velocity": [vp, C.POINTER(C.c_int32)],
                 "lbm_probe_loss_grad": [vp, vp, C.c_int64, vp, vp, f64, vp, vp, vp, vp],
                 "lbm_spline_basis": [i32, i32, vp],
@@ -259,6 +263,19 @@ def lbm_get_abb_velocity(plan: Plan) -> int:
     m = C.c_int32()
     _check(load().lbm_get_abb_velocity(plan.handle, C.byref(m)), "lbm_get_abb_velocity")
     return m.value
+
+
+def lbm_set_collision(plan: Plan, mode: int, s_e: float = 1.0, s_eps: float = 1.0, s_q: float = 1.0) -> None:
+    _check(load().lbm_set_collision(plan.handle, int(mode), float(s_e), float(s_eps), float(s_q)),
+           "lbm_set_collision")
+
+
+def lbm_get_collision(plan: Plan):
+    """(mode, (s_e, s_eps, s_q))."""
+    m = C.c_int32()
+    r = (C.c_double * 3)()
+    _check(load().lbm_get_collision(plan.handle, C.byref(m), C.cast(r, C.c_void_p)), "lbm_get_collision")
+    return m.value, tuple(r)
 
 
 def lbm_forward(plan: Plan, rho_in, tau, rho_out: float, f, ws, stream=None) -> None:
@@ -466,6 +483,10 @@ class Solver:
         """Adds the density-probe term to loss and its seed to lam (after loss_grad)."""
         self.run(lambda: lbm_probe_loss_grad(self.plan, f, nodes, rho_target, weight, loss, lam, self.ws))
         return loss, lam
+
+    def set_collision(self, mode: int, s_e: float = 1.0, s_eps: float = 1.0, s_q: float = 1.0) -> None:
+        """LBM_COLLISION_BGK (default) or LBM_COLLISION_MRT with the free rates (D2Q9)."""
+        lbm_set_collision(self.plan, mode, s_e, s_eps, s_q)
 
     def set_abb_velocity(self, mode: int) -> None:
         """LBM_ABB_U_NODE (default) or LBM_ABB_U_EXTRAP: where Eq. 6 takes its velocity."""
