@@ -48,6 +48,94 @@ class InversionResult:
     err_history: list
 
 
+@dataclasses.dataclass
+class LbfgsResult:
+    x: np.ndarray
+    iterations: int
+    evaluations: int
+    seconds: float
+    converged: bool
+    losses: list
+    errs: list
+
+
+def lbfgs(evaluate, x0, max_evals=400, memory=20, errors=None, done=None, lower=None, time_limit=None):
+    """Limited-memory BFGS (two-loop recursion) with a secant step along each
+    direction, exact for a quadratic loss.  evaluate(x) -> (loss, gradient);
+    errors(x) -> a record stored per iteration and done(record) -> stop;
+    lower = {index: bound} keeps those coordinates above their bounds (the
+    step is shortened to reach at most the bound).  A secant point is taken
+    only if it lowers the loss, and a step whose loss is non-finite or larger
+    is halved until it is not; a non-finite loss that halving cannot cure
+    ends the run."""
+    t_start = time.perf_counter()
+    x = np.array(x0, np.float64)
+    f, g = evaluate(x)
+    evals = 1
+    S, Y, losses, errs = [], [], [f], []
+    converged = False
+    it = 0
+    while evals < max_evals:
+        it += 1
+        q = g.copy()
+        alphas = []
+        for sv, yv in reversed(list(zip(S, Y))):
+            a = sv @ q / (yv @ sv)
+            alphas.append(a)
+            q -= a * yv
+        gamma = (S[-1] @ Y[-1]) / (Y[-1] @ Y[-1]) if S else 1.0 / max(np.linalg.norm(g), 1e-300)
+        r = gamma * q
+        for (sv, yv), a in zip(zip(S, Y), reversed(alphas)):
+            b = yv @ r / (yv @ sv)
+            r += sv * (a - b)
+        d = -r
+        d0 = g @ d
+        if d0 >= 0:  # not a descent direction: restart from steepest descent
+            S, Y = [], []
+            d = -g / max(np.linalg.norm(g), 1e-300)
+            d0 = g @ d
+        t_max = np.inf
+        for i, lo in (lower or {}).items():
+            if d[i] < 0:
+                t_max = min(t_max, max((x[i] - lo) / -d[i], 0.0))
+        t = min(1.0, t_max)
+        f1, g1 = evaluate(x + t * d)
+        evals += 1
+        d1 = g1 @ d
+        if np.isfinite(f1) and d1 > d0:  # secant step on the directional derivative
+            t_new = min(-d0 / (d1 - d0) * t, t_max)
+            if abs(t_new - t) > 1e-12 * t and evals < max_evals:
+                f2, g2 = evaluate(x + t_new * d)
+                evals += 1
+                if np.isfinite(f2) and f2 <= f1:
+                    t, f1, g1 = t_new, f2, g2
+        while not (np.isfinite(f1) and f1 <= f + 1e-6 * abs(f)) and evals < max_evals and t > 1e-6:
+            t *= 0.5
+            f1, g1 = evaluate(x + t * d)
+            evals += 1
+        if not np.isfinite(f1):
+            break
+        sv, yv = t * d, g1 - g
+        if yv @ sv > 0:
+            S.append(sv)
+            Y.append(yv)
+            if len(S) > memory:
+                S.pop(0)
+                Y.pop(0)
+        x, f, g = x + sv, f1, g1
+        losses.append(f)
+        if errors is not None:
+            e = errors(x)
+            if e is not None:
+                errs.append(e)
+                if done is not None and done(e):
+                    converged = True
+                    break
+        if time_limit is not None and time.perf_counter() - t_start > time_limit:
+            break
+    return LbfgsResult(x, it, evals, time.perf_counter() - t_start, converged, losses, errs)
+
+
 class Inversion:
     """Adam inversion of the inlet density (constant head or profile) and,
     optionally, tau, against a target velocity field."""
@@ -187,80 +275,28 @@ class Inversion:
             x = np.concatenate([x, self.theta_tau.cpu().numpy()])
         td = None if truth_delta is None else np.broadcast_to(np.asarray(truth_delta, np.float64), (p.n_in,))
         nu_true = None if truth_tau is None else (truth_tau - 0.5) / 3.0
+
+        def errors(xk):
+            if td is None:
+                return None
+            e_in = float(np.linalg.norm(self._delta(xk[:n]) - td) / np.linalg.norm(td))
+            e_nu = None
+            if nu_true is not None and self.invert_tau:
+                e_nu = float(abs(TAU_SCALE * xk[n] / 3.0 - nu_true) / nu_true)
+            return e_in, e_nu
+
+        def done(e):
+            return e[0] <= tol and (e[1] is None or e[1] <= tol)
+
         torch.cuda.synchronize(self.s.device)
-        t_start = time.perf_counter()
-        evals = 0
-        f, g = self._evaluate(x)
-        evals += 1
-        S, Y, losses, errs = [], [], [f], []
-        converged = False
-        e_in = e_nu = None
-        it = 0
-        while evals < max_evals:
-            it += 1
-            q = g.copy()
-            alphas = []
-            for sv, yv in reversed(list(zip(S, Y))):
-                a = sv @ q / (yv @ sv)
-                alphas.append(a)
-                q -= a * yv
-            gamma = (S[-1] @ Y[-1]) / (Y[-1] @ Y[-1]) if S else 1.0 / max(np.linalg.norm(g), 1e-300)
-            r = gamma * q
-            for (sv, yv), a in zip(zip(S, Y), reversed(alphas)):
-                b = yv @ r / (yv @ sv)
-                r += sv * (a - b)
-            d = -r
-            d0 = g @ d
-            if d0 >= 0:  # not a descent direction: restart from steepest descent
-                S, Y = [], []
-                d = -g / max(np.linalg.norm(g), 1e-300)
-                d0 = g @ d
-            # the step keeps tau above 1/2 (nu > 0): beyond it the lattice is unstable
-            t_max = np.inf
-            if self.invert_tau and d[n] < 0:
-                t_max = max((x[n] - TAU_MIN_THETA) / -d[n], 0.0)
-            t = min(1.0, t_max)
-            f1, g1 = self._evaluate(x + t * d)
-            evals += 1
-            d1 = g1 @ d
-            if np.isfinite(f1) and d1 > d0:  # secant step on the directional derivative (exact for a quadratic)
-                t_new = min(-d0 / (d1 - d0) * t, t_max)
-                if abs(t_new - t) > 1e-12 * t and evals < max_evals:
-                    f2, g2 = self._evaluate(x + t_new * d)
-                    evals += 1
-                    if np.isfinite(f2) and f2 <= f1:
-                        t, f1, g1 = t_new, f2, g2
-            # halve the step while the loss is non-finite or has grown (not for a quadratic)
-            while not (np.isfinite(f1) and f1 <= f + 1e-6 * abs(f)) and evals < max_evals and t > 1e-6:
-                t *= 0.5
-                f1, g1 = self._evaluate(x + t * d)
-                evals += 1
-            if not np.isfinite(f1):
-                break
-            sv, yv = t * d, g1 - g
-            if yv @ sv > 0:
-                S.append(sv)
-                Y.append(yv)
-                if len(S) > memory:
-                    S.pop(0)
-                    Y.pop(0)
-            x, f, g = x + sv, f1, g1
-            losses.append(f)
-            if td is not None:
-                e_in = float(np.linalg.norm(self._delta(x[:n]) - td) / np.linalg.norm(td))
-                if nu_true is not None and self.invert_tau:
-                    e_nu = float(abs(TAU_SCALE * x[n] / 3.0 - nu_true) / nu_true)
-                errs.append((e_in, e_nu))
-                if e_in <= tol and (e_nu is None or e_nu <= tol):
-                    converged = True
-                    break
-            if time_limit is not None and time.perf_counter() - t_start > time_limit:
-                break
-        secs = time.perf_counter() - t_start
+        r = lbfgs(self._evaluate, x, max_evals=max_evals, memory=memory, errors=errors, done=done,
+                  lower=({n: TAU_MIN_THETA} if self.invert_tau else None), time_limit=time_limit)
+        x = r.x
         self.theta.copy_(torch.from_numpy(self._delta(x[:n]) / INLET_SCALE))
         if self.invert_tau:
             self.theta_tau.fill_(float(x[n]))
-        self.evaluations = evals
-        return InversionResult(it, secs, converged, self.rho_out + self._delta(x[:n]),
+        self.evaluations = r.evaluations
+        e_in, e_nu = r.errs[-1] if r.errs else (None, None)
+        return InversionResult(r.iterations, r.seconds, r.converged, self.rho_out + self._delta(x[:n]),
                                TAU_OFFSET + TAU_SCALE * x[n] if self.invert_tau else self.tau_fixed, e_in, e_nu,
-                               losses, errs)
+                               r.losses, r.errs)
