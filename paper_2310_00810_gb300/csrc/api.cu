@@ -118,9 +118,9 @@ bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 25
 unsigned char* bytes(void* ws) { return static_cast<unsigned char*>(ws); }
 
 // The MRT rates into the status section, where the kernels read them (Bc::mrt).
-__global__ void k_write_mrt_rates(uint32_t* status, float s_e, float s_eps, float s_q)
+__global__ void k_write_mrt_rates(uint32_t* status, double s_e, double s_eps, double s_q)
 {
-    float* r = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(status) + kMrtRates);
+    double* r = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(status) + kMrtRates);
     r[0] = s_e;
     r[1] = s_eps;
     r[2] = s_q;
@@ -394,9 +394,9 @@ lbm_status lbm_set_collision(lbm_plan* p, int32_t mode, double s_e, double s_eps
         if (p->info.q != 9) return LBM_ERR_UNSUPPORTED;
         auto ok = [](double r) { return r > 0.0 && r < 2.0; };
         if (!ok(s_e) || !ok(s_eps) || !ok(s_q)) return LBM_ERR_INVALID_ARG;
-        p->info.mrt_rates[0] = (float)s_e;
-        p->info.mrt_rates[1] = (float)s_eps;
-        p->info.mrt_rates[2] = (float)s_q;
+        p->info.mrt_rates[0] = s_e;
+        p->info.mrt_rates[1] = s_eps;
+        p->info.mrt_rates[2] = s_q;
     }
     p->info.mrt = mode == LBM_COLLISION_MRT ? 1 : 0;
     drop_graphs(p);
@@ -408,7 +408,7 @@ lbm_status lbm_get_collision(const lbm_plan* p, int32_t* mode, double* rates)
     if (!p || !mode) return LBM_ERR_INVALID_ARG;
     *mode = p->info.mrt ? LBM_COLLISION_MRT : LBM_COLLISION_BGK;
     if (rates)
-        for (int i = 0; i < 3; ++i) rates[i] = p->info.mrt ? (double)p->info.mrt_rates[i] : 0.0;
+        for (int i = 0; i < 3; ++i) rates[i] = p->info.mrt ? p->info.mrt_rates[i] : 0.0;
     return LBM_OK;
 }
 

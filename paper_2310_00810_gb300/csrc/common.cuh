@@ -78,7 +78,7 @@ struct PlanInfo {
     int overlap;      // 1: reverse sweep recomputes the next segment on a second stream during the adjoint steps
     int uw_extrap;    // 1: Eq. 6 with the extrapolated wall velocity (one-node-per-thread or fluid-only kernels)
     int mrt;          // 1: D2Q9 MRT collision (one-node-per-thread or fluid-only kernels)
-    float mrt_rates[3];  // s_e, s_eps, s_q of the MRT collision
+    double mrt_rates[3];  // s_e, s_eps, s_q of the MRT collision
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     size_t persist_max_bytes;
     int tma_min_tiles;  // smallest tile count for which the TMA kernels are used
@@ -114,12 +114,12 @@ constexpr size_t kBarOffset = 64;  // byte offset of the PersistBar in the statu
 constexpr size_t kScalarCount = 8;    // double: ROI fluid-node count
 constexpr size_t kScalarWeight = 16;  // double: loss weight
 constexpr size_t kScalarTmp = 24;     // double: scratch
-constexpr size_t kMrtRates = 128;     // float[4]: s_e, s_eps, s_q of the MRT collision (written per call)
+constexpr size_t kMrtRates = 128;     // double[3]: s_e, s_eps, s_q of the MRT collision (written per call)
 
 // The MRT rates a kernel reads (Bc::mrt): s_e, s_eps, s_q.
-__device__ __forceinline__ const float* mrt_rates(const uint32_t* status)
+__device__ __forceinline__ const double* mrt_rates(const uint32_t* status)
 {
-    return reinterpret_cast<const float*>(reinterpret_cast<const unsigned char*>(status) + kMrtRates);
+    return reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(status) + kMrtRates);
 }
 
 // --------------------------------------------------------------- reductions

@@ -94,7 +94,7 @@ __device__ __forceinline__ T mrt_rate(int r, T omega, const T (&s)[3])
 // MRT collision (Eq. 16) in place on shifted populations:
 // f* = f - M^{-1} S M (f - f^eq), m^eq = M f^eq with f^eq of Eq. 5.
 template <typename T>
-__device__ __forceinline__ void collide_mrt(T (&v)[9], T omega, const float* __restrict__ rates)
+__device__ __forceinline__ void collide_mrt(T (&v)[9], T omega, const double* __restrict__ rates)
 {
     using L = Lattice<9>;
     const T s[3] = {T(rates[0]), T(rates[1]), T(rates[2])};
@@ -148,7 +148,7 @@ __device__ __forceinline__ void collide_any(T (&v)[Q], T omega, const Bc& bc)
 template <typename T>
 __device__ __forceinline__ T adjoint_collision_mrt(const T (&f)[9], const T (&mu)[9], T drho, T rho,
                                                    const T (&u)[3], const T (&G)[3], T omega,
-                                                   const float* __restrict__ rates, T (&lam)[9])
+                                                   const double* __restrict__ rates, T (&lam)[9])
 {
     using L = Lattice<9>;
     const T s[3] = {T(rates[0]), T(rates[1]), T(rates[2])};
