@@ -27,6 +27,13 @@
  * Density probes (an optional second loss term): w sum_p (rho(x_p) - rho_p)^2
  * over a list of probe nodes, with its seed dL/df_k = 2 w (rho - rho_p).
  *
+ * Options for the cylinder-wake flow of section 3.4: periodic top and bottom
+ * (set_periodic_y: links leaving y = -1/2 or ny - 1/2 re-enter on the other
+ * side instead of bouncing back) and a velocity inlet (set_velocity_inlet:
+ * the links through x = -1/2 take the moving-wall bounce-back
+ * f_i = f*_opp(i) + 6 w_i rho_0 (c_i . u_in), rho_0 = 1, in place of Eq. 6;
+ * the outlet keeps Eq. 6).
+ *
  * MRT collision (section 3.4, Eq. 16-18; D2Q9 only, an option set by
  * set_collision): f* = f - M^{-1} S M (f - f^eq), M the moment matrix of
  * Eq. 18 (rows rho, e, epsilon, j_x, q_x, j_y, q_y, p_xx, p_xy; the printed
@@ -164,11 +171,32 @@ typedef struct {
 
 enum { LINK_FLUID = 0, LINK_BB = 1, LINK_ABB_IN = 2, LINK_ABB_OUT = 3 };
 
+static int g_periodic_y = 0;
+static int g_vel_inlet = 0;
+static double g_u_in[3] = {0, 0, 0};
+
+int SYM(set_periodic_y)(int on)
+{
+    g_periodic_y = on ? 1 : 0;
+    return 0;
+}
+
+int SYM(set_velocity_inlet)(int on, double ux, double uy, double uz)
+{
+    g_vel_inlet = on ? 1 : 0;
+    g_u_in[0] = ux;
+    g_u_in[1] = uy;
+    g_u_in[2] = uz;
+    return 0;
+}
+
 /* What node (x,y,z) receives in direction i: the population streaming along
- * the link from x - c_i.  Wall planes (y, z) win over pressure planes (x). */
+ * the link from x - c_i.  Wall planes (y, z) win over pressure planes (x);
+ * with periodic y a link leaving the y range re-enters on the other side. */
 static int classify(const domain* D, const lattice* L, int x, int y, int z, int i, long* src)
 {
     int sx = x - L->c[i][0], sy = y - L->c[i][1], sz = z - L->c[i][2];
+    if (g_periodic_y) sy = (sy + D->ny) % D->ny;
     if (sy < 0 || sy >= D->ny || sz < 0 || sz >= D->nz) return LINK_BB;
     if (sx < 0) return LINK_ABB_IN;
     if (sx >= D->nx) return LINK_ABB_OUT;
@@ -420,6 +448,10 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
                         v = fstar[(long)i * N + s];
                     } else if (cls == LINK_BB) {
                         v = fstar[(long)L.opp[i] * N + n];
+                    } else if (cls == LINK_ABB_IN && g_vel_inlet) {
+                        double cu = 0;
+                        for (int a = 0; a < L.d; ++a) cu += L.c[i][a] * g_u_in[a];
+                        v = fstar[(long)L.opp[i] * N + n] + 6.0 * L.w[i] * cu;
                     } else {
                         real_t rw = cls == LINK_ABB_IN ? inlet_rho(rho_in, inlet_profile, &D, y, z) : *rho_out;
                         v = -fstar[(long)L.opp[i] * N + n] + abb_source(&L, i, rw, u);
@@ -683,8 +715,8 @@ int orc_adjoint_step(int q, int nx, int ny, int nz, const uint8_t* mask, const d
                     double lam = lam_next[(long)i * N + n];
                     if (cls == LINK_FLUID) {
                         mu[(long)i * N + s] += lam;
-                    } else if (cls == LINK_BB) {
-                        mu[(long)L.opp[i] * N + n] += lam;
+                    } else if (cls == LINK_BB || (cls == LINK_ABB_IN && g_vel_inlet)) {
+                        mu[(long)L.opp[i] * N + n] += lam;  /* the velocity inlet's source is constant */
                     } else {
                         double rw = cls == LINK_ABB_IN ? inlet_rho(rho_in, inlet_profile, &D, y, z) : *rho_out;
                         mu[(long)L.opp[i] * N + n] -= lam;

@@ -121,6 +121,41 @@ class collision:
         return False
 
 
+def set_periodic_y(on: bool) -> None:
+    """Periodic top and bottom (both builds; every later call)."""
+    for cs in (False, True):
+        lib = _lib(cs)
+        fn = lib.orc_cs_set_periodic_y if cs else lib.orc_set_periodic_y
+        _check(fn(1 if on else 0), "set_periodic_y")
+
+
+def set_velocity_inlet(u) -> None:
+    """Velocity inlet u = (u_x, u_y[, u_z]) through x = -1/2, or None for Eq. 6 (both builds)."""
+    v = [0.0, 0.0, 0.0] if u is None else [float(a) for a in u] + [0.0] * (3 - len(u))
+    for cs in (False, True):
+        lib = _lib(cs)
+        fn = lib.orc_cs_set_velocity_inlet if cs else lib.orc_set_velocity_inlet
+        fn.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double]
+        _check(fn(0 if u is None else 1, *v), "set_velocity_inlet")
+
+
+class wake_options:
+    """``with wake_options(periodic_y=True, velocity_inlet=(0.05, 0)): ...``"""
+
+    def __init__(self, periodic_y=False, velocity_inlet=None):
+        self.p, self.u = periodic_y, velocity_inlet
+
+    def __enter__(self):
+        set_periodic_y(self.p)
+        set_velocity_inlet(self.u)
+        return self
+
+    def __exit__(self, *exc):
+        set_periodic_y(False)
+        set_velocity_inlet(None)
+        return False
+
+
 class abb_velocity:
     """``with abb_velocity(UW_EXTRAP): ...`` sets the Eq. 6 velocity for the block."""
 
