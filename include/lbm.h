@@ -162,6 +162,22 @@ enum { LBM_COLLISION_BGK = 0, LBM_COLLISION_MRT = 1 };
 LBM_API lbm_status lbm_set_collision(lbm_plan* plan, int32_t mode, double s_e, double s_eps, double s_q);
 LBM_API lbm_status lbm_get_collision(const lbm_plan* plan, int32_t* mode, double* rates);
 
+/* Cylinder-wake options (section 3.4: the flow past a cylinder has a
+ * free-stream velocity inlet and periodic top and bottom boundaries).
+ * lbm_set_periodic_y: links leaving y = -1/2 or ny - 1/2 re-enter on the
+ *   other side instead of bouncing back.  It shapes the link words and the
+ *   fluid-only tables, so it must be set before lbm_init_geometry /
+ *   lbm_bind_geometry (INVALID_ARG afterwards).  The flood fill of isolated
+ *   pores does not wrap.
+ * lbm_set_velocity_inlet: the links through x = -1/2 take the moving-wall
+ *   bounce-back f_i = f*_opp(i) + 6 w_i rho_0 (c_i . u_in), rho_0 = 1, instead
+ *   of Eq. 6 (the outlet keeps Eq. 6; d_rho_in is not used and its gradient
+ *   is zero).  u_in finite; uz = 0 on D2Q9 plans.
+ * Both run in the fluid-only layout only: lbm_forward, lbm_step and
+ * lbm_adjoint return UNSUPPORTED on a dense plan with either option set. */
+LBM_API lbm_status lbm_set_periodic_y(lbm_plan* plan, int32_t on);
+LBM_API lbm_status lbm_set_velocity_inlet(lbm_plan* plan, int32_t on, double ux, double uy, double uz);
+
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
  * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and two
  * segment buffers, adjoint ping-pong states and FP64 reduction slots. */

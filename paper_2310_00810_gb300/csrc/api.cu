@@ -117,20 +117,40 @@ bool aligned256(const void* ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 25
 
 unsigned char* bytes(void* ws) { return static_cast<unsigned char*>(ws); }
 
-// The MRT rates into the status section, where the kernels read them (Bc::mrt).
-__global__ void k_write_mrt_rates(uint32_t* status, double s_e, double s_eps, double s_q)
+// The MRT rates and the inlet velocity into the status section, where the
+// kernels read them (Bc::mrt, Bc::vel_inlet).
+struct CallParams {
+    double rates[3], u_in[3];
+};
+
+__global__ void k_write_call_params(uint32_t* status, CallParams c)
 {
-    double* r = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(status) + kMrtRates);
-    r[0] = s_e;
-    r[1] = s_eps;
-    r[2] = s_q;
+    unsigned char* b = reinterpret_cast<unsigned char*>(status);
+    double* r = reinterpret_cast<double*>(b + kMrtRates);
+    double* u = reinterpret_cast<double*>(b + kInletVelocity);
+    for (int i = 0; i < 3; ++i) {
+        r[i] = c.rates[i];
+        u[i] = c.u_in[i];
+    }
 }
 
 lbm_status write_mrt_rates(const lbm_plan* p, const Bc& bc, cudaStream_t s)
 {
-    if (!p->info.mrt) return LBM_OK;
-    k_write_mrt_rates<<<1, 1, 0, s>>>(bc.status, p->info.mrt_rates[0], p->info.mrt_rates[1], p->info.mrt_rates[2]);
+    if (!p->info.mrt && !p->info.vel_inlet) return LBM_OK;
+    CallParams c;
+    for (int i = 0; i < 3; ++i) {
+        c.rates[i] = p->info.mrt_rates[i];
+        c.u_in[i] = p->info.u_in[i];
+    }
+    k_write_call_params<<<1, 1, 0, s>>>(bc.status, c);
     return cuda_status(cudaGetLastError());
+}
+
+// The periodic-y and velocity-inlet options exist in the fluid-only layout only.
+lbm_status check_layout_options(const lbm_plan* p)
+{
+    if ((p->info.geo.periodic_y || p->info.vel_inlet) && !p->info.cmp.nf) return LBM_ERR_UNSUPPORTED;
+    return LBM_OK;
 }
 
 Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
@@ -142,6 +162,7 @@ Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
     bc.status = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(ws) + p->ws.status);
     bc.uw_extrap = p->info.uw_extrap;
     bc.mrt = p->info.mrt;
+    bc.vel_inlet = p->info.vel_inlet;
     return bc;
 }
 
@@ -403,6 +424,26 @@ lbm_status lbm_set_collision(lbm_plan* p, int32_t mode, double s_e, double s_eps
     return LBM_OK;
 }
 
+lbm_status lbm_set_periodic_y(lbm_plan* p, int32_t on)
+{
+    if (!p || (on != 0 && on != 1) || p->link) return LBM_ERR_INVALID_ARG;
+    p->info.geo.periodic_y = on;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_velocity_inlet(lbm_plan* p, int32_t on, double ux, double uy, double uz)
+{
+    if (!p || (on != 0 && on != 1) || !std::isfinite(ux) || !std::isfinite(uy) || !std::isfinite(uz))
+        return LBM_ERR_INVALID_ARG;
+    if (on && p->info.q == 9 && uz != 0.0) return LBM_ERR_INVALID_ARG;
+    p->info.vel_inlet = on;
+    p->info.u_in[0] = on ? ux : 0.0;
+    p->info.u_in[1] = on ? uy : 0.0;
+    p->info.u_in[2] = on ? uz : 0.0;
+    drop_graphs(p);
+    return LBM_OK;
+}
+
 lbm_status lbm_get_collision(const lbm_plan* p, int32_t* mode, double* rates)
 {
     if (!p || !mode) return LBM_ERR_INVALID_ARG;
@@ -482,6 +523,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
                        void* d_ws, void* stream)
 {
     LBM_TRY(check_common(p, d_ws));
+    LBM_TRY(check_layout_options(p));
     if (!d_rho_in || !d_tau || !d_f || !d_ws) return LBM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
@@ -534,6 +576,7 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
                     void* d_f_out, int32_t n_steps, void* d_ws, void* stream)
 {
     LBM_TRY(check_common(p, d_ws));
+    LBM_TRY(check_layout_options(p));
     if (!d_rho_in || !d_tau || !d_f_in || !d_f_out || !d_ws || n_steps < 1) return LBM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
@@ -632,6 +675,7 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
                        const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream)
 {
     LBM_TRY(check_common(p, d_ws));
+    LBM_TRY(check_layout_options(p));
     if (!d_rho_in || !d_tau || !d_lambda || !d_grad_rho_in || !d_grad_tau || !d_ws) return LBM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);

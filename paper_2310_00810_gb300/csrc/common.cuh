@@ -36,6 +36,7 @@ struct Geo {
     long long N;
     const uint32_t* link;
     int skip_sectors;  // 1: kernels may skip stores of 32-byte sectors holding only solid nodes (nx % 8 == 0)
+    int periodic_y = 0;  // 1: links leaving the y range re-enter on the other side (fluid-only layout only)
 };
 
 struct Bc {
@@ -43,6 +44,7 @@ struct Bc {
     short profile;         // 1: rho_in[z*ny + y], 0: rho_in[0]
     char uw_extrap = 0;    // 1: Eq. 6 takes u_w extrapolated to the pressure plane (LBM_ABB_U_EXTRAP)
     char mrt = 0;          // 1: D2Q9 MRT collision (Eq. 16-18); its free rates are in the status section
+    char vel_inlet = 0;    // 1: velocity inlet through x = -1/2 (moving-wall bounce-back); u_in in the status section
     double rho_out;
     uint32_t* status;      // device status word (bounded waits latch LBM_ERR_TIMEOUT here)
 };
@@ -78,6 +80,8 @@ struct PlanInfo {
     int overlap;      // 1: reverse sweep recomputes the next segment on a second stream during the adjoint steps
     int uw_extrap;    // 1: Eq. 6 with the extrapolated wall velocity (one-node-per-thread or fluid-only kernels)
     int mrt;          // 1: D2Q9 MRT collision (one-node-per-thread or fluid-only kernels)
+    int vel_inlet;    // 1: velocity inlet instead of Eq. 6 at x = -1/2 (fluid-only kernels)
+    double u_in[3];   // its velocity
     double mrt_rates[3];  // s_e, s_eps, s_q of the MRT collision
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     size_t persist_max_bytes;
@@ -115,6 +119,13 @@ constexpr size_t kScalarCount = 8;    // double: ROI fluid-node count
 constexpr size_t kScalarWeight = 16;  // double: loss weight
 constexpr size_t kScalarTmp = 24;     // double: scratch
 constexpr size_t kMrtRates = 128;     // double[3]: s_e, s_eps, s_q of the MRT collision (written per call)
+constexpr size_t kInletVelocity = 160;  // double[3]: the velocity inlet's u_in (written per call)
+
+// The velocity inlet's u_in a kernel reads (Bc::vel_inlet).
+__device__ __forceinline__ const double* inlet_velocity(const uint32_t* status)
+{
+    return reinterpret_cast<const double*>(reinterpret_cast<const unsigned char*>(status) + kInletVelocity);
+}
 
 // The MRT rates a kernel reads (Bc::mrt): s_e, s_eps, s_q.
 __device__ __forceinline__ const double* mrt_rates(const uint32_t* status)

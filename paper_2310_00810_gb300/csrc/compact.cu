@@ -174,13 +174,14 @@ __global__ void __launch_bounds__(256) k_cmp_nbr(const uint32_t* __restrict__ li
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nf) return;
     const long long n = idx[k];
-    const int x = (int)(n % g.nx);
+    const int x = (int)(n % g.nx), y = (int)((n / g.nx) % g.ny), z = (int)(n / ((long long)g.nx * g.ny));
     const uint32_t lw = link[n];
-    const long long plane = (long long)g.nx * g.ny;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         int32_t code;
-        const int xs = x - L::c(i, 0);
+        const int xs = x - L::c(i, 0), zs = z - L::c(i, 2);
+        int ys = y - L::c(i, 1);
+        if (g.periodic_y) ys = (ys + g.ny) % g.ny;  // ys is in -1..ny
         if ((lw >> i) & 1u) {
             code = kCmpBB;
         } else if (xs < 0 || xs >= g.nx) {
@@ -188,8 +189,9 @@ __global__ void __launch_bounds__(256) k_cmp_nbr(const uint32_t* __restrict__ li
         } else {
             // a link that is neither bounce-back nor Eq. 6 starts at a fluid node inside the lattice;
             // anything else (an inconsistent link array) is treated as bounce-back
-            const long long m = n - link_offset<Q>(i, g.nx, plane);
-            code = (m >= 0 && m < g.N) ? cmap[m] : kCmpBB;
+            const bool inside = ys >= 0 && ys < g.ny && zs >= 0 && zs < g.nz;
+            const long long m = ((long long)zs * g.ny + ys) * g.nx + xs;
+            code = inside ? cmap[m] : kCmpBB;
             if (code < 0) code = kCmpBB;
         }
         nbr[(long long)(i - 1) * nf + k] = code;
@@ -241,6 +243,13 @@ __device__ __forceinline__ void pull_cmp(T (&v)[Q], const T* __restrict__ src, l
                 v[i] = src[(long long)i * NF + code[i]];
             } else if (code[i] == kCmpBB) {
                 v[i] = loc[L::opp(i)];
+            } else if (sd.xin && bc.vel_inlet) {
+                // velocity inlet: moving-wall bounce-back, f_i = f*_opp(i) + 6 w_i (c_i . u_in) (rho_0 = 1)
+                const double* uin = inlet_velocity(bc.status);
+                double cu = 0.0;
+#pragma unroll
+                for (int a = 0; a < L::D; ++a) cu += (double)L::c(i, a) * uin[a];
+                v[i] = loc[L::opp(i)] + T(6.0 * L::w(i) * cu);
             } else {
                 const T cu = cdot<Q, T>(i, u);
                 v[i] = -loc[L::opp(i)] + T(2.0 * L::w(i)) * (drw + rwT * (T(4.5) * cu * cu - T(1.5) * uu));
@@ -441,8 +450,8 @@ __device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T*
         const int32_t co = code[o];
         if (co >= 0) {
             mu[j] = lam_in[(size_t)j * NF + co];
-        } else if (co == kCmpBB) {
-            mu[j] = lam_in[(size_t)o * NF + k];
+        } else if (co == kCmpBB || (sd.xin && bc.vel_inlet)) {
+            mu[j] = lam_in[(size_t)o * NF + k];  // the velocity inlet's source is constant
         } else {
             const T li = lam_in[(size_t)o * NF + k];
             mu[j] = -li;
@@ -524,6 +533,7 @@ __global__ void __launch_bounds__(kCmpThreads)
     const size_t NF = (size_t)c.nf;
     for (int side = 0; side < 2; ++side) {
         const bool xin = side == 0;
+        if (xin && bc.vel_inlet) continue;  // the velocity inlet does not use u_w
         const int32_t kb = cmap[row * g.nx + (xin ? 0 : g.nx - 1)];
         if (kb < 0) continue;
         int32_t cb[Q], ce[Q];

@@ -230,7 +230,7 @@ __global__ void k_fill_finalise(uint8_t* __restrict__ mask, long long N, unsigne
 
 template <int Q>
 __global__ void k_links(const uint8_t* __restrict__ mask, uint32_t* __restrict__ link, int nx, int ny, int nz,
-                        unsigned long long* __restrict__ fluid)
+                        int periodic_y, unsigned long long* __restrict__ fluid)
 {
     using L = Lattice<Q>;
     const long long N = (long long)nx * ny * nz;
@@ -245,7 +245,9 @@ __global__ void k_links(const uint8_t* __restrict__ mask, uint32_t* __restrict__
         uint32_t w = 0;
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
-            const int sx = x - L::c(i, 0), sy = y - L::c(i, 1), sz = z - L::c(i, 2);
+            const int sx = x - L::c(i, 0), sz = z - L::c(i, 2);
+            int sy = y - L::c(i, 1);
+            if (periodic_y) sy = (sy + ny) % ny;  // sy is in -1..ny
             if (sy < 0 || sy >= ny || sz < 0 || sz >= nz)
                 w |= 1u << i;
             else if (sx >= 0 && sx < nx && mask[((long long)sz * ny + sy) * nx + sx])
@@ -300,9 +302,9 @@ lbm_status geometry_launch(const PlanInfo& p, const lbm_geom_desc& g, uint8_t* m
         k_fill_finalise<<<blocks, 256, 0, s>>>(mask, N, cnt + 2);
     }
     if (p.q == 9)
-        k_links<9><<<blocks, 256, 0, s>>>(mask, link, nx, ny, nz, cnt + 3);
+        k_links<9><<<blocks, 256, 0, s>>>(mask, link, nx, ny, nz, p.geo.periodic_y, cnt + 3);
     else
-        k_links<19><<<blocks, 256, 0, s>>>(mask, link, nx, ny, nz, cnt + 3);
+        k_links<19><<<blocks, 256, 0, s>>>(mask, link, nx, ny, nz, p.geo.periodic_y, cnt + 3);
     k_geometry_info<<<1, 1, 0, s>>>(info, N, porosity);
     return cuda_status(cudaGetLastError());
 }

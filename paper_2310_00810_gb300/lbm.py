@@ -33,7 +33,7 @@ LBM_COLLISION_BGK, LBM_COLLISION_MRT = 0, 1
 ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
     "lbm_compact_size", "lbm_compact_bind", "lbm_set_abb_velocity", "lbm_get_abb_velocity",
-    "lbm_set_collision", "lbm_get_collision",
+    "lbm_set_collision", "lbm_get_collision", "lbm_set_periodic_y", "lbm_set_velocity_inlet",
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_probe_loss_grad", "lbm_spline_basis",
     "lbm_spline_profile", "lbm_spline_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
@@ -97,6 +97,8 @@ def load():
                 "lbm_compact_bind": [vp, C.c_int64, vp, vp],
                 "lbm_set_abb_velocity": [vp, i32],
                 "lbm_set_collision": [vp, i32, f64, f64, f64],
+                "lbm_set_periodic_y": [vp, i32],
+                "lbm_set_velocity_inlet": [vp, i32, f64, f64, f64],
                 "lbm_get_collision": [vp, C.POINTER(C.c_int32), vp],
                 "lbm_get_abb_velocity": [vp, C.POINTER(C.c_int32)],
                 "lbm_probe_loss_grad": [vp, vp, C.c_int64, vp, vp, f64, vp, vp, vp, vp],
@@ -270,6 +272,16 @@ def lbm_set_collision(plan: Plan, mode: int, s_e: float = 1.0, s_eps: float = 1.
            "lbm_set_collision")
 
 
+def lbm_set_periodic_y(plan: Plan, on: bool) -> None:
+    _check(load().lbm_set_periodic_y(plan.handle, 1 if on else 0), "lbm_set_periodic_y")
+
+
+def lbm_set_velocity_inlet(plan: Plan, u) -> None:
+    """u = (ux, uy[, uz]) turns the velocity inlet on; None turns it off (Eq. 6)."""
+    v = [0.0, 0.0, 0.0] if u is None else [float(a) for a in u] + [0.0] * (3 - len(u))
+    _check(load().lbm_set_velocity_inlet(plan.handle, 0 if u is None else 1, *v), "lbm_set_velocity_inlet")
+
+
 def lbm_get_collision(plan: Plan):
     """(mode, (s_e, s_eps, s_q))."""
     m = C.c_int32()
@@ -395,9 +407,12 @@ class Solver:
 
     def __init__(self, q, nx, ny, nz=1, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
                  loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST, geometry=None, device="cuda", link=None,
-                 mask=None, layout=None):
+                 mask=None, layout=None, periodic_y=False):
         self.device = torch.device(device)
         self.plan = Plan(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+        if periodic_y:  # before the geometry: it shapes the link words (fluid-only layout only)
+            lbm_set_periodic_y(self.plan, True)
+            layout = "compact"
         # the library replays its T-step sweeps as CUDA graphs on a non-default stream
         self.stream = torch.cuda.Stream(device=self.device)
         p = self.plan
@@ -487,6 +502,10 @@ class Solver:
     def set_collision(self, mode: int, s_e: float = 1.0, s_eps: float = 1.0, s_q: float = 1.0) -> None:
         """LBM_COLLISION_BGK (default) or LBM_COLLISION_MRT with the free rates (D2Q9)."""
         lbm_set_collision(self.plan, mode, s_e, s_eps, s_q)
+
+    def set_velocity_inlet(self, u) -> None:
+        """A velocity inlet u = (ux, uy[, uz]) through x = -1/2 (None: Eq. 6); fluid-only layout."""
+        lbm_set_velocity_inlet(self.plan, u)
 
     def set_abb_velocity(self, mode: int) -> None:
         """LBM_ABB_U_NODE (default) or LBM_ABB_U_EXTRAP: where Eq. 6 takes its velocity."""

@@ -1,0 +1,145 @@
+"""The cylinder-wake options on the GPU (fluid-only layout): periodic top and
+bottom and the velocity inlet, with BGK and MRT, against the oracle; the
+exact uniform-flow fixed point; and a viscosity inversion from a downstream
+velocity snapshot (section 3.4)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2310_00810_gb300 import invert as I
+from paper_2310_00810_gb300 import lbm
+from paper_2310_00810_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RATES = (1.64, 1.54, 1.9)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2310_00810_gb300 import build
+
+    build.build()
+    lbm.load()
+
+
+@pytest.fixture(autouse=True)
+def _oracle_defaults():
+    yield
+    O.set_periodic_y(False)
+    O.set_velocity_inlet(None)
+    O.set_collision(O.COLL_BGK)
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    den = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (den if den > 0 else 1.0)
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+
+
+def cylinder(nx, ny, cx, cy, d):
+    y, x = np.mgrid[0:ny, 0:nx]
+    return (((x - cx) ** 2 + (y - cy) ** 2) <= (d / 2) ** 2).astype(np.uint8)
+
+
+def wake_solver(m, precision, T, stride=0, mrt=True, u_in=(0.05, 0.0)):
+    ny, nx = m.shape
+    s = lbm.Solver(9, nx, ny, precision=precision, n_steps=T, ckpt_stride=stride, geometry=torch.as_tensor(m),
+                   periodic_y=True)
+    assert s.layout == "compact"
+    s.set_velocity_inlet(u_in)
+    if mrt:
+        s.set_collision(lbm.LBM_COLLISION_MRT, *RATES)
+    return s
+
+
+def test_options_are_checked():
+    s = wake_solver(np.zeros((8, 16), np.uint8), 8, 4)
+    with pytest.raises(lbm.LBMError) as e:
+        lbm.lbm_set_periodic_y(s.plan, True)  # after the geometry
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(lbm.LBMError) as e:
+        s.set_velocity_inlet((0.05, 0.0, 0.01))  # u_z on a D2Q9 plan
+    assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+    s.set_velocity_inlet((0.05, 0.0))
+    s.set_layout("dense")
+    with pytest.raises(lbm.LBMError) as e:
+        s.forward(dev([1.0]), dev([0.8]), 1.0)
+    assert e.value.status == lbm.LBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("mrt", [False, True])
+def test_uniform_flow_is_a_fixed_point(mrt):
+    nx, ny, u = 48, 16, (0.06, 0.0)
+    m = np.zeros((ny, nx), np.uint8)
+    s = wake_solver(m, 8, 1, mrt=mrt, u_in=u)
+    feq = O.equilibrium(9, np.ones(m.shape), np.stack([np.full(m.shape, u[0]), np.zeros(m.shape)]))
+    fs = feq - O.lattice(9)[1].reshape(9, 1, 1)
+    got = s.step(dev([1.0]), dev([0.7]), 1.0, dev(fs), 5).cpu().numpy()
+    np.testing.assert_allclose(got, fs, rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("precision", [8, 4])
+@pytest.mark.parametrize("mrt", [False, True])
+@pytest.mark.parametrize("stride", [0, 7])
+def test_wake_gradient_matches_oracle(precision, mrt, stride):
+    nx, ny, T, tau = 96, 40, 60, 0.62
+    m = cylinder(nx, ny, 20, 19.5, 8)
+    m[0, 20] = 1  # a solid node on y = 0 makes the wrap visible in the link words
+    s = wake_solver(m, precision, T, stride, mrt)
+    roi = np.zeros(m.shape, np.uint8)
+    roi[8:32, 40:80] = 1
+    ut = W.perturbation((2,) + m.shape, seed=71, scale=1e-3)
+    f = s.forward(dev([1.0]), dev([tau]), 1.0)
+    L, lam = s.loss_grad(f, dev(ut), dev(roi, torch.uint8))
+    g_in, g_tau = s.adjoint(dev([1.0]), dev([tau]), 1.0, lam)
+    _, u = s.macroscopic(f)
+    if mrt:
+        O.set_collision(O.COLL_MRT, *RATES)
+    with O.wake_options(periodic_y=True, velocity_inlet=(0.05, 0.0)):
+        Lw, _, g_tau_w, fT = O.gradient(9, m, 1.0, 1.0, tau, T, ut, roi=roi, ckpt_stride=5, return_fT=True)
+    _, uw = O.macroscopic(9, m, fT)
+    links = s.link.cpu().numpy().view(np.uint32).reshape(m.shape)
+    with O.wake_options(periodic_y=True):
+        assert np.array_equal(links, O.links(9, m))
+    if precision == 8:
+        assert rel(u.cpu().numpy(), uw) < 1e-11
+        assert abs(L.item() - Lw) <= 1e-10 * abs(Lw)
+        assert abs(g_tau.item() - g_tau_w) <= 1e-9 * abs(g_tau_w)
+    else:
+        assert rel(u.cpu().numpy(), uw) < 1e-4
+        assert abs(L.item() - Lw) <= 1e-4 * abs(Lw)
+        assert abs(g_tau.item() - g_tau_w) <= 1e-3 * abs(g_tau_w)
+    assert g_in.item() == 0.0  # the velocity inlet does not use rho_in
+
+
+def test_viscosity_inversion_from_a_downstream_snapshot():
+    """Section 3.4's inversion on a small wake (160 x 64, D = 8, u_in = 0.08,
+    MRT, T = 2000): from nu = 0.06 to the truth nu = 0.02 by L-BFGS on tau,
+    against the velocity snapshot in a rectangle downstream of the cylinder."""
+    nx, ny, T = 160, 64, 2000
+    m = cylinder(nx, ny, 32, 31.5, 8)
+    s = wake_solver(m, 8, T, u_in=(0.08, 0.0))
+    nu_true = 0.02
+    f = s.forward(dev([1.0]), dev([0.5 + 3 * nu_true]), 1.0)
+    _, ut = s.macroscopic(f)
+    roi = torch.zeros(m.shape, dtype=torch.uint8, device="cuda")
+    roi[:, 48:] = 1
+    tau_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rin = dev([1.0])
+
+    def evaluate(x):
+        tau_t.fill_(0.5 + 0.1 * float(x[0]))
+        fT = s.forward(rin, tau_t, 1.0)
+        L, lam = s.loss_grad(fT, ut, roi)
+        _, g_tau = s.adjoint(rin, tau_t, 1.0, lam)
+        return L.item(), np.array([g_tau.item() * 0.1])
+
+    res = I.lbfgs(evaluate, np.array([3 * 0.06 / 0.1]), max_evals=40, lower={0: 0.05},
+                  errors=lambda x: (abs(0.1 * x[0] / 3 - nu_true) / nu_true, None), done=lambda e: e[0] < 1e-3)
+    assert res.converged and res.evaluations <= 25, res.errs
