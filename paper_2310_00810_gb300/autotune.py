@@ -84,6 +84,10 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
     """Choose and (by default) apply the fastest kernel configuration for the
     solver's plan.  Returns {"choice": {...}, "timings_us": {...}}."""
     p = solver.plan
+    if getattr(solver, "periodic_y", False):
+        # periodic link words wrap in y, which only the fluid-only kernels follow: no dense candidates
+        return {"choice": lbm.lbm_plan_get_kernels(p), "layout": solver.layout, "timings_us": {},
+                "us_per_time_step": None, "skipped": "periodic y runs in the fluid-only layout only"}
     key = _key(p)
     if use_cache and cache:
         hit = _load(cache).get(key)

@@ -410,6 +410,7 @@ class Solver:
                  mask=None, layout=None, periodic_y=False):
         self.device = torch.device(device)
         self.plan = Plan(q, nx, ny, nz, precision, n_steps, ckpt_stride, loss_kind, loss_norm, inlet_kind)
+        self.periodic_y = bool(periodic_y)
         if periodic_y:  # before the geometry: it shapes the link words (fluid-only layout only)
             lbm_set_periodic_y(self.plan, True)
             layout = "compact"
