@@ -206,7 +206,10 @@ LBM_API lbm_status lbm_init_geometry(lbm_plan* plan, const lbm_geom_desc* g, uin
 
 /* Binds an existing link array (from lbm_init_geometry of a plan of the
  * same lattice size and Q) to this plan, so plans of different precision or
- * step count can share one geometry.  The pointer must stay valid. */
+ * step count can share one geometry.  The pointer must stay valid.  The
+ * array must come from a plan with the same lbm_set_periodic_y setting: the
+ * dense kernels trust the wall bits at y = 0 and ny - 1 to keep every pull
+ * inside the lattice. */
 LBM_API lbm_status lbm_bind_geometry(lbm_plan* plan, const uint32_t* d_link);
 
 /* Fluid-only ("compact") internal state layout.  The population traffic of
