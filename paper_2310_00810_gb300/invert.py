@@ -48,6 +48,34 @@ class InversionResult:
     err_history: list
 
 
+class SnapshotSeries:
+    """A loss summed over velocity snapshots at steps t_1 < ... < t_K (the wake
+    of section 3.4 observed over time rather than at one instant):
+        L = sum_k L_k(u(t_k)),  L_k the plan's final-step loss against u_k on the ROI.
+    Its gradient is the sum of the K single-snapshot gradients, each one
+    checkpointed sweep of t_k steps through the library (cost sum_k t_k steps;
+    the seeds are not injected into one shared reverse sweep).
+    make_solver(t) returns a solver of t steps with the geometry and options
+    of the problem; targets[k] is u_k (float64 [D, ...])."""
+
+    def __init__(self, make_solver, times, targets, roi=None):
+        if len(times) != len(targets) or not len(times):
+            raise ValueError("one target per snapshot time")
+        self.solvers = [make_solver(int(t)) for t in times]
+        self.targets = [u.contiguous() for u in targets]
+        self.roi = roi
+
+    def loss_and_grad(self, rho_in, tau, rho_out: float):
+        """(L, dL/drho_in, dL/dtau) as float64 tensors on the device."""
+        L = g_in = g_tau = None
+        for s, ut in zip(self.solvers, self.targets):
+            f = s.forward(rho_in, tau, rho_out)
+            l, lam = s.loss_grad(f, ut, self.roi)
+            gi, gt = s.adjoint(rho_in, tau, rho_out, lam)
+            L, g_in, g_tau = (l, gi, gt) if L is None else (L + l, g_in + gi, g_tau + gt)
+        return L, g_in, g_tau
+
+
 @dataclasses.dataclass
 class LbfgsResult:
     x: np.ndarray

@@ -143,3 +143,26 @@ def test_viscosity_inversion_from_a_downstream_snapshot():
     res = I.lbfgs(evaluate, np.array([3 * 0.06 / 0.1]), max_evals=40, lower={0: 0.05},
                   errors=lambda x: (abs(0.1 * x[0] / 3 - nu_true) / nu_true, None), done=lambda e: e[0] < 1e-3)
     assert res.converged and res.evaluations <= 25, res.errs
+
+
+def test_snapshot_series_gradient_matches_the_oracle():
+    """A loss over three snapshots (steps 40, 50, 60) equals the sum of the
+    oracle's single-snapshot losses, and so does its gradient."""
+    nx, ny, tau = 96, 40, 0.62
+    m = cylinder(nx, ny, 20, 19.5, 8)
+    times = (40, 50, 60)
+    targets = [W.perturbation((2,) + m.shape, seed=80 + k, scale=1e-3) for k in range(3)]
+    roi = np.zeros(m.shape, np.uint8)
+    roi[8:32, 40:80] = 1
+    series = I.SnapshotSeries(lambda t: wake_solver(m, 8, t), times, [dev(u) for u in targets],
+                              dev(roi, torch.uint8))
+    L, g_in, g_tau = series.loss_and_grad(dev([1.0]), dev([tau]), 1.0)
+    O.set_collision(O.COLL_MRT, *RATES)
+    Lw = gw = 0.0
+    with O.wake_options(periodic_y=True, velocity_inlet=(0.05, 0.0)):
+        for t, ut in zip(times, targets):
+            l, _, g = O.gradient(9, m, 1.0, 1.0, tau, t, ut, roi=roi, ckpt_stride=5)
+            Lw, gw = Lw + l, gw + g
+    assert abs(L.item() - Lw) <= 1e-10 * Lw
+    assert abs(g_tau.item() - gw) <= 1e-9 * abs(gw)
+    assert g_in.item() == 0.0
