@@ -23,7 +23,6 @@
 // (density and inlet-gradient slot of the row) and the conversions between
 // the caller's dense arrays and the internal compact states.
 #include <algorithm>
-#include <cstdlib>
 #include <type_traits>
 
 #include "device.cuh"
@@ -472,8 +471,8 @@ __device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T*
 // Adjoint step in the compact layout: the gather form of adjoint.cu.  The
 // forward copies f*_j(x) to x + c_j, the node that pulls direction j from x;
 // its compact index is nbr of direction opp(j) at k (x + c_j = x - c_opp(j)).
-template <int Q, typename T, bool T0, int NT = kCmpThreads>
-__global__ void __launch_bounds__(NT, 1024 / NT)
+template <int Q, typename T, bool T0>
+__global__ void __launch_bounds__(kCmpThreads, 4)
     k_adjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c, Geo g,
                   Bc bc, const double* __restrict__ tau, double* __restrict__ grad_acc,
                   double* __restrict__ partial)
@@ -630,34 +629,12 @@ void launch_adjoint(const PlanInfo& p, int t0, const void* gprev, const void* la
     const T* li = static_cast<const T*>(lam_in);
     T* lo = static_cast<T*>(lam_out);
     const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
-    // D3Q19 FP32: LBM_CMP_ADJ_THREADS = 128 / 256 / 512 sets the block size of the interior adjoint
-    // (the per-warp partials do not depend on it)
-    static const int nt = [] {
-        const char* e = std::getenv("LBM_CMP_ADJ_THREADS");
-        const int v = e ? std::atoi(e) : kCmpThreads;
-        return (v == 128 || v == 512) ? v : kCmpThreads;
-    }();
-    bool launched = false;
-    if constexpr (Q == 19 && std::is_same<T, float>::value) {
-        if (!t0 && nt != kCmpThreads) {
-            const dim3 g2((unsigned)((p.cmp.nf + nt - 1) / nt)), b2(nt);
-            if (nt == 128)
-                launch_k(p.pdl, k_adjoint_cmp<Q, T, false, 128>, g2, b2, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau,
-                         grad_acc, partial);
-            else
-                launch_k(p.pdl, k_adjoint_cmp<Q, T, false, 512>, g2, b2, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau,
-                         grad_acc, partial);
-            launched = true;
-        }
-    }
-    if (launched) {
-    } else if (t0) {
+    if (t0)
         launch_k(p.pdl, k_adjoint_cmp<Q, T, true>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
                  partial);
-    } else {
+    else
         launch_k(p.pdl, k_adjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
                  partial);
-    }
     if (bc.uw_extrap && !t0) {  // at t = 0 the fluid is at rest and the pass adds nothing
         const long long rows = (long long)p.geo.ny * p.geo.nz;
         launch_k(p.pdl, k_adjoint_uw_cmp<Q, T>, dim3((unsigned)((rows + kCmpThreads - 1) / kCmpThreads)), block, 0, s,
