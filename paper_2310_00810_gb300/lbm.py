@@ -505,8 +505,11 @@ class Solver:
         lbm_set_collision(self.plan, mode, s_e, s_eps, s_q)
 
     def set_velocity_inlet(self, u) -> None:
-        """A velocity inlet u = (ux, uy[, uz]) through x = -1/2 (None: Eq. 6); fluid-only layout."""
+        """A velocity inlet u = (ux, uy[, uz]) through x = -1/2 (None: Eq. 6).  It runs in the
+        fluid-only layout, which this switches to."""
         lbm_set_velocity_inlet(self.plan, u)
+        if u is not None and self.layout != "compact":
+            self.set_layout("compact")
 
     def set_abb_velocity(self, mode: int) -> None:
         """LBM_ABB_U_NODE (default) or LBM_ABB_U_EXTRAP: where Eq. 6 takes its velocity."""
