@@ -166,3 +166,17 @@ def test_snapshot_series_gradient_matches_the_oracle():
     assert abs(L.item() - Lw) <= 1e-10 * Lw
     assert abs(g_tau.item() - gw) <= 1e-9 * abs(gw)
     assert g_in.item() == 0.0
+
+
+def test_velocity_inlet_in_a_walled_channel():
+    """Without periodicity (walls at y = -1/2, ny - 1/2): the solver moves to
+    the fluid-only layout when the inlet is set, and matches the oracle."""
+    nx, ny, T = 64, 24, 30
+    m = cylinder(nx, ny, 20, 11.5, 6)
+    s = lbm.Solver(9, nx, ny, precision=8, n_steps=T, geometry=torch.as_tensor(m), layout="dense")
+    s.set_velocity_inlet((0.04, 0.0))
+    assert s.layout == "compact"
+    _, u = s.macroscopic(s.forward(dev([1.0]), dev([0.7]), 1.0))
+    with O.wake_options(periodic_y=False, velocity_inlet=(0.04, 0.0)):
+        _, uw = O.macroscopic(9, m, O.forward(9, m, 1.0, 1.0, 0.7, T))
+    assert rel(u.cpu().numpy(), uw) < 1e-11
