@@ -87,3 +87,42 @@ def test_spline_basis_host_call_matches_the_oracle(lib):
         with pytest.raises(lbm.LBMError) as e:
             lbm.lbm_spline_basis(K, n)
         assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_option_setters_validate_on_the_host(lib):
+    """The option calls are host-only: argument checks without a GPU."""
+    p9 = lbm.Plan(9, 64, 32, 1, 4, n_steps=4)
+    p19 = lbm.Plan(19, 32, 16, 16, 4, n_steps=4)
+
+    def status(fn):
+        try:
+            fn()
+        except lbm.LBMError as e:
+            return e.status
+        return lbm.LBM_OK
+
+    # MRT: D2Q9 only, rates in (0, 2)
+    assert status(lambda: lbm.lbm_set_collision(p19, lbm.LBM_COLLISION_MRT, 1.6, 1.5, 1.9)) == lbm.LBM_ERR_UNSUPPORTED
+    assert status(lambda: lbm.lbm_set_collision(p9, lbm.LBM_COLLISION_MRT, 2.0, 1.5, 1.9)) == lbm.LBM_ERR_INVALID_ARG
+    assert status(lambda: lbm.lbm_set_collision(p9, 2)) == lbm.LBM_ERR_INVALID_ARG
+    assert status(lambda: lbm.lbm_set_collision(p9, lbm.LBM_COLLISION_MRT, 1.6, 1.5, 1.9)) == lbm.LBM_OK
+    mode, rates = lbm.lbm_get_collision(p9)
+    assert mode == lbm.LBM_COLLISION_MRT and rates == (1.6, 1.5, 1.9)
+    assert status(lambda: lbm.lbm_set_collision(p9, lbm.LBM_COLLISION_BGK)) == lbm.LBM_OK
+    assert lbm.lbm_get_collision(p9) == (lbm.LBM_COLLISION_BGK, (0.0, 0.0, 0.0))
+    # Eq. 6 velocity
+    assert status(lambda: lbm.lbm_set_abb_velocity(p9, 3)) == lbm.LBM_ERR_INVALID_ARG
+    assert status(lambda: lbm.lbm_set_abb_velocity(p9, lbm.LBM_ABB_U_EXTRAP)) == lbm.LBM_OK
+    assert lbm.lbm_get_abb_velocity(p9) == lbm.LBM_ABB_U_EXTRAP
+    # velocity inlet: finite, no u_z on D2Q9
+    assert status(lambda: lbm.lbm_set_velocity_inlet(p9, (0.05, 0.0, 0.01))) == lbm.LBM_ERR_INVALID_ARG
+    assert status(lambda: lbm.lbm_set_velocity_inlet(p9, (float("nan"), 0.0))) == lbm.LBM_ERR_INVALID_ARG
+    assert status(lambda: lbm.lbm_set_velocity_inlet(p19, (0.05, 0.0, 0.01))) == lbm.LBM_OK
+    # periodic y before any geometry
+    assert status(lambda: lbm.lbm_set_periodic_y(p9, True)) == lbm.LBM_OK
+    assert lib.lbm_set_periodic_y(p9.handle, 2) == lbm.LBM_ERR_INVALID_ARG
+    # splines need a profile inlet and at most ny knots; probes need a workspace and geometry
+    assert lib.lbm_spline_profile(p9.handle, 4, 1, None, None, None, 1.0, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_spline_grad(p9.handle, 4, 1, None, None, None, None, None) == lbm.LBM_ERR_INVALID_ARG
+    assert lib.lbm_probe_loss_grad(p9.handle, None, -1, None, None, 1.0, None, None, None, None) == \
+        lbm.LBM_ERR_INVALID_ARG
