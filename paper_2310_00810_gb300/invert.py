@@ -48,6 +48,78 @@ class InversionResult:
     err_history: list
 
 
+class IterationLog:
+    """An lbfgs callback writing one JSON line per iteration (iteration,
+    evaluations, seconds, loss, error record, and x when it is short)."""
+
+    def __init__(self, path: str, max_x: int = 64):
+        self.path, self.max_x = path, max_x
+
+    def __call__(self, state: dict) -> None:
+        import json
+
+        rec = {k: state[k] for k in ("iteration", "evaluations", "seconds", "loss")}
+        rec["error"] = None if state["error"] is None else [None if v is None else float(v) for v in state["error"]]
+        if state["x"].size <= self.max_x:
+            rec["x"] = [float(v) for v in state["x"]]
+        with open(self.path, "a") as fh:
+            fh.write(json.dumps(rec) + "\n")
+
+
+class Checkpoint:
+    """An lbfgs callback saving the resumable state (x and the curvature pairs)
+    every `every` iterations to `path` (npz, written to a temporary file then
+    renamed, so a crash never leaves a torn file); Checkpoint.load(path)
+    returns (x, history, iteration, evaluations) for lbfgs(x0=x, history=history)."""
+
+    def __init__(self, path: str, every: int = 1):
+        self.path, self.every = path, every
+
+    def __call__(self, state: dict) -> None:
+        import os
+
+        if state["iteration"] % self.every:
+            return
+        tmp = self.path + ".tmp.npz"
+        n = state["x"].size
+        pairs = lambda vs: np.array(vs, np.float64).reshape(len(vs), n) if vs else np.zeros((0, n))
+        np.savez(tmp, x=state["x"], S=pairs(state["S"]), Y=pairs(state["Y"]), iteration=state["iteration"],
+                 evaluations=state["evaluations"])
+        os.replace(tmp, self.path)
+
+    @staticmethod
+    def load(path: str):
+        with np.load(path) as z:
+            return z["x"], (list(z["S"]), list(z["Y"])), int(z["iteration"]), int(z["evaluations"])
+
+
+class InjectedFailure(RuntimeError):
+    """Raised by a fault-injecting evaluation (LBM_INJECT_FAIL_AFTER)."""
+
+
+def inject_failures(evaluate, after: int | None = None):
+    """Host-side fault injection for recovery tests: the returned evaluation
+    raises InjectedFailure on its call number `after` + 1 (default: the
+    LBM_INJECT_FAIL_AFTER environment variable; unset, evaluate is returned
+    unchanged).  Nothing is injected on the GPU."""
+    import os
+
+    if after is None:
+        env = os.environ.get("LBM_INJECT_FAIL_AFTER")
+        if env is None:
+            return evaluate
+        after = int(env)
+    count = [0]
+
+    def wrapped(x):
+        count[0] += 1
+        if count[0] > after:
+            raise InjectedFailure(f"injected failure at evaluation {count[0]}")
+        return evaluate(x)
+
+    return wrapped
+
+
 class SnapshotSeries:
     """A loss summed over velocity snapshots at steps t_1 < ... < t_K (the wake
     of section 3.4 observed over time rather than at one instant):
@@ -87,7 +159,8 @@ class LbfgsResult:
     errs: list
 
 
-def lbfgs(evaluate, x0, max_evals=400, memory=20, errors=None, done=None, lower=None, time_limit=None):
+def lbfgs(evaluate, x0, max_evals=400, memory=20, errors=None, done=None, lower=None, time_limit=None,
+          callback=None, history=None):
     """Limited-memory BFGS (two-loop recursion) with a secant step along each
     direction, exact for a quadratic loss.  evaluate(x) -> (loss, gradient);
     errors(x) -> a record stored per iteration and done(record) -> stop;
@@ -95,12 +168,17 @@ def lbfgs(evaluate, x0, max_evals=400, memory=20, errors=None, done=None, lower=
     step is shortened to reach at most the bound).  A secant point is taken
     only if it lowers the loss, and a step whose loss is non-finite or larger
     is halved until it is not; a non-finite loss that halving cannot cure
-    ends the run."""
+    ends the run.
+    callback(state) runs after every iteration with a dict of the iteration,
+    evaluations, seconds, loss, error record, x and the curvature pairs S, Y;
+    history = (S, Y) from such a state resumes a run at its x exactly."""
     t_start = time.perf_counter()
     x = np.array(x0, np.float64)
     f, g = evaluate(x)
     evals = 1
     S, Y, losses, errs = [], [], [f], []
+    if history is not None:
+        S, Y = [np.array(v, np.float64) for v in history[0]], [np.array(v, np.float64) for v in history[1]]
     converged = False
     it = 0
     while evals < max_evals:
@@ -152,13 +230,15 @@ def lbfgs(evaluate, x0, max_evals=400, memory=20, errors=None, done=None, lower=
                 Y.pop(0)
         x, f, g = x + sv, f1, g1
         losses.append(f)
-        if errors is not None:
-            e = errors(x)
-            if e is not None:
-                errs.append(e)
-                if done is not None and done(e):
-                    converged = True
-                    break
+        e = errors(x) if errors is not None else None
+        if e is not None:
+            errs.append(e)
+        if callback is not None:
+            callback({"iteration": it, "evaluations": evals, "seconds": time.perf_counter() - t_start, "loss": f,
+                      "error": e, "x": x.copy(), "S": [v.copy() for v in S], "Y": [v.copy() for v in Y]})
+        if e is not None and done is not None and done(e):
+            converged = True
+            break
         if time_limit is not None and time.perf_counter() - t_start > time_limit:
             break
     return LbfgsResult(x, it, evals, time.perf_counter() - t_start, converged, losses, errs)
@@ -204,6 +284,28 @@ class Inversion:
         self.g_in = torch.zeros(p.n_in, dtype=torch.float64, device=dev)
         self.g_tau = torch.zeros(1, dtype=torch.float64, device=dev)
         self.t = 0
+
+    def state_dict(self) -> dict:
+        """The Adam inversion's resumable state (host copies)."""
+        keys = ("theta", "m", "v", "theta_tau", "m_tau", "v_tau", "rho_in", "tau")
+        d = {k: getattr(self, k).detach().cpu().clone() for k in keys}
+        d["t"] = self.t
+        return d
+
+    def load_state_dict(self, d: dict) -> None:
+        for k in ("theta", "m", "v", "theta_tau", "m_tau", "v_tau", "rho_in", "tau"):
+            getattr(self, k).copy_(d[k])
+        self.t = int(d["t"])
+
+    def save(self, path: str) -> None:
+        """torch.save of state_dict(), through a temporary file and a rename."""
+        import os
+
+        torch.save(self.state_dict(), path + ".tmp")
+        os.replace(path + ".tmp", path)
+
+    def load(self, path: str) -> None:
+        self.load_state_dict(torch.load(path, map_location="cpu"))
 
     def _loss_and_seed(self):
         s, p, st = self.s, self.s.plan, self.s.stream
@@ -292,15 +394,21 @@ class Inversion:
         return INLET_SCALE * (x_in if self.spline is None else self.spline[2] @ x_in)
 
     def run_lbfgs(self, max_evals: int = 400, tol: float = 1e-3, truth_delta=None, truth_tau=None,
-                  memory: int = 20, time_limit: float | None = None) -> InversionResult:
+                  memory: int = 20, time_limit: float | None = None, callback=None,
+                  resume=None) -> InversionResult:
         """L-BFGS on the scaled parameters until the relative error on delta
-        (and nu) is <= tol, or max_evals gradient evaluations / time_limit."""
+        (and nu) is <= tol, or max_evals gradient evaluations / time_limit.
+        callback: an lbfgs callback (IterationLog, Checkpoint); resume = (x,
+        history) from Checkpoint.load continues a run where it stopped."""
         p = self.s.plan
         n = self._n_par()
         self.tau_fixed = float(self.tau.cpu().item())
         x = self.theta.cpu().numpy().copy() if self.spline is None else np.zeros(n)
         if self.invert_tau:
             x = np.concatenate([x, self.theta_tau.cpu().numpy()])
+        history = None
+        if resume is not None:
+            x, history = np.array(resume[0], np.float64), resume[1]
         td = None if truth_delta is None else np.broadcast_to(np.asarray(truth_delta, np.float64), (p.n_in,))
         nu_true = None if truth_tau is None else (truth_tau - 0.5) / 3.0
 
@@ -317,8 +425,9 @@ class Inversion:
             return e[0] <= tol and (e[1] is None or e[1] <= tol)
 
         torch.cuda.synchronize(self.s.device)
-        r = lbfgs(self._evaluate, x, max_evals=max_evals, memory=memory, errors=errors, done=done,
-                  lower=({n: TAU_MIN_THETA} if self.invert_tau else None), time_limit=time_limit)
+        r = lbfgs(inject_failures(self._evaluate), x, max_evals=max_evals, memory=memory, errors=errors, done=done,
+                  lower=({n: TAU_MIN_THETA} if self.invert_tau else None), time_limit=time_limit, callback=callback,
+                  history=history)
         x = r.x
         self.theta.copy_(torch.from_numpy(self._delta(x[:n]) / INLET_SCALE))
         if self.invert_tau:

@@ -63,3 +63,87 @@ def test_non_finite_trials_are_halved_away():
     res = I.lbfgs(ev, np.array([-1.9, 0.0, 1.9]), max_evals=200,
                   errors=lambda x: (float(np.max(np.abs(x - x_star))), None), done=lambda e: e[0] < 1e-9)
     assert res.converged and all(np.isfinite(l) for l in res.losses)
+
+
+def _problem():
+    r = np.random.Generator(np.random.PCG64(7))
+    n = 5
+    Q = r.normal(size=(n, n))
+    A = Q @ Q.T + n * np.eye(n)
+    b = r.normal(size=n)
+
+    def ev(x):  # a quadratic plus a quartic term: several iterations, not exact after n
+        return 0.5 * x @ A @ x - b @ x + 0.05 * np.sum(x ** 4), A @ x - b + 0.2 * x ** 3
+
+    return ev, n
+
+
+def test_iteration_log_writes_one_json_line_per_iteration(tmp_path):
+    import json
+
+    ev, n = _problem()
+    path = str(tmp_path / "log.jsonl")
+    res = I.lbfgs(ev, np.zeros(n), max_evals=30, errors=lambda x: (float(np.linalg.norm(x)), None),
+                  callback=I.IterationLog(path))
+    lines = [json.loads(l) for l in open(path)]
+    assert [l["iteration"] for l in lines] == list(range(1, res.iterations + 1))
+    assert lines[-1]["loss"] == res.losses[-1] and len(lines[-1]["x"]) == n
+
+
+def test_checkpoint_resume_after_an_injected_failure_is_exact(tmp_path):
+    """A run that fails (host-side injection) after 11 evaluations, resumed
+    from its last checkpoint, ends at the same point, bit for bit, as a run
+    that never failed."""
+    ev, n = _problem()
+    kw = dict(max_evals=60, errors=lambda x: (float(np.linalg.norm(ev(x)[1])), None), done=lambda e: e[0] < 1e-12)
+    whole = I.lbfgs(ev, np.zeros(n), **kw)
+    path = str(tmp_path / "ckpt.npz")
+    try:
+        I.lbfgs(I.inject_failures(ev, after=11), np.zeros(n), callback=I.Checkpoint(path), **kw)
+        assert False, "the injected failure did not fire"
+    except I.InjectedFailure:
+        pass
+    x, history, it, evals = I.Checkpoint.load(path)
+    assert 0 < it and evals <= 11
+    rest = I.lbfgs(ev, x, history=history, **kw)
+    assert whole.converged and rest.converged
+    assert np.array_equal(rest.x, whole.x)
+
+
+def test_injection_reads_the_environment(monkeypatch):
+    ev, n = _problem()
+    assert I.inject_failures(ev) is ev
+    monkeypatch.setenv("LBM_INJECT_FAIL_AFTER", "2")
+    f = I.inject_failures(ev)
+    f(np.zeros(n))
+    f(np.zeros(n))
+    try:
+        f(np.zeros(n))
+        assert False
+    except I.InjectedFailure:
+        pass
+
+
+def test_adam_state_round_trip(tmp_path):
+    """The Adam inversion's state (theta, moments, step count, derived rho_in
+    and tau) saves and restores exactly; host-only, with a stand-in solver."""
+    import types
+
+    import torch
+
+    plan = types.SimpleNamespace(n_in=6, ny=6, nz=1)
+    solver = types.SimpleNamespace(plan=plan, device=torch.device("cpu"),
+                                   new_state=lambda: torch.zeros((9, 6, 12), dtype=torch.float64))
+    inv = I.Inversion(solver, torch.zeros((2, 6, 12), dtype=torch.float64), 1.0, theta0=0.3, tau0=0.9,
+                      invert_tau=True)
+    r = np.random.Generator(np.random.PCG64(1))
+    for k in ("theta", "m", "v", "theta_tau", "m_tau", "v_tau", "rho_in", "tau"):
+        getattr(inv, k).copy_(torch.as_tensor(r.normal(size=getattr(inv, k).shape)))
+    inv.t = 17
+    path = str(tmp_path / "adam.pt")
+    inv.save(path)
+    other = I.Inversion(solver, torch.zeros((2, 6, 12), dtype=torch.float64), 1.0)
+    other.load(path)
+    assert other.t == 17
+    for k in ("theta", "m", "v", "theta_tau", "m_tau", "v_tau", "rho_in", "tau"):
+        assert torch.equal(getattr(other, k), getattr(inv, k)), k
