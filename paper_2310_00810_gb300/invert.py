@@ -19,6 +19,12 @@ The host reads back only the small parameter vector when it checks the stop
 rule.  ``truth`` (optional) turns on the relative-error stop used for
 time-to-target measurements: |delta - delta*| / |delta*| on delta = rho_in -
 rho_out, and |nu - nu*| / |nu*| for tau.
+
+Also here: the pure L-BFGS routine ``lbfgs`` (any evaluation function), the
+density-probe and spline-knot variants of the inversion, ``SnapshotSeries``
+(a loss over several observation times), and host-side recovery helpers:
+``IterationLog`` (JSON lines), ``Checkpoint`` (exact resume), Adam state
+``save``/``load`` and ``inject_failures`` (fault injection for tests).
 """
 from __future__ import annotations
 
