@@ -652,9 +652,7 @@ def run_e2e(P, args, device, barrier, world):
 # DRAM bytes (read + write) per launch on the roofline lattices, from one ncu capture of each kernel
 # on a smaller lattice of the same recipe, scaled by the fluid nodes processed (traffic grows in
 # proportion): dense TMA kernels from disks4096x2048 (x 4 nodes), compact kernels from
-# disks4096x2048 (x 4.0001 fluid nodes) and spheres256x128x128 (x 8.0006 fluid nodes).  Summaries in
-# profiles/ (k_step_tma_halo_disks4096x2048.md, k_adjoint_tma_halo_disks4096x2048.md,
-# k_step_cmp_gs_disks4096x2048.md, k_step_cmp_spheres256x128x128.md, k_adjoint_cmp_*.md).
+# disks4096x2048 (x 4.0001 fluid nodes) and spheres256x128x128 (x 8.0006 fluid nodes).
 HBM_TRAFFIC = {
     ("disks8192x4096", "dense"): {"stream-collide": 4 * (343.118080e6 + 201.248512e6),
                                   "adjoint": 4 * (642.651648e6 + 217.033472e6)},

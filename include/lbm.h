@@ -99,7 +99,8 @@ typedef struct lbm_plan lbm_plan;
 
 /* Creates a plan for one lattice (host memory only; no device allocation).
  * Errors: INVALID_ARG for an unsupported q/precision, non-positive sizes,
- * nz != 1 with q = 9, T < 1 or a negative stride. */
+ * ny or nz above 65535 (the kernels put rows and layers on the grid's y and
+ * z dimensions), nz != 1 with q = 9, T < 1 or a negative stride. */
 LBM_API lbm_status lbm_plan_create(const lbm_desc* desc, lbm_plan** out);
 LBM_API lbm_status lbm_plan_destroy(lbm_plan* plan);
 
@@ -286,7 +287,11 @@ LBM_API lbm_status lbm_loss_grad(lbm_plan* plan, const void* d_f, const double* 
  *    LBM_ERR_INVALID_ARG; use lbm_loss_grad for those.
  *  - The first call on a device looks up the array's device address for
  *    that device (with it current); make that first call before any stream
- *    capture.
+ *    capture.  The address is kept with the id of the CUDA context it was
+ *    taken in: after a device reset (cudaDeviceReset) the next call runs in a
+ *    new context and looks the address up again (again: before any capture).
+ *    The call makes the current device's primary context current on the
+ *    calling thread (cudaSetDevice).
  *  - All calls share the one array, which keeps the last call's contents:
  *    calls whose kernels may overlap on the GPU (different streams without
  *    ordering between them) race on it and must be serialised by the caller.
@@ -318,7 +323,7 @@ LBM_API lbm_status lbm_probe_loss_grad(lbm_plan* plan, const void* d_f, int64_t 
                                        const double* d_rho_target, double weight, double* d_loss, void* d_lambda,
                                        void* d_ws, void* stream);
 
-/* Cubic-spline inlet profiles (section 3.1.3: the multi-parameter inversion
+/* Cubic-spline inlet profiles (section 3.1.2: the multi-parameter inversion
  * imposes the inlet pressure as a cubic spline through a few inlet
  * densities).  Knot values c[Kz][Ky] give
  *   rho_in[z ny + y] = rho_out + sum_{b,a} Bz[z][b] By[y][a] c[b][a],

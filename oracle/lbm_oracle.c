@@ -17,7 +17,8 @@
  *                             + 2 w_i rho_w (1 + (u.c_i)^2/(2 c_s^4) - u.u/(2 c_s^2))
  *   "Bounce Back" stage (section 2.2): halfway, link-wise bounce-back at
  *   grain nodes and at the walls y = -1/2, ny - 1/2 (and z = -1/2, nz - 1/2).
- * Readings of garbled or silent passages (see the design notes): sums run
+ * Readings of garbled or silent passages (Eq. 1-2, Eq. 4, section 3.2, Eq. 6,
+ * and the "Bounce Back" stage of section 2.2): sums run
  * over i = 0..Q-1; the BGK sign is -(f - f^eq)/tau; c_s^2 = 1/3; u_w in
  * Eq. 6 is the boundary node's own velocity at time t (or, as an option,
  * that velocity extrapolated to the pressure plane: set_abb_velocity); a

@@ -1,6 +1,6 @@
 """FP64 oracle of the cubic-spline inlet profile (test infrastructure only).
 
-Section 3.1.3 imposes the target inlet pressure of the multi-parameter
+Section 3.1.2 imposes the target inlet pressure of the multi-parameter
 inversion as a cubic spline through a few inlet densities.  Stated here from
 the definition of the natural cubic spline:
 

@@ -276,6 +276,7 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     if (d->q != 9 && d->q != 19) return LBM_ERR_INVALID_ARG;
     if (d->precision != 4 && d->precision != 8) return LBM_ERR_INVALID_ARG;
     if (d->nx < 2 || d->ny < 1 || d->nz < 1) return LBM_ERR_INVALID_ARG;
+    if (d->ny > 65535 || d->nz > 65535) return LBM_ERR_INVALID_ARG;  // grid.y = ny, grid.z = nz
     if (d->q == 9 && d->nz != 1) return LBM_ERR_INVALID_ARG;
     if (d->n_steps < 1 || d->ckpt_stride < 0) return LBM_ERR_INVALID_ARG;
     if (d->loss_kind != LBM_LOSS_VEC && d->loss_kind != LBM_LOSS_NORM) return LBM_ERR_INVALID_ARG;

@@ -474,7 +474,8 @@ lbm_status lbm_batch_create(const lbm_desc* c, int32_t n, const int32_t* nx, con
     const int vec = (c->q == 9 && c->precision == 4) ? 4 : 2;
     long long so = 0, no = 0, vo = 0, io = 0, ao = 0;
     for (int i = 0; i < n; ++i) {
-        if (nx[i] < 2 || ny[i] < 1 || nz[i] < 1 || (c->q == 9 && nz[i] != 1) || nx[i] % vec != 0) {
+        if (nx[i] < 2 || ny[i] < 1 || nz[i] < 1 || ny[i] > 65535 || nz[i] > 65535 || (c->q == 9 && nz[i] != 1) ||
+            nx[i] % vec != 0) {
             delete b;
             return LBM_ERR_INVALID_ARG;
         }

@@ -5,6 +5,10 @@
 // All sums over nodes are FP64: per-block partials (warp shuffles, then
 // shared memory) followed by one fixed-order pass, so results are
 // deterministic run to run.
+#include <cuda.h>
+
+#include <mutex>
+
 #include "device.cuh"
 
 namespace lbm {
@@ -169,7 +173,7 @@ __global__ void k_loss_final(const double* __restrict__ partial, int nb, double*
     const double L = block_reduce_array(partial, nb);
     if (threadIdx.x == 0) {
         *d_loss = L;
-        if (!isfinite(L)) atomicOr(status, 1u << LBM_ERR_NONFINITE);
+        if (status && !isfinite(L)) atomicOr(status, 1u << LBM_ERR_NONFINITE);
     }
 }
 
@@ -206,15 +210,52 @@ lbm_status loss_launch(const PlanInfo& p, const void* f, const double* u_target,
 
 // ------------------------------------------- loss without a workspace
 
-// Scratch of lbm_loss_grad_noalloc: a status slot and two scalars, then one
-// FP64 partial per thread block of the loss grid.  Every GPU that loads the
-// library holds this array until the process exits.
-constexpr int kNoallocHead = 32;  // doubles before the partials (status, count, weight, padding)
+// Scratch of lbm_loss_grad_noalloc: two scalars, then one FP64 partial per
+// thread block of the loss grid.  Every GPU that loads the library holds this
+// array until the process exits.
+constexpr int kNoallocHead = 32;  // doubles before the partials (count, weight, padding)
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocHead + LBM_NOALLOC_MAX_BLOCKS];
 
 namespace {
 constexpr int kMaxDevices = 64;
-double* g_noalloc_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+// The array's device address is looked up once per device and context: a
+// device reset (cudaDeviceReset) or a new primary context loads the module
+// again, possibly at another address, so the cached address is kept with the
+// id of the context it was taken in and looked up again when that id changes.
+struct NoallocAddr {
+    unsigned long long ctx_id = 0;
+    double* addr = nullptr;
+};
+NoallocAddr g_noalloc_addr[kMaxDevices];
+std::mutex g_noalloc_mu;
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context (driver entry points fetched
+// through the runtime, so the library does not link the driver library).
+bool current_context_id(unsigned long long* id)
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_current || !get_id) {
+        void* a = nullptr;
+        void* b = nullptr;
+        cudaDriverEntryPointQueryResult qa, qb;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa) != cudaSuccess ||
+            qa != cudaDriverEntryPointSuccess || !a)
+            return false;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb) != cudaSuccess ||
+            qb != cudaDriverEntryPointSuccess || !b)
+            return false;
+        get_current = reinterpret_cast<PfnCtxGetCurrent>(a);
+        get_id = reinterpret_cast<PfnCtxGetId>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
 }  // namespace
 
 lbm_status loss_launch_noalloc(const PlanInfo& p, const void* f, const double* u_target, const uint8_t* roi, int kind,
@@ -224,21 +265,29 @@ lbm_status loss_launch_noalloc(const PlanInfo& p, const void* f, const double* u
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return LBM_ERR_UNSUPPORTED;
-    // One-time set-up per device (with that device current): the host-side
-    // name of the array is not a device address, so ask the runtime for it.
-    double* base = __atomic_load_n(&g_noalloc_addr[dev], __ATOMIC_ACQUIRE);
-    if (!base) {
-        void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LBM_ERR_CUDA;
-        base = static_cast<double*>(ptr);
-        __atomic_store_n(&g_noalloc_addr[dev], base, __ATOMIC_RELEASE);
+    // makes the device's primary context current on this thread (the runtime
+    // initialises it here), so that its id can be read; allocates nothing
+    if (cudaSetDevice(dev) != cudaSuccess) return LBM_ERR_CUDA;
+    unsigned long long ctx_id = 0;
+    if (!current_context_id(&ctx_id)) return LBM_ERR_CUDA;
+    double* base = nullptr;
+    {
+        // set-up per device and context (with that device current): the
+        // host-side name of the array is not a device address, so ask the
+        // runtime for it
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        NoallocAddr& a = g_noalloc_addr[dev];
+        if (!a.addr || a.ctx_id != ctx_id) {
+            void* ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LBM_ERR_CUDA;
+            a.addr = static_cast<double*>(ptr);
+            a.ctx_id = ctx_id;
+        }
+        base = a.addr;
     }
-    uint32_t* status = reinterpret_cast<uint32_t*>(base);
-    double* scalars = base + 1;  // [0] ROI fluid count, [1] loss weight
+    double* scalars = base;  // [0] ROI fluid count, [1] loss weight
     double* partial = base + kNoallocHead;
-    // the status slot is OR-ed into, so it must start at zero; the scalars and
-    // the partials are fully overwritten before they are read
-    if (cudaMemsetAsync(status, 0, sizeof(double), s) != cudaSuccess) return LBM_ERR_CUDA;
+    // the scalars and the partials are fully overwritten before they are read
     k_count_roi<<<p.grid, kStepThreads, 0, s>>>(p.geo, roi, partial);
     k_loss_weight<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, norm == LBM_NORM_MEAN_FLUID, scalars);
 #define LBM_NOALLOC_LOSS(Q, T)                                                                                     \
@@ -258,7 +307,8 @@ lbm_status loss_launch_noalloc(const PlanInfo& p, const void* f, const double* u
     else if (p.q == 19 && p.prec == 8) LBM_NOALLOC_LOSS(19, double);
     else return LBM_ERR_UNSUPPORTED;
 #undef LBM_NOALLOC_LOSS
-    k_loss_final<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, d_loss, status);
+    // no status word on this path: a non-finite loss shows as NaN/Inf in d_loss
+    k_loss_final<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, d_loss, nullptr);
     return cuda_status(cudaGetLastError());
 }
 

@@ -1,4 +1,4 @@
-// Cubic-spline inlet profiles (arXiv 2310.00810, section 3.1.3: the
+// Cubic-spline inlet profiles (arXiv 2310.00810, section 3.1.2: the
 // multi-parameter inversion imposes the inlet pressure as a cubic spline
 // through a few inlet densities).  Knot values c[Kz][Ky] map linearly to the
 // inlet density,

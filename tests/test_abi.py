@@ -45,7 +45,8 @@ def test_nothing_else_is_exported(lib):
 
 @pytest.mark.parametrize("bad", [
     dict(q=7), dict(precision=2), dict(nx=1), dict(ny=0), dict(nz=2), dict(n_steps=0), dict(ckpt_stride=-1),
-    dict(loss_kind=5), dict(inlet_kind=3),
+    dict(loss_kind=5), dict(inlet_kind=3), dict(ny=65536),
+    dict(q=19, nx=4, ny=4, nz=65536),
 ])
 def test_plan_create_rejects_bad_descriptors(lib, bad):
     args = dict(q=9, nx=64, ny=32, nz=1, precision=4, n_steps=10, ckpt_stride=0, loss_kind=0, loss_norm=0,
@@ -54,6 +55,12 @@ def test_plan_create_rejects_bad_descriptors(lib, bad):
     with pytest.raises(lbm.LBMError) as e:
         lbm.Plan(**args)
     assert e.value.status == lbm.LBM_ERR_INVALID_ARG
+
+
+def test_plan_create_accepts_the_largest_grid_rows(lib):
+    """ny = 65535 (nz = 65535) is the last row (layer) count a launch grid holds."""
+    lbm.Plan(9, 2, 65535, 1, 4, n_steps=1)
+    lbm.Plan(19, 2, 2, 65535, 4, n_steps=1)
 
 
 def test_workspace_size_counts_checkpoints(lib):

@@ -2,12 +2,12 @@
 the benchmark uses (autotuned layout and kernel family).
 
 The 512x256 D2Q9 disk packing (20000 steps in the benchmark) and the
-128x64x64 D3Q19 sphere packing (10000 steps) are too long for the oracle at
-their full step counts, so the oracle checks every output of shorter runs
-on the full lattices, and properties that hold at any step count are checked
-at the full T: the rest state is a fixed point when rho_in = rho_out, and the
-adjoint gradient of an FP64 plan matches a central difference of its own
-forward sweep."""
+128x64x64 D3Q19 sphere packing (10000 steps): the oracle checks every output
+of shorter runs on the full lattices (FP32 and both layouts), and the FP32
+velocity (both lattices) and gradient (D2Q9) at the full step counts.
+Properties that hold at any step count are checked at the full T too: the
+rest state is a fixed point when rho_in = rho_out, and the adjoint gradient
+of an FP64 plan matches a central difference of its own forward sweep."""
 import os
 
 import numpy as np
@@ -121,3 +121,49 @@ def test_fullsize_fp64_gradient_matches_central_difference(name, T):
     Lm, _ = s.loss_grad(s.forward(dev([wl.rho_out + h - e]), tau, wl.rho_out), dev(ut))
     fd = (Lp.item() - Lm.item()) / (2 * e)
     assert abs(g_in.item() - fd) <= 1e-5 * abs(fd)
+
+
+# The benchmark lattices at their FULL step counts, FP32, in the benchmark's
+# (autotuned) launch configuration, against the FP64 oracle run to the same
+# T.  This is where FP32 drift over tens of thousands of steps would show:
+# the bound is 1e-4 relative L2 on the (near-)steady velocity and 1e-3
+# relative on the gradients.  The oracle takes a few minutes on the host cores.
+
+
+def test_fullsize_fp32_d2q9_velocity_and_gradient_at_full_T():
+    """512x256 D2Q9 FP32, T = 20000, the 256-entry profile: the velocity of
+    f^T, then the loss, dL/drho_in and dL/dtau of one checkpointed gradient
+    evaluation, against one oracle reverse sweep (sqrt(T) checkpoints; it
+    also returns its f^T)."""
+    name = "disks512x256"
+    wl = W.WORKLOADS[name]
+    _, s = make(name, wl.steps)
+    m = s.mask_field.cpu().numpy()
+    rin = inlet_of(wl, s)
+    ut = W.perturbation((s.plan.d, *m.shape), seed=2003, scale=1e-4)
+    f = s.forward(dev(rin), dev([wl.tau]), wl.rho_out)
+    _, u = s.macroscopic(f)
+    L, lam = s.loss_grad(f, dev(ut))
+    g_in, g_tau = s.adjoint(dev(rin), dev([wl.tau]), wl.rho_out, lam)
+    Lw, g_in_w, g_tau_w, fT_w = O.gradient(wl.q, m, oracle_inlet(wl, rin), wl.rho_out, wl.tau, wl.steps, ut,
+                                           ckpt_stride=int(np.ceil(np.sqrt(wl.steps))), return_fT=True)
+    _, u_w = O.macroscopic(wl.q, m, fT_w)
+    assert rel(u.cpu().numpy(), u_w) < 1e-4
+    assert abs(L.item() - Lw) <= 1e-4 * abs(Lw)
+    assert rel(g_in.cpu().numpy(), np.ravel(g_in_w)) < 1e-3
+    assert abs(g_tau.item() - g_tau_w) <= 1e-3 * abs(g_tau_w)
+
+
+def test_fullsize_fp32_d3q19_velocity_at_full_T():
+    """128x64x64 D3Q19 FP32 duct, T = 10000, fluid-only layout (the
+    benchmark's), constant head: the velocity of f^T against the oracle."""
+    name = "spheres128x64x64"
+    wl = W.WORKLOADS[name]
+    _, s = make(name, wl.steps, layout="compact")
+    m = s.mask_field.cpu().numpy()
+    rin = inlet_of(wl, s)
+    f = s.forward(dev(rin), dev([wl.tau]), wl.rho_out)
+    _, u = s.macroscopic(f)
+    want = O.forward(wl.q, m, oracle_inlet(wl, rin), wl.rho_out, wl.tau, wl.steps)
+    _, u_w = O.macroscopic(wl.q, m, want)
+    assert rel(u.cpu().numpy(), u_w) < 1e-4

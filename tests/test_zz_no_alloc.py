@@ -28,12 +28,14 @@ def _dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
-@pytest.mark.parametrize("q,precision,norm,kind", [
-    (9, 4, lbm.LBM_NORM_SUM, lbm.LBM_LOSS_VEC),
-    (9, 8, lbm.LBM_NORM_MEAN_FLUID, lbm.LBM_LOSS_NORM),
-    (19, 4, lbm.LBM_NORM_MEAN_FLUID, lbm.LBM_LOSS_VEC),
+@pytest.mark.parametrize("q,precision,norm,kind,with_roi", [
+    (9, 4, lbm.LBM_NORM_SUM, lbm.LBM_LOSS_VEC, True),
+    (9, 8, lbm.LBM_NORM_MEAN_FLUID, lbm.LBM_LOSS_NORM, True),
+    (19, 4, lbm.LBM_NORM_MEAN_FLUID, lbm.LBM_LOSS_VEC, True),
+    (9, 4, lbm.LBM_NORM_MEAN_FLUID, lbm.LBM_LOSS_VEC, False),  # no ROI: the mean over every fluid node
+    (19, 8, lbm.LBM_NORM_SUM, lbm.LBM_LOSS_NORM, False),
 ])
-def test_noalloc_matches_workspace_loss_twice(q, precision, norm, kind):
+def test_noalloc_matches_workspace_loss_twice(q, precision, norm, kind, with_roi):
     if q == 9:
         shape, g = (96, 260), dict(kind=lbm.LBM_GEOM_DISKS, seed=5, r_min=3, r_max=8, target_porosity=0.65)
     else:
@@ -41,7 +43,7 @@ def test_noalloc_matches_workspace_loss_twice(q, precision, norm, kind):
     nx, ny, nz = shape[-1], shape[-2], (shape[0] if q == 19 else 1)
     s = lbm.Solver(q, nx, ny, nz, precision=precision, n_steps=1, loss_kind=kind, loss_norm=norm, geometry=g)
     d = 2 if q == 9 else 3
-    roi = _dev(W.roi_band(shape, axis=len(shape) - 1, start=nx // 4), torch.uint8)
+    roi = _dev(W.roi_band(shape, axis=len(shape) - 1, start=nx // 4), torch.uint8) if with_roi else None
     for call in range(2):
         f = _dev(W.perturbation((q,) + shape, seed=100 + call, scale=2e-3), s.plan.dtype)
         ut = _dev(W.perturbation((d,) + shape, seed=200 + call, scale=3e-3))
@@ -54,9 +56,32 @@ def test_noalloc_matches_workspace_loss_twice(q, precision, norm, kind):
         assert torch.equal(lam, want_lam)
 
 
+def test_noalloc_allocates_nothing():
+    """After a first call (which looks up the scratch address), further calls
+    leave the device's free memory and torch's allocator untouched."""
+    shape = (64, 200)
+    s = lbm.Solver(9, 200, 64, precision=4, n_steps=1,
+                   geometry=dict(kind=lbm.LBM_GEOM_DISKS, seed=3, r_min=3, r_max=6, target_porosity=0.7))
+    f = _dev(W.perturbation((9,) + shape, seed=7, scale=2e-3), torch.float32)
+    ut = _dev(W.perturbation((2,) + shape, seed=8, scale=3e-3))
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lam = torch.zeros_like(f)
+    s.run(lambda: lbm.lbm_loss_grad_noalloc(s.plan, f, ut, None, loss, lam))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        s.run(lambda: lbm.lbm_loss_grad_noalloc(s.plan, f, ut, None, loss, lam))
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_allocated() == alloc0
+    assert np.isfinite(loss.item()) and loss.item() > 0
+
+
 def test_noalloc_rejects_lattices_beyond_its_scratch():
-    ny = lbm.LBM_NOALLOC_MAX_BLOCKS + 1  # one block per row at nx <= 128
-    plan = lbm.Plan(9, 64, ny, 1, precision=4, n_steps=1)
+    ny = lbm.LBM_NOALLOC_MAX_BLOCKS // 2 + 1  # two blocks per row at 128 < nx <= 256
+    plan = lbm.Plan(9, 256, ny, 1, precision=4, n_steps=1)
     link = torch.zeros(plan.N, dtype=torch.int32, device="cuda")
     lbm.lbm_bind_geometry(plan, link)
     with pytest.raises(lbm.LBMError) as e:
