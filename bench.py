@@ -623,12 +623,9 @@ def run_e2e(P, args, device, barrier, world):
     h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
     h_g = torch.empty(wl.ny, dtype=torch.float64).pin_memory()
     d_rho, d_tau, d_ut = torch.empty_like(P["rho_in"]), torch.empty_like(P["tau"]), torch.empty_like(P["u_target"])
-    K = max(1, min(args.steps, 3))
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s.stream)
-    for _ in range(K):
+    K = max(10, args.steps)
+
+    def one():
         with torch.cuda.stream(s.stream):
             d_rho.copy_(h_rho, non_blocking=True)
             d_tau.copy_(h_tau, non_blocking=True)
@@ -639,6 +636,14 @@ def run_e2e(P, args, device, barrier, world):
         with torch.cuda.stream(s.stream):
             h_loss.copy_(P["loss"], non_blocking=True)
             h_g.copy_(P["g_in"], non_blocking=True)
+
+    one()  # warm call: the sweeps' graphs do not depend on these buffers, so nothing is captured anew
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(K):
+        one()
     e1.record(s.stream)
     barrier()
     ms = e0.elapsed_time(e1)

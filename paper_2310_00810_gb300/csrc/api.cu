@@ -17,10 +17,17 @@
 // then runs the adjoint steps of the segment backwards.
 //
 // Launch sequences.  A forward or reverse sweep is T to 3T kernel launches;
-// on a stream other than the legacy default stream each distinct sequence
-// (same operation, pointers and scalars) is captured once into a CUDA graph
-// and replayed with one cudaGraphLaunch.  When the caller's stream is itself
-// being captured, the launches go straight into the caller's graph.
+// on a stream other than the legacy default stream the part of the sequence
+// that touches only the workspace and the geometry is captured once into a
+// CUDA graph and replayed with one cudaGraphLaunch.  The graph does not
+// depend on the caller's arrays: every call first copies its rho_in and tau
+// into the workspace (and the reverse sweep its lambda^T), and the launches
+// that write the caller's outputs (the final stream-only launch, the gradient
+// finalisation) run after the graph, outside it.  So a caller that passes
+// fresh tensors on every call still replays the same graph; only a new
+// workspace, geometry or rho_out (or a kernel choice) captures a new one.
+// When the caller's stream is itself being captured, the launches go
+// straight into the caller's graph.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -92,6 +99,8 @@ void layout(lbm_plan* p)
     size_t o = 0;
     w.status = o;
     o += 256;
+    w.call = o;
+    o += align256(sizeof(double) * (size_t)(p->info.n_in + 1));
     w.grad_acc = o;
     o += align256(sizeof(double) * (size_t)p->info.n_acc);
     w.partial = o;
@@ -163,7 +172,25 @@ Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
     bc.uw_extrap = p->info.uw_extrap;
     bc.mrt = p->info.mrt;
     bc.vel_inlet = p->info.vel_inlet;
+    bc.wait_us = p->info.wait_us;
+    bc.test_stall = p->info.test_stall ? 1 : 0;
     return bc;
+}
+
+// Copies this call's rho_in and tau into the workspace (stream-ordered), where
+// the sweep kernels read them; returns the staged pointers.
+lbm_status stage_inputs(const lbm_plan* p, void* d_ws, const double* d_rho_in, const double* d_tau,
+                        const double** rho_in, const double** tau, cudaStream_t s)
+{
+    double* r = reinterpret_cast<double*>(static_cast<unsigned char*>(d_ws) + p->ws.call);
+    double* t = r + p->info.n_in;
+    if (cudaMemcpyAsync(r, d_rho_in, sizeof(double) * (size_t)p->info.n_in, cudaMemcpyDeviceToDevice, s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(t, d_tau, sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    *rho_in = r;
+    *tau = t;
+    return LBM_OK;
 }
 
 PersistArgs persist_args(const lbm_plan* p, void* d_ws)
@@ -345,6 +372,13 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     I.adj_family = LBM_FAMILY_AUTO;
     const char* sl = std::getenv("LBM_SPIN_LIMIT");
     I.spin_limit = sl ? (unsigned)std::strtoul(sl, nullptr, 10) : (1u << 24);
+    // LBM_WAIT_US bounds each mbarrier wait of the TMA kernels in time (default 2 s; tests set it tiny)
+    const char* wu = std::getenv("LBM_WAIT_US");
+    I.wait_us = wu ? (unsigned)std::strtoul(wu, nullptr, 10) : 2000000u;
+    // LBM_TEST_STALL_TMA=1 makes the TMA producers issue no copies: a wait that nothing completes, for the
+    // failure-path test of the bounded waits (no fault: the consumers give up after LBM_WAIT_US)
+    const char* ts = std::getenv("LBM_TEST_STALL_TMA");
+    I.test_stall = ts && ts[0] == '1';
     *out = p;
     return LBM_OK;
 }
@@ -529,7 +563,10 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
     p->last_ws = d_ws;
-    const Bc bc = make_bc(p, d_rho_in, rho_out, d_ws);
+    const double* rho_in = nullptr;
+    const double* tau = nullptr;
+    LBM_TRY(stage_inputs(p, d_ws, d_rho_in, d_tau, &rho_in, &tau, s));
+    const Bc bc = make_bc(p, rho_in, rho_out, d_ws);
     const int T = p->desc.n_steps, k = p->k, S = p->S;
     const size_t st = align256(p->info.state_bytes);
     auto slot = [&](int t) -> unsigned char* {  // checkpoint slot of g^t, or nullptr
@@ -545,32 +582,35 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         a.out = d_f;
         unsigned char* g0 = slot(0) ? slot(0) : ping0;
         if (cudaMemsetAsync(g0, 0, p->info.state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
-        if (T == 1) return step_launch(p->info, kStreamOnly, g0, d_f, bc, d_tau, s);
-        return forward_persist(p->info, a, bc, d_tau, s);
+        if (T == 1) return step_launch(p->info, kStreamOnly, g0, d_f, bc, tau, s);
+        return forward_persist(p->info, a, bc, tau, s);
     }
+    // the state chain g^0 .. g^{T-1}: checkpoint slots where the reverse sweep needs them, else ping-pong
+    auto next_state = [&](int t, const unsigned char* cur) -> unsigned char* {
+        unsigned char* dst = slot(t);
+        return dst ? dst : (cur == ping0 ? ping1 : ping0);
+    };
+    unsigned char* g0 = slot(0) ? slot(0) : ping0;
+    unsigned char* last = g0;
+    for (int t = 1; t <= T - 1; ++t) last = next_state(t, last);
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         LBM_TRY(write_mrt_rates(p, bc, st_));
-        // g^0 = rest
-        unsigned char* cur = slot(0);
-        if (!cur) cur = ping0;
-        if (cudaMemsetAsync(cur, 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
+        if (cudaMemsetAsync(g0, 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;  // g^0 = rest
+        unsigned char* cur = g0;
         for (int t = 1; t <= T - 1; ++t) {
-            unsigned char* dst = slot(t);
-            if (!dst) dst = (cur == ping0) ? ping1 : ping0;
-            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, st_));
+            unsigned char* dst = next_state(t, cur);
+            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, tau, st_));
             cur = dst;
         }
-        return final_stream(p, cur, d_f, bc, d_tau, st_);
+        return LBM_OK;
     };
     GraphKey key;
     key.op = 1;
-    key.ptr[0] = d_rho_in;
-    key.ptr[1] = d_tau;
-    key.ptr[2] = d_f;
-    key.ptr[3] = d_ws;
-    key.ptr[4] = p->link;
+    key.ptr[0] = d_ws;
+    key.ptr[1] = p->link;
     key.scalar = rho_out;
-    return run_sequence(p, key, s, issue);
+    LBM_TRY(run_sequence(p, key, s, issue));
+    return final_stream(p, last, d_f, bc, tau, s);  // f^T = S(g^{T-1}) into the caller's array
 }
 
 lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out, const void* d_f_in,
@@ -581,35 +621,41 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
     if (!d_rho_in || !d_tau || !d_f_in || !d_f_out || !d_ws || n_steps < 1) return LBM_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
-    const Bc bc = make_bc(p, d_rho_in, rho_out, d_ws);
+    const double* rho_in = nullptr;
+    const double* tau = nullptr;
+    LBM_TRY(stage_inputs(p, d_ws, d_rho_in, d_tau, &rho_in, &tau, s));
+    const Bc bc = make_bc(p, rho_in, rho_out, d_ws);
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
+    // collide the caller's state into ping0, n - 1 stream-collide launches between the ping-pong
+    // buffers (the cached part), then stream into the caller's output
+    LBM_TRY(write_mrt_rates(p, bc, s));
+    if (p->info.cmp.nf)
+        LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bc, tau, s));
+    else
+        LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, tau, s));
+    unsigned char* last = (n_steps - 1) % 2 == 0 ? ping0 : ping1;
     auto issue = [&](cudaStream_t st_) -> lbm_status {
-        LBM_TRY(write_mrt_rates(p, bc, st_));
-        if (p->info.cmp.nf)
-            LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bc, d_tau, st_));
-        else
-            LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, d_tau, st_));
         unsigned char* cur = ping0;
         for (int t = 1; t < n_steps; ++t) {
             unsigned char* dst = cur == ping0 ? ping1 : ping0;
-            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, d_tau, st_));
+            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, tau, st_));
             cur = dst;
         }
-        return final_stream(p, cur, d_f_out, bc, d_tau, st_);
+        return LBM_OK;
     };
-    if (n_steps < 8) return issue(s);
-    GraphKey key;
-    key.op = 2;
-    key.ptr[0] = d_rho_in;
-    key.ptr[1] = d_tau;
-    key.ptr[2] = d_f_in;
-    key.ptr[3] = d_f_out;
-    key.ptr[4] = d_ws;
-    key.ptr[5] = p->link;
-    key.scalar = rho_out;
-    key.n = n_steps;
-    return run_sequence(p, key, s, issue);
+    if (n_steps < 8) {
+        LBM_TRY(issue(s));
+    } else {
+        GraphKey key;
+        key.op = 2;
+        key.ptr[0] = d_ws;
+        key.ptr[1] = p->link;
+        key.scalar = rho_out;
+        key.n = n_steps;
+        LBM_TRY(run_sequence(p, key, s, issue));
+    }
+    return final_stream(p, last, d_f_out, bc, tau, s);
 }
 
 lbm_status lbm_loss_grad(lbm_plan* p, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
@@ -681,7 +727,10 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
     p->last_ws = d_ws;
-    const Bc bc = make_bc(p, d_rho_in, rho_out, d_ws);
+    const double* rho_in = nullptr;
+    const double* tau = nullptr;
+    LBM_TRY(stage_inputs(p, d_ws, d_rho_in, d_tau, &rho_in, &tau, s));
+    const Bc bc = make_bc(p, rho_in, rho_out, d_ws);
     const int T = p->desc.n_steps, k = p->k, S = p->S;
     const size_t st = align256(p->info.state_bytes);
     double* grad_acc = reinterpret_cast<double*>(ws + p->ws.grad_acc);
@@ -694,8 +743,8 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             return LBM_ERR_CUDA;
         PersistArgs a = persist_args(p, d_ws);
         a.lam_in = d_lambda;
-        LBM_TRY(reverse_persist(p->info, a, bc, d_tau, grad_acc, partial, s));
-        return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
+        LBM_TRY(reverse_persist(p->info, a, bc, tau, grad_acc, partial, s));
+        return finish_gradients_launch(p->info, grad_acc, partial, tau, d_grad_rho_in, d_grad_tau,
                                        reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
     }
     // seg(b, j): state j of segment buffer b; buffer sg & 1 holds segment sg,
@@ -713,13 +762,15 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             if (sg == 0 && j == 1) {
                 if (cudaMemsetAsync(seg(0, 1), 0, p->info.state_bytes, s_) != cudaSuccess) return LBM_ERR_CUDA;
             } else {
-                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), bc, d_tau, s_));
+                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), bc, tau, s_));
             }
             prev = seg(sg, j);
         }
         return LBM_OK;
     };
-    const void* lam_cur = d_lambda;
+    // lambda^T enters through the workspace (lam[1]), so the cached graph does not depend on d_lambda
+    void* lam_T = ws + p->ws.lam[1];
+    const void* lam_cur = lam_T;
     int lam_next = 0;
     auto adjoint_steps = [&](int sg, cudaStream_t s_) -> lbm_status {
         const int len = std::min(k, T - sg * k);
@@ -727,7 +778,7 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             const unsigned char* src = j == 0 ? base_of(sg) : seg(sg, j);
             const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
             void* lam_out = ws + p->ws.lam[lam_next];
-            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, d_tau, grad_acc, partial, s_));
+            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, tau, grad_acc, partial, s_));
             lam_cur = lam_out;
             lam_next ^= 1;
         }
@@ -739,18 +790,18 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         for (auto& e : p->ev)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LBM_ERR_CUDA;
     }
+    if (p->info.cmp.nf)  // lambda^T into the compact layout
+        LBM_TRY(compact_gather_launch(p->info, d_lambda, lam_T, s));
+    else if (cudaMemcpyAsync(lam_T, d_lambda, p->dense_state_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         LBM_TRY(write_mrt_rates(p, bc, st_));
-        lam_cur = d_lambda;
+        lam_cur = lam_T;
         lam_next = 0;
         if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, st_) != cudaSuccess)
             return LBM_ERR_CUDA;
         if (cudaMemsetAsync(partial, 0, sizeof(double) * (size_t)p->info.n_partial, st_) != cudaSuccess)
             return LBM_ERR_CUDA;
-        if (p->info.cmp.nf) {  // lambda^T into the compact layout
-            LBM_TRY(compact_gather_launch(p->info, d_lambda, ws + p->ws.lam[1], st_));
-            lam_cur = ws + p->ws.lam[1];
-        }
         if (!overlap) {
             for (int sg = S - 1; sg >= 0; --sg) {
                 LBM_TRY(recompute(sg, st_));
@@ -779,20 +830,17 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             }
             if (!ok(cudaEventRecord(join, B)) || !ok(cudaStreamWaitEvent(A, join, 0))) return LBM_ERR_CUDA;
         }
-        return finish_gradients_launch(p->info, grad_acc, partial, d_tau, d_grad_rho_in, d_grad_tau,
-                                       reinterpret_cast<uint32_t*>(ws + p->ws.status), st_);
+        return LBM_OK;
     };
     GraphKey key;
     key.op = 3;
-    key.ptr[0] = d_rho_in;
-    key.ptr[1] = d_tau;
-    key.ptr[2] = d_lambda;
-    key.ptr[3] = d_grad_rho_in;
-    key.ptr[4] = d_grad_tau;
-    key.ptr[5] = d_ws;
-    key.ptr[6] = p->link;
+    key.ptr[0] = d_ws;
+    key.ptr[1] = p->link;
     key.scalar = rho_out;
-    return run_sequence(p, key, s, issue);
+    LBM_TRY(run_sequence(p, key, s, issue));
+    // the gradients into the caller's arrays
+    return finish_gradients_launch(p->info, grad_acc, partial, tau, d_grad_rho_in, d_grad_tau,
+                                   reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
 }
 
 lbm_status lbm_macroscopic(lbm_plan* p, const void* d_f, double* d_rho, double* d_u, void* stream)

@@ -21,6 +21,7 @@ enum StepMode : int { kStreamCollide = 0, kCollideOnly = 1, kStreamOnly = 2 };
 // Workspace sections (byte offsets into the caller's d_ws, 256-byte aligned).
 struct Workspace {
     size_t status;      // uint32 status word + FP64 scalars (count, weight)
+    size_t call;        // double[n_in + 1]: this call's rho_in and tau, copied from the caller's arrays
     size_t grad_acc;    // double[n_acc]   per-inlet-node dL/drho_w accumulators
     size_t partial;     // double[n_blocks] per-block dL/domega accumulators
     size_t partial2;    // double[n_blocks] per-block loss / count partials
@@ -47,6 +48,8 @@ struct Bc {
     char vel_inlet = 0;    // 1: velocity inlet through x = -1/2 (moving-wall bounce-back); u_in in the status section
     double rho_out;
     uint32_t* status;      // device status word (bounded waits latch LBM_ERR_TIMEOUT here)
+    uint32_t wait_us = 2000000u;  // time bound of each mbarrier wait of the TMA kernels, in microseconds
+    char test_stall = 0;   // 1: TMA producers issue no copies, so every consumer wait runs out (tests only)
 };
 
 // Fluid-only ("compact") layout tables (compact.cu).  nf = 0: dense layout.
@@ -84,6 +87,8 @@ struct PlanInfo {
     double u_in[3];   // its velocity
     double mrt_rates[3];  // s_e, s_eps, s_q of the MRT collision
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
+    unsigned wait_us;     // time bound of each mbarrier wait of the TMA kernels (microseconds)
+    int test_stall;       // LBM_TEST_STALL_TMA=1: the TMA producers issue nothing (failure-path tests)
     size_t persist_max_bytes;
     int tma_min_tiles;  // smallest tile count for which the TMA kernels are used
     size_t state_bytes;   // bytes of one internal state (Q N, or Q nf in the compact layout)

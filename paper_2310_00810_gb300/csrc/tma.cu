@@ -14,8 +14,13 @@
 // keeps HBM busy.  Copies that fall outside the lattice are zero-filled by
 // the hardware; those links are bounce-back or Eq. 6 links and are replaced.
 //
-// Every mbarrier wait is bounded: on timeout the kernel latches
-// LBM_ERR_TIMEOUT in the status word and returns.
+// Every mbarrier wait is bounded in time (%globaltimer; Bc::wait_us): on
+// timeout the kernel latches LBM_ERR_TIMEOUT in the status word, raises the
+// CTA's abort flag and returns, after the producer has waited for the copies
+// it already issued to land (a CTA never exits with a bulk copy still
+// writing into its shared memory).  A kernel that starts with
+// LBM_ERR_TIMEOUT already latched returns at once, so one wait that gave up
+// costs a sweep one wait limit, not one per launch.
 #include <cuda.h>
 
 #include <algorithm>
@@ -27,7 +32,8 @@ namespace lbm {
 
 namespace {
 
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kPollCap = 1u << 30;            // backstop on the polls of one wait
+constexpr uint64_t kDrainNs = 1000000000ull;       // bound of the wait for issued copies before exit (1 s)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -59,17 +65,52 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait on one mbarrier phase; false on timeout or when another
-// thread of the CTA has given up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status, volatile int* abort)
+__device__ __forceinline__ uint64_t global_ns()
 {
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
-        if (mbar_test(bar, parity)) return true;
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait on one mbarrier phase: false once limit_ns has elapsed (then
+// LBM_ERR_TIMEOUT is latched and the CTA's abort flag raised) or when another
+// thread of the CTA has given up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t* status, volatile int* abort,
+                                          uint64_t limit_ns)
+{
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0; it < kPollCap; it += 32) {
+#pragma unroll 1
+        for (int j = 0; j < 32; ++j)
+            if (mbar_test(bar, parity)) return true;
         if (*abort) return false;
+        if (global_ns() - t0 > limit_ns) break;
     }
     atomicOr(status, 1u << LBM_ERR_TIMEOUT);
     *abort = 1;
     return false;
+}
+
+// Producer epilogue: waits until the copies of the last issued tiles (tile j
+// completes phase j / stages of full[j % stages]) have landed, so that no
+// bulk copy is still writing into this CTA's shared memory when it exits.
+// Copies complete in microseconds; the bound only guards a broken memory
+// system.
+__device__ __forceinline__ void drain_copies(uint64_t* full, int stages, int issued)
+{
+    for (int j = issued > stages ? issued - stages : 0; j < issued; ++j) {
+        const uint64_t t0 = global_ns();
+        while (!mbar_test(&full[j % stages], (uint32_t)(j / stages) & 1u))
+            if (global_ns() - t0 > kDrainNs) break;
+    }
+}
+
+// 1 when a bounded wait of an earlier launch gave up (LBM_ERR_TIMEOUT latched
+// and not yet read by lbm_get_status): the launch then does nothing.
+__device__ __forceinline__ int timeout_latched(const uint32_t* status)
+{
+    return (int)((*reinterpret_cast<const volatile uint32_t*>(status) >> LBM_ERR_TIMEOUT) & 1u);
 }
 
 __device__ __forceinline__ void tma_load4(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
@@ -195,19 +236,22 @@ __global__ void __launch_bounds__(Shape<Q, FwdTile<Q>>::NCONS + 32, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], S::NCONS / 32);
         }
-        s_abort = 0;
+        s_abort = timeout_latched(bc.status);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     volatile int* abort = &s_abort;
+    if (*abort) return;  // uniform: every thread read the same flag after the barrier
+    const uint64_t wait_ns = (uint64_t)bc.wait_us * 1000ull;
 
     if (tid >= S::NCONS) {  // producer warp: one thread issues the copies
         if (tid == S::NCONS) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
             int k = 0;
-            for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
+            const int n_tiles = bc.test_stall ? 0 : tg.total;
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
                 const int s = k % C::STAGES;
-                if (k >= C::STAGES && !mbar_wait(&empty[s], ((k / C::STAGES) - 1) & 1, bc.status, abort)) break;
+                if (k >= C::STAGES && !mbar_wait(&empty[s], ((k / C::STAGES) - 1) & 1, bc.status, abort, wait_ns)) break;
                 const int x0 = (t % tg.ntx) * C::TX, y0 = ((t / tg.ntx) % tg.nty) * C::TY,
                           z0 = (t / (tg.ntx * tg.nty)) * C::TZ;
                 mbar_expect_tx(&full[s], (uint32_t)(Q * S::BOX * 4));
@@ -216,6 +260,7 @@ __global__ void __launch_bounds__(Shape<Q, FwdTile<Q>>::NCONS + 32, 1)
                 for (int i = 0; i < Q; ++i)
                     tma_load4(st + i * S::BOX, &map, &full[s], x0 - 4, y0 - L::c(i, 1), z0 - L::c(i, 2), i);
             }
+            drain_copies(full, C::STAGES, k);
         }
         return;
     }
@@ -226,7 +271,7 @@ __global__ void __launch_bounds__(Shape<Q, FwdTile<Q>>::NCONS + 32, 1)
     int k = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
         const int s = k % C::STAGES;
-        const bool ok = mbar_wait(&full[s], (k / C::STAGES) & 1, bc.status, abort);
+        const bool ok = mbar_wait(&full[s], (k / C::STAGES) & 1, bc.status, abort, wait_ns);
         if (!__all_sync(0xffffffffu, ok)) break;
         const int x = (t % tg.ntx) * C::TX + 4 * gx, y = ((t / tg.ntx) % tg.nty) * C::TY + gy,
                   z = (t / (tg.ntx * tg.nty)) * C::TZ + gz;
@@ -311,20 +356,23 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], H::NCONS / 32);
         }
-        s_abort = 0;
+        s_abort = timeout_latched(bc.status);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     volatile int* abort = &s_abort;
+    if (*abort) return;  // uniform: every thread read the same flag after the barrier
+    const uint64_t wait_ns = (uint64_t)bc.wait_us * 1000ull;
 
     if (tid >= H::NCONS) {
         if (tid == H::NCONS) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_link)) : "memory");
             int k = 0;
-            for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
+            const int n_tiles = bc.test_stall ? 0 : tg.total;
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
                 const int s = k % H::STAGES;
-                if (k >= H::STAGES && !mbar_wait(&empty[s], ((k / H::STAGES) - 1) & 1, bc.status, abort)) break;
+                if (k >= H::STAGES && !mbar_wait(&empty[s], ((k / H::STAGES) - 1) & 1, bc.status, abort, wait_ns)) break;
                 const int x0 = (t % tg.ntx) * H::TX, y0 = (t / tg.ntx) * H::TY;
                 unsigned char* st = smem + s * H::STAGE_BYTES;
                 mbar_expect_tx(&full[s], H::TX_BYTES);
@@ -333,6 +381,7 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
                     tma_load4(st + (size_t)i * H::BOX * 4, &map, &full[s], x0 - 4, y0 - 1, 0, i);
                 tma_load3(st + (size_t)9 * H::BOX * 4, &map_link, &full[s], x0, y0, 0);
             }
+            drain_copies(full, H::STAGES, k);
         }
         return;
     }
@@ -342,7 +391,7 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
     int k = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
         const int s = k % H::STAGES;
-        const bool ok = mbar_wait(&full[s], (k / H::STAGES) & 1, bc.status, abort);
+        const bool ok = mbar_wait(&full[s], (k / H::STAGES) & 1, bc.status, abort, wait_ns);
         if (!__all_sync(0xffffffffu, ok)) break;
         const int x = (t % tg.ntx) * H::TX + 4 * gx, y = (t / tg.ntx) * H::TY + gy;
         const unsigned char* st = smem + s * H::STAGE_BYTES;
@@ -426,11 +475,13 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], H::NCONS / 32);
         }
-        s_abort = 0;
+        s_abort = timeout_latched(bc.status);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     volatile int* abort = &s_abort;
+    if (*abort) return;  // uniform: every thread read the same flag after the barrier
+    const uint64_t wait_ns = (uint64_t)bc.wait_us * 1000ull;
 
     if (tid >= H::NCONS) {
         if (tid == H::NCONS) {
@@ -439,9 +490,10 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_link)) : "memory");
             const uint32_t tx_bytes = (uint32_t)((T0 ? 9 : 18) * H::BW * H::BH * 4 + H::LINKS * 4);
             int k = 0;
-            for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
+            const int n_tiles = bc.test_stall ? 0 : tg.total;
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
                 const int s = k % H::STAGES;
-                if (k >= H::STAGES && !mbar_wait(&empty[s], ((k / H::STAGES) - 1) & 1, bc.status, abort)) break;
+                if (k >= H::STAGES && !mbar_wait(&empty[s], ((k / H::STAGES) - 1) & 1, bc.status, abort, wait_ns)) break;
                 const int x0 = (t % tg.ntx) * H::TX, y0 = (t / tg.ntx) * H::TY;
                 unsigned char* st = smem + s * H::STAGE_BYTES;
                 mbar_expect_tx(&full[s], tx_bytes);
@@ -452,6 +504,7 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
                 }
                 tma_load3(st + (size_t)18 * H::BOX * 4, &map_link, &full[s], x0, y0, 0);
             }
+            drain_copies(full, H::STAGES, k);
         }
         return;
     }
@@ -462,7 +515,7 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
     int k = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
         const int s = k % H::STAGES;
-        const bool ok = mbar_wait(&full[s], (k / H::STAGES) & 1, bc.status, abort);
+        const bool ok = mbar_wait(&full[s], (k / H::STAGES) & 1, bc.status, abort, wait_ns);
         if (!__all_sync(0xffffffffu, ok)) break;
         const int x = (t % tg.ntx) * H::TX + 4 * gx, y = (t / tg.ntx) * H::TY + gy;
         const unsigned char* st = smem + s * H::STAGE_BYTES;
@@ -532,20 +585,23 @@ __global__ void __launch_bounds__(Shape<Q, AdjTile<Q>>::NCONS + 32, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], S::NCONS / 32);
         }
-        s_abort = 0;
+        s_abort = timeout_latched(bc.status);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     volatile int* abort = &s_abort;
+    if (*abort) return;  // uniform: every thread read the same flag after the barrier
+    const uint64_t wait_ns = (uint64_t)bc.wait_us * 1000ull;
 
     if (tid >= S::NCONS) {
         if (tid == S::NCONS) {
             if (!T0) asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_g)) : "memory");
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_l)) : "memory");
             int k = 0;
-            for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
+            const int n_tiles = bc.test_stall ? 0 : tg.total;
+            for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
                 const int s = k % C::STAGES;
-                if (k >= C::STAGES && !mbar_wait(&empty[s], ((k / C::STAGES) - 1) & 1, bc.status, abort)) break;
+                if (k >= C::STAGES && !mbar_wait(&empty[s], ((k / C::STAGES) - 1) & 1, bc.status, abort, wait_ns)) break;
                 const int x0 = (t % tg.ntx) * C::TX, y0 = ((t / tg.ntx) % tg.nty) * C::TY,
                           z0 = (t / (tg.ntx * tg.nty)) * C::TZ;
                 mbar_expect_tx(&full[s], (uint32_t)((T0 ? 1 : 2) * Q * S::BOX * 4));
@@ -557,6 +613,7 @@ __global__ void __launch_bounds__(Shape<Q, AdjTile<Q>>::NCONS + 32, 1)
                     tma_load4(st + (Q + i) * S::BOX, &map_l, &full[s], x0 - 4, y0 + L::c(i, 1), z0 + L::c(i, 2), i);
                 }
             }
+            drain_copies(full, C::STAGES, k);
         }
         return;
     }
@@ -568,7 +625,7 @@ __global__ void __launch_bounds__(Shape<Q, AdjTile<Q>>::NCONS + 32, 1)
     int k = 0;
     for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
         const int s = k % C::STAGES;
-        const bool ok = mbar_wait(&full[s], (k / C::STAGES) & 1, bc.status, abort);
+        const bool ok = mbar_wait(&full[s], (k / C::STAGES) & 1, bc.status, abort, wait_ns);
         if (!__all_sync(0xffffffffu, ok)) break;
         const int x = (t % tg.ntx) * C::TX + 4 * gx, y = ((t / tg.ntx) % tg.nty) * C::TY + gy,
                   z = (t / (tg.ntx * tg.nty)) * C::TZ + gz;

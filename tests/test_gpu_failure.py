@@ -53,3 +53,36 @@ def test_nonfinite_parameter_is_reported():
     L, lam = s.loss_grad(f, ut)
     torch.cuda.synchronize()
     assert s.status() == lbm.LBM_ERR_NONFINITE
+
+
+def test_tma_wait_gives_up_once_per_sweep(monkeypatch):
+    """The TMA producers are told to issue nothing (LBM_TEST_STALL_TMA), so
+    the consumers' first wait is one that nothing completes.  It gives up
+    after LBM_WAIT_US (50 ms here), latches LBM_ERR_TIMEOUT, and every later
+    TMA launch of the 400-step sweep returns at entry: the sweep ends after
+    about one wait limit instead of one per launch (20 s).  The context stays
+    usable."""
+    import time
+
+    g = dict(kind=lbm.LBM_GEOM_DISKS, seed=3, r_min=3, r_max=6, target_porosity=0.7)
+    monkeypatch.setenv("LBM_TEST_STALL_TMA", "1")
+    monkeypatch.setenv("LBM_WAIT_US", "50000")
+    s = lbm.Solver(9, 256, 128, precision=4, n_steps=400, geometry=g, layout="dense")
+    lbm.lbm_plan_set_kernels(s.plan, step_family=lbm.LBM_FAMILY_TMA, adjoint_family=lbm.LBM_FAMILY_TMA)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.forward(dev([1.001]), dev([0.8]), 1.0)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    assert s.status() == lbm.LBM_ERR_TIMEOUT
+    assert dt < 4.0, f"the sweep took {dt:.2f} s: later launches did not return at entry"
+    monkeypatch.delenv("LBM_TEST_STALL_TMA")
+    monkeypatch.delenv("LBM_WAIT_US")
+    s2 = lbm.Solver(9, 256, 128, precision=4, n_steps=40, link=s.link, mask=s.mask, layout="dense")
+    lbm.lbm_plan_set_kernels(s2.plan, step_family=lbm.LBM_FAMILY_TMA, adjoint_family=lbm.LBM_FAMILY_TMA)
+    f = s2.forward(dev([1.001]), dev([0.8]), 1.0)
+    _, u = s2.macroscopic(f)
+    m = s.mask_field.cpu().numpy()
+    _, uw = O.macroscopic(9, m, O.forward(9, m, 1.001, 1.0, 0.8, 40))
+    assert np.linalg.norm(u.cpu().numpy() - uw) / np.linalg.norm(uw) < 1e-4
+    assert s2.status() == lbm.LBM_OK
