@@ -246,7 +246,8 @@ LBM_API lbm_status lbm_compact_bind(lbm_plan* plan, int64_t n_fluid, void* d_tab
  *  d_rho_in  double[1 or ny nz]  inlet density (Eq. 6 rho_w at x = -1/2)
  *  d_tau     double[1]           relaxation time (> 1/2)
  *  rho_out   outlet density (Eq. 6 rho_w at x = nx - 1/2)
- *  d_f       out: f^T, shifted, plan precision, Q N values
+ *  d_f       out: f^T, shifted, plan precision, Q N values (every entry is
+ *            written; solid nodes get 0)
  *  d_ws      workspace of lbm_workspace_size bytes, 256-byte aligned and
  *            zero-filled before its first use (it holds the status word)
  * Errors: INVALID_ARG (null pointers, no geometry bound), CUDA. */

@@ -247,12 +247,14 @@ void set_dense(lbm_plan* p)
     } while (0)
 
 // The last launch of a sweep: stream-only from the internal state cur into
-// the caller's dense array (compact layout: solids zeroed first).
+// the caller's dense array.  Solid nodes are zeroed first: the compact layout
+// writes fluid nodes only, and the dense kernels skip 32-byte sectors that
+// hold only solid nodes.
 lbm_status final_stream(const lbm_plan* p, const void* cur, void* d_f, const Bc& bc, const double* tau,
                         cudaStream_t s)
 {
-    if (!p->info.cmp.nf) return step_launch(p->info, kStreamOnly, cur, d_f, bc, tau, s);
     if (cudaMemsetAsync(d_f, 0, p->dense_state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
+    if (!p->info.cmp.nf) return step_launch(p->info, kStreamOnly, cur, d_f, bc, tau, s);
     return step_launch_cmp(p->info, kStreamOnly, cur, d_f, false, true, bc, tau, s);
 }
 
