@@ -425,6 +425,37 @@ LBM_API lbm_status lbm_batch_adjoint(lbm_batch* batch, const double* d_rho_in, c
                                      const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws,
                                      void* stream);
 
+/* Fluid-only layout for a batch (the single-lattice lbm_compact_* calls,
+ * batched): the fluid nodes of every instance packed into one compact state,
+ * each instance's range padded to a multiple of 256 nodes so that every
+ * thread block of the step and adjoint kernels belongs to one instance; per
+ * fluid-node update the kernels move 2 Q populations plus the neighbour
+ * table instead of every node of every instance.  Each instance gets bit for
+ * bit the populations and gradients a single plan in the compact layout
+ * computes.  The layout is internal: the batch calls keep taking and
+ * returning the packed dense arrays of lbm_batch_layout, and the workspace
+ * size does not change.
+ * lbm_batch_compact_size: bytes of the table buffer for n_fluid[i] fluid
+ *   nodes per instance (host array of n; d_info[4 i + 3] of
+ *   lbm_batch_init_geometry).
+ * lbm_batch_compact_bind: builds the tables into d_tables (device,
+ *   caller-owned, 256-byte aligned, lbm_batch_compact_size bytes, valid while
+ *   the batch uses them) from the link words, using d_ws (the workspace given
+ *   to lbm_batch_init_geometry) as scratch, and switches the batch to the
+ *   fluid-only layout.  Synchronises the stream (it checks every n_fluid[i]
+ *   against the link words).  n_fluid = NULL switches back to the dense
+ *   layout.  A new lbm_batch_init_geometry switches back as well.
+ * Errors: INVALID_ARG (geometry not initialised on d_ws, a count out of
+ *   range or not the instance's fluid count, misaligned d_tables), CUDA. */
+LBM_API lbm_status lbm_batch_compact_size(const lbm_batch* batch, const int64_t* n_fluid, size_t* bytes);
+LBM_API lbm_status lbm_batch_compact_bind(lbm_batch* batch, const int64_t* n_fluid, void* d_tables, void* d_ws,
+                                          void* stream);
+
+/* Reads (synchronously) and clears the batch's device status word in d_ws
+ * (a non-finite loss or gradient of any instance latches
+ * LBM_ERR_NONFINITE). */
+LBM_API lbm_status lbm_batch_get_status(lbm_batch* batch, void* d_ws, lbm_status* status);
+
 /* Reads (synchronously) and clears the plan's device status word. */
 LBM_API lbm_status lbm_get_status(lbm_plan* plan, lbm_status* status);
 

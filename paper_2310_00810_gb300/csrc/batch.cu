@@ -301,6 +301,34 @@ __global__ void k_batch_finish(const BInst* __restrict__ insts, const double* __
     }
 }
 
+// The same in the fluid-only layout: instance i's dL/domega partials are the
+// warp slots [k0 / 32, (k0 + nf + 31) / 32) of the packed compact kernels,
+// summed in the order a single compact plan sums its own.
+__global__ void k_batch_finish_cmp(const BCmpInst* __restrict__ insts, const double* __restrict__ partial,
+                                   const double* __restrict__ grad_acc, const double* __restrict__ tau,
+                                   double* __restrict__ g_in, double* __restrict__ g_tau, uint32_t* status)
+{
+    const BCmpInst I = insts[blockIdx.x];
+    const long long w0 = I.k0 >> 5, nw = (I.nf + 31) >> 5;
+    double v = 0.0;
+    for (long long u = threadIdx.x; u < nw; u += blockDim.x) v += partial[w0 + u];
+    v = block_sum(v, threadIdx.x, blockDim.x);
+    const int n_acc = I.g.ny * I.g.nz;
+    double gs = 0.0;
+    if (I.n_in == 1) {
+        for (int a = threadIdx.x; a < n_acc; a += blockDim.x) gs += grad_acc[I.acc_off + a];
+        gs = block_sum(gs, threadIdx.x, blockDim.x);
+    } else {
+        for (int a = threadIdx.x; a < n_acc; a += blockDim.x) g_in[I.in_off + a] = grad_acc[I.acc_off + a];
+    }
+    if (threadIdx.x == 0) {
+        const double t = tau[blockIdx.x];
+        g_tau[blockIdx.x] = -v / (t * t);
+        if (I.n_in == 1) g_in[I.in_off] = gs;
+        if (!isfinite(v) || !isfinite(gs)) atomicOr(status, 1u << LBM_ERR_NONFINITE);
+    }
+}
+
 }  // namespace
 
 // -------------------------------------------------------------------- host
@@ -319,6 +347,14 @@ struct lbm_batch {
     bool tables_ready = false;
     void* tables_ws = nullptr;
     bool pdl = true;
+    size_t n_part = 0;  // FP64 dL/domega slots: one per unit (dense) or per warp (fluid-only)
+    // fluid-only layout (lbm_batch_compact_bind)
+    bool cmp = false;
+    long long nfp = 0;                 // packed compact nodes (every instance padded to kBatchCmpAlign)
+    std::vector<BCmpInst> cinsts;
+    std::vector<int> blk_inst;
+    BCmpArgs ca = {};
+    size_t cmp_state_bytes = 0;
     struct G {
         int op;
         const void* ptr[6];
@@ -525,7 +561,12 @@ lbm_status lbm_batch_create(const lbm_desc* c, int32_t n, const int32_t* nx, con
     b->in_off.push_back(io);
     b->acc_off.push_back(ao);
     b->state_elems = (size_t)so;
-    b->state_bytes = al256((size_t)so * (size_t)c->precision);
+    // a workspace state slot holds a packed dense state or a packed fluid-only one (every instance's fluid
+    // nodes rounded up to kBatchCmpAlign, which can exceed its dense size when nearly all nodes are fluid)
+    long long cmp_bound = 0;
+    for (int i = 0; i < n; ++i)
+        cmp_bound += (b->info[i].geo.N + kBatchCmpAlign - 1) / kBatchCmpAlign * kBatchCmpAlign;
+    b->state_bytes = al256((size_t)std::max(so, (long long)c->q * cmp_bound) * (size_t)c->precision);
     size_t o = 0;
     b->o_status = o;
     o += 256;
@@ -535,8 +576,13 @@ lbm_status lbm_batch_create(const lbm_desc* c, int32_t n, const int32_t* nx, con
     o += al256(sizeof(BUnit) * b->units.size());
     b->o_acc = o;
     o += al256(sizeof(double) * (size_t)ao);
+    // dL/domega slots: one per unit in the dense layout, one per warp of the packed fluid-only
+    // layout (at most ceil(N_i / 256) blocks of 8 warps per instance)
+    long long warps = 0;
+    for (int i = 0; i < n; ++i) warps += (b->info[i].geo.N + kBatchCmpAlign - 1) / kBatchCmpAlign * (kBatchCmpAlign / 32);
+    b->n_part = std::max(b->units.size(), (size_t)warps);
     b->o_part = o;
-    o += al256(sizeof(double) * b->units.size());
+    o += al256(sizeof(double) * b->n_part);
     b->o_part2 = o;
     o += al256(sizeof(double) * b->units.size());
     b->o_scal = o;
@@ -603,6 +649,10 @@ lbm_status lbm_batch_init_geometry(lbm_batch* b, const lbm_geom_desc* g, uint8_t
         b->insts[i].g.link = d_link + b->node_off[i];
     }
     unsigned char* ws = static_cast<unsigned char*>(d_ws);
+    b->cmp = false;  // a new geometry invalidates fluid-only tables
+    for (auto& gr : b->graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    b->graphs.clear();
     if (cudaMemsetAsync(ws + b->o_status, 0, 256, s) != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaMemcpyAsync(ws + b->o_insts, b->insts.data(), sizeof(BInst) * b->insts.size(), cudaMemcpyHostToDevice,
                         s) != cudaSuccess)
@@ -630,19 +680,26 @@ lbm_status lbm_batch_forward(lbm_batch* b, const double* d_rho_in, const double*
         if (s1 % k == 0 && s1 / k >= 1 && s1 / k <= S - 1) return ws + b->o_ckpt + b->state_bytes * (size_t)(s1 / k - 1);
         return nullptr;
     };
+    BCmpArgs ca = b->ca;
+    ca.status = reinterpret_cast<uint32_t*>(ws + b->o_status);
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         unsigned char* cur = slot(0) ? slot(0) : ws + b->o_ping[0];
-        if (cudaMemsetAsync(cur, 0, b->state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
+        if (cudaMemsetAsync(cur, 0, b->cmp ? b->cmp_state_bytes : b->state_bytes, st_) != cudaSuccess)
+            return LBM_ERR_CUDA;
         for (int t = 1; t <= T - 1; ++t) {
             unsigned char* dst = slot(t);
             if (!dst) dst = ws + b->o_ping[t & 1];
-            lbm_status st = step(b, kStreamCollide, cur, dst, d_rho_in, d_tau, rho_out, ws, st_);
+            lbm_status st = b->cmp ? bstep_launch_cmp(ca, kStreamCollide, cur, dst, false, d_rho_in, d_tau, rho_out, st_)
+                                   : step(b, kStreamCollide, cur, dst, d_rho_in, d_tau, rho_out, ws, st_);
             if (st != LBM_OK) return st;
             cur = dst;
         }
-        return step(b, kStreamOnly, cur, d_f, d_rho_in, d_tau, rho_out, ws, st_);
+        if (!b->cmp) return step(b, kStreamOnly, cur, d_f, d_rho_in, d_tau, rho_out, ws, st_);
+        // fluid nodes only: the solid entries of the caller's packed array are zeroed first
+        if (cudaMemsetAsync(d_f, 0, (size_t)b->state_elems * (size_t)b->prec, st_) != cudaSuccess) return LBM_ERR_CUDA;
+        return bstep_launch_cmp(ca, kStreamOnly, cur, d_f, true, d_rho_in, d_tau, rho_out, st_);
     };
-    return run_graph(b, 1, {d_rho_in, d_tau, d_f, d_ws}, rho_out, s, issue);
+    return run_graph(b, b->cmp ? 11 : 1, {d_rho_in, d_tau, d_f, d_ws}, rho_out, s, issue);
 }
 
 lbm_status lbm_batch_loss_grad(lbm_batch* b, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
@@ -689,13 +746,22 @@ lbm_status lbm_batch_adjoint(lbm_batch* b, const double* d_rho_in, const double*
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(d_ws);
     const int T = b->desc.n_steps, k = b->k, S = b->S;
+    BCmpArgs ca = b->ca;
+    ca.status = reinterpret_cast<uint32_t*>(ws + b->o_status);
+    const size_t sb = b->cmp ? b->cmp_state_bytes : b->state_bytes;
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         if (cudaMemsetAsync(ws + b->o_acc, 0, sizeof(double) * (size_t)b->acc_off.back(), st_) != cudaSuccess)
             return LBM_ERR_CUDA;
-        if (cudaMemsetAsync(ws + b->o_part, 0, sizeof(double) * b->units.size(), st_) != cudaSuccess)
-            return LBM_ERR_CUDA;
+        if (cudaMemsetAsync(ws + b->o_part, 0, sizeof(double) * b->n_part, st_) != cudaSuccess) return LBM_ERR_CUDA;
         const void* lam_cur = d_lambda;
         int lam_next = 0;
+        if (b->cmp) {  // lambda^T into the packed compact layout
+            lbm_status st = bgather_launch_cmp(ca, d_lambda, ws + b->o_lam[1], st_);
+            if (st != LBM_OK) return st;
+            lam_cur = ws + b->o_lam[1];
+        }
+        double* acc = reinterpret_cast<double*>(ws + b->o_acc);
+        double* part = reinterpret_cast<double*>(ws + b->o_part);
         for (int sg = S - 1; sg >= 0; --sg) {
             const int t0 = sg * k, len = std::min(k, T - t0);
             auto seg = [&](int j) -> unsigned char* { return ws + b->o_seg + b->state_bytes * (size_t)j; };
@@ -703,9 +769,11 @@ lbm_status lbm_batch_adjoint(lbm_batch* b, const double* d_rho_in, const double*
             const unsigned char* prev = base;
             for (int j = 1; j < len; ++j) {
                 if (sg == 0 && j == 1) {
-                    if (cudaMemsetAsync(seg(1), 0, b->state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
+                    if (cudaMemsetAsync(seg(1), 0, sb, st_) != cudaSuccess) return LBM_ERR_CUDA;
                 } else {
-                    lbm_status st = step(b, kStreamCollide, prev, seg(j), d_rho_in, d_tau, rho_out, ws, st_);
+                    lbm_status st =
+                        b->cmp ? bstep_launch_cmp(ca, kStreamCollide, prev, seg(j), false, d_rho_in, d_tau, rho_out, st_)
+                               : step(b, kStreamCollide, prev, seg(j), d_rho_in, d_tau, rho_out, ws, st_);
                     if (st != LBM_OK) return st;
                 }
                 prev = seg(j);
@@ -713,19 +781,131 @@ lbm_status lbm_batch_adjoint(lbm_batch* b, const double* d_rho_in, const double*
             for (int j = len - 1; j >= 0; --j) {
                 const unsigned char* src = j == 0 ? base : seg(j);
                 void* lam_out = ws + b->o_lam[lam_next];
-                lbm_status st = adjoint(b, sg == 0 && j == 0, src, lam_cur, lam_out, d_rho_in, d_tau, rho_out, ws, st_);
+                const bool at0 = sg == 0 && j == 0;
+                lbm_status st = b->cmp ? badjoint_launch_cmp(ca, at0 ? 1 : 0, src, lam_cur, lam_out, d_rho_in, d_tau,
+                                                             rho_out, acc, part, st_)
+                                       : adjoint(b, at0, src, lam_cur, lam_out, d_rho_in, d_tau, rho_out, ws, st_);
                 if (st != LBM_OK) return st;
                 lam_cur = lam_out;
                 lam_next ^= 1;
             }
         }
-        k_batch_finish<<<b->n, kReduceThreads, 0, st_>>>(
-            reinterpret_cast<const BInst*>(ws + b->o_insts), reinterpret_cast<const double*>(ws + b->o_part),
-            reinterpret_cast<const double*>(ws + b->o_acc), d_tau, d_grad_rho_in, d_grad_tau,
-            reinterpret_cast<uint32_t*>(ws + b->o_status));
+        if (b->cmp)
+            k_batch_finish_cmp<<<b->n, kReduceThreads, 0, st_>>>(ca.insts, part, acc, d_tau, d_grad_rho_in, d_grad_tau,
+                                                                ca.status);
+        else
+            k_batch_finish<<<b->n, kReduceThreads, 0, st_>>>(
+                reinterpret_cast<const BInst*>(ws + b->o_insts), part, acc, d_tau, d_grad_rho_in, d_grad_tau,
+                ca.status);
         return cuda_status(cudaGetLastError());
     };
-    return run_graph(b, 3, {d_rho_in, d_tau, d_lambda, d_grad_rho_in, d_grad_tau, d_ws}, rho_out, s, issue);
+    return run_graph(b, b->cmp ? 13 : 3, {d_rho_in, d_tau, d_lambda, d_grad_rho_in, d_grad_tau, d_ws}, rho_out, s,
+                     issue);
+}
+
+lbm_status lbm_batch_compact_size(const lbm_batch* b, const int64_t* n_fluid, size_t* bytes)
+{
+    if (!b || !n_fluid || !bytes) return LBM_ERR_INVALID_ARG;
+    long long nfp = 0;
+    for (int i = 0; i < b->n; ++i) {
+        if (n_fluid[i] < 0 || n_fluid[i] > b->info[i].geo.N) return LBM_ERR_INVALID_ARG;
+        nfp += (n_fluid[i] + kBatchCmpAlign - 1) / kBatchCmpAlign * kBatchCmpAlign;
+    }
+    *bytes = al256(sizeof(BCmpInst) * (size_t)b->n) + al256(sizeof(int) * (size_t)(nfp / kBatchCmpAlign)) +
+             al256(sizeof(int32_t) * (size_t)nfp) + al256(sizeof(int32_t) * (size_t)(b->q - 1) * (size_t)nfp);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_compact_bind(lbm_batch* b, const int64_t* n_fluid, void* d_tables, void* d_ws, void* stream)
+{
+    if (!b || !b->tables_ready || d_ws != b->tables_ws) return LBM_ERR_INVALID_ARG;
+    for (auto& g : b->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    if (!n_fluid) {  // back to the dense layout
+        b->cmp = false;
+        return LBM_OK;
+    }
+    if (!d_tables || (reinterpret_cast<uintptr_t>(d_tables) & 255u)) return LBM_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(d_ws);
+    std::vector<BCmpInst> ci((size_t)b->n);
+    long long nfp = 0;
+    for (int i = 0; i < b->n; ++i) {
+        if (n_fluid[i] < 0 || n_fluid[i] > b->info[i].geo.N) return LBM_ERR_INVALID_ARG;
+        BCmpInst& c = ci[(size_t)i];
+        c.g = b->insts[(size_t)i].g;
+        c.k0 = nfp;
+        c.nf = n_fluid[i];
+        c.f_off = b->state_off[(size_t)i];
+        c.in_off = b->in_off[(size_t)i];
+        c.acc_off = b->acc_off[(size_t)i];
+        c.n_in = b->info[(size_t)i].n_in;
+        nfp += (c.nf + kBatchCmpAlign - 1) / kBatchCmpAlign * kBatchCmpAlign;
+    }
+    if (nfp >= (1LL << 31)) return LBM_ERR_INVALID_ARG;  // neighbour codes are int32
+    unsigned char* tb = static_cast<unsigned char*>(d_tables);
+    const size_t t_insts = 0, t_blk = al256(sizeof(BCmpInst) * (size_t)b->n);
+    const size_t t_idx = t_blk + al256(sizeof(int) * (size_t)(nfp / kBatchCmpAlign));
+    const size_t t_nbr = t_idx + al256(sizeof(int32_t) * (size_t)nfp);
+    int32_t* idx = reinterpret_cast<int32_t*>(tb + t_idx);
+    int32_t* nbr = reinterpret_cast<int32_t*>(tb + t_nbr);
+    std::vector<int> blk((size_t)(nfp / kBatchCmpAlign));
+    // each instance's tables are built in the workspace's state buffers (free at this point), then
+    // packed; compact_build checks the fluid count against the link words (and synchronises)
+    unsigned char* scratch = ws + b->o_ping[0];
+    const size_t cap = b->o_ckpt - b->o_ping[0];
+    for (int i = 0; i < b->n; ++i) {
+        const BCmpInst& c = ci[(size_t)i];
+        PlanInfo I = b->info[(size_t)i];
+        I.geo.link = b->insts[(size_t)i].g.link;
+        if (compact_table_bytes(I, c.nf) > cap) return LBM_ERR_INVALID_ARG;
+        Cmp local{0, nullptr, nullptr};
+        const int32_t* cmap = nullptr;
+        lbm_status st = compact_build(I, c.nf, scratch, &local, &cmap, s);
+        if (st != LBM_OK) return st;
+        st = bpack_launch_cmp(local, b->q, c.k0, nfp, idx, nbr, s);
+        if (st != LBM_OK) return st;
+        for (long long bl = c.k0 / kBatchCmpAlign; bl < (c.k0 + c.nf + kBatchCmpAlign - 1) / kBatchCmpAlign; ++bl)
+            blk[(size_t)bl] = i;
+    }
+    if (cudaMemcpyAsync(tb + t_insts, ci.data(), sizeof(BCmpInst) * ci.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess ||
+        (!blk.empty() &&
+         cudaMemcpyAsync(tb + t_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice, s) != cudaSuccess))
+        return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ERR_CUDA;  // host vectors outlive the copies
+    b->cinsts = ci;
+    b->blk_inst = blk;
+    b->nfp = nfp;
+    b->cmp_state_bytes = (size_t)b->q * (size_t)nfp * (size_t)b->prec;
+    BCmpArgs& a = b->ca;
+    a.c = Cmp{nfp, idx, nbr};
+    a.insts = reinterpret_cast<const BCmpInst*>(tb + t_insts);
+    a.blk_inst = reinterpret_cast<const int*>(tb + t_blk);
+    a.n_blocks = (unsigned)(nfp / kBatchCmpAlign);
+    a.q = b->q;
+    a.prec = b->prec;
+    a.pdl = b->pdl ? 1 : 0;
+    a.status = nullptr;  // set per call from the workspace
+    b->cmp = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_status(lbm_batch* b, void* d_ws, lbm_status* status)
+{
+    if (!b || !d_ws || !status || (reinterpret_cast<uintptr_t>(d_ws) & 255u)) return LBM_ERR_INVALID_ARG;
+    *status = LBM_OK;
+    uint32_t word = 0;
+    uint32_t* dev = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(d_ws) + b->o_status);
+    if (cudaMemcpy(&word, dev, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaMemset(dev, 0, sizeof(word)) != cudaSuccess) return LBM_ERR_CUDA;
+    for (int bit = 1; bit < 32; ++bit)
+        if (word & (1u << bit)) {
+            *status = static_cast<lbm_status>(bit);
+            break;
+        }
+    return LBM_OK;
 }
 
 }  // extern "C"

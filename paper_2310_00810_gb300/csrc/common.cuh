@@ -241,6 +241,36 @@ inline PlanInfo with_family(const PlanInfo& p, int family)
 }
 
 size_t compact_table_bytes(const PlanInfo& p, long long nf);
+
+// Batches in the fluid-only layout: the fluid nodes of every instance packed
+// into one compact state [Q][nfp], instance i at compact indices
+// [k0, k0 + nf), k0 a multiple of kBatchCmpAlign, so that every thread block
+// of the compact kernels belongs to one instance (blk_inst[block]).
+constexpr int kBatchCmpAlign = 256;
+struct BCmpInst {
+    Geo g;              // the instance's sizes (the compact kernels use no link words)
+    long long k0, nf;   // first compact index and fluid nodes
+    long long f_off;    // its dense [Q][N] arrays in a packed dense state (elements)
+    long long in_off;   // inlet densities and their gradients
+    long long acc_off;  // per-inlet-node accumulators (ny * nz)
+    int n_in, pad;
+};
+struct BCmpArgs {
+    Cmp c;                   // c.nf = nfp (the packed stride), c.idx local dense indices, c.nbr packed codes
+    const BCmpInst* insts;   // device
+    const int* blk_inst;     // device: instance of each kBatchCmpAlign-node block
+    unsigned n_blocks;       // nfp / kBatchCmpAlign
+    int q, prec, pdl;
+    uint32_t* status;
+};
+lbm_status bstep_launch_cmp(const BCmpArgs& a, int mode, const void* src, void* dst, bool dense_out,
+                            const double* rho_in, const double* tau, double rho_out, cudaStream_t s);
+lbm_status badjoint_launch_cmp(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out,
+                               const double* rho_in, const double* tau, double rho_out, double* grad_acc,
+                               double* partial, cudaStream_t s);
+lbm_status bgather_launch_cmp(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s);
+lbm_status bpack_launch_cmp(const Cmp& local, int q, long long k0, long long nfp, int32_t* idx, int32_t* nbr,
+                            cudaStream_t s);
 lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, const int32_t** cmap_out,
                          cudaStream_t s);
 lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* dst, bool dense_in, bool dense_out,

@@ -309,17 +309,14 @@ __device__ __noinline__ void step_node_eq6(const T* __restrict__ src, T* __restr
     store_node<Q, T, DOUT>(dst, v, k, c, g);
 }
 
-// MODE: stream-collide, collide-only or stream-only (step.cu).  DIN: the
-// collide-only input is a dense [Q][N] state; DOUT: the output is written
-// into a dense [Q][N] state (solid entries are left to the caller).
+// One node of a step (MODE: stream-collide, collide-only or stream-only,
+// step.cu).  DIN: the collide-only input is a dense [Q][N] state; DOUT: the
+// output is written into a dense [Q][N] state (solid entries are left to the
+// caller).  Shared by the single-lattice and the batched kernels.
 template <int Q, typename T, int MODE, bool DIN, bool DOUT>
-__global__ void __launch_bounds__(kCmpThreads, 4) k_step_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c,
-                                                             Geo g, Bc bc, const double* __restrict__ tau)
+__device__ __forceinline__ void step_cmp_node(const T* __restrict__ src, T* __restrict__ dst, long long k, const Cmp& c,
+                                              const Geo& g, const Bc& bc, T omega)
 {
-    pdl_enter();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= c.nf) return;
-    const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
     T v[Q];
     if (MODE == kCollideOnly) {
         const long long n = DIN ? (long long)c.idx[k] : k;
@@ -336,6 +333,17 @@ __global__ void __launch_bounds__(kCmpThreads, 4) k_step_cmp(const T* __restrict
     }
     if (MODE != kStreamOnly) collide_any<Q, T>(v, omega, bc);
     store_node<Q, T, DOUT>(dst, v, k, c, g);
+}
+
+template <int Q, typename T, int MODE, bool DIN, bool DOUT>
+__global__ void __launch_bounds__(kCmpThreads, 4) k_step_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c,
+                                                             Geo g, Bc bc, const double* __restrict__ tau)
+{
+    pdl_enter();
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= c.nf) return;
+    const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
+    step_cmp_node<Q, T, MODE, DIN, DOUT>(src, dst, k, c, g, bc, omega);
 }
 
 // Grid-stride form of the interior stream-collide step: a thread walks the
@@ -471,6 +479,52 @@ __device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T*
 // Adjoint step in the compact layout: the gather form of adjoint.cu.  The
 // forward copies f*_j(x) to x + c_j, the node that pulls direction j from x;
 // its compact index is nbr of direction opp(j) at k (x + c_j = x - c_opp(j)).
+// One node; returns its dL/domega term.  Shared by the single-lattice and the
+// batched kernels.
+template <int Q, typename T, bool T0>
+__device__ __forceinline__ T adjoint_cmp_node(const T* __restrict__ gprev, const T* __restrict__ lam_in,
+                                              T* __restrict__ lam_out, long long k, const Cmp& c, const Geo& g,
+                                              const Bc& bc, T omega, double* __restrict__ grad_acc)
+{
+    using L = Lattice<Q>;
+    int32_t code[Q];
+    if (load_codes<Q>(code, c, k)) return adjoint_node_eq6<Q, T, T0>(gprev, lam_in, lam_out, k, c, g, bc, omega, grad_acc);
+    // Interior node: every load of f^t and of the gathered lambda depends
+    // only on the table, so all 2 Q are in flight together.
+    const size_t NF = (size_t)c.nf;
+    const int32_t k32 = (int32_t)k;
+    T f[Q], mu[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const int o = L::opp(i);
+        if (T0) {
+            f[i] = T(0);
+        } else {
+            const bool fl = i > 0 && code[i] >= 0;
+            f[i] = (gprev + (size_t)(fl ? i : o) * NF)[fl ? code[i] : k32];
+        }
+        const bool ml = i > 0 && code[o] >= 0;
+        mu[i] = (lam_in + (size_t)(ml ? i : o) * NF)[ml ? code[o] : k32];
+    }
+    T drho, rho, u[3];
+    moments<Q, T>(f, drho, rho, u);
+    const T G[3] = {T(0), T(0), T(0)};
+    return adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF, bc);
+}
+
+// One FP64 partial per warp (its sum in T), accumulated in place across time
+// steps: no block barrier, so a warp that finishes early frees its slot at
+// once instead of waiting for the slowest warp of the block.  The warp of
+// compact node k owns slot k >> 5 (lane 0 holds the warp's first node).
+template <typename T>
+__device__ __forceinline__ void add_warp_partial(T dom, bool live, long long k, double* __restrict__ partial)
+{
+    T dw = dom;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
+    if ((threadIdx.x & 31) == 0 && live) partial[k >> 5] += (double)dw;
+}
+
 template <int Q, typename T, bool T0>
 __global__ void __launch_bounds__(kCmpThreads, 4)
     k_adjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c, Geo g,
@@ -478,45 +532,11 @@ __global__ void __launch_bounds__(kCmpThreads, 4)
                   double* __restrict__ partial)
 {
     pdl_enter();
-    using L = Lattice<Q>;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
     T dom = T(0);
-    if (k < c.nf) {
-        int32_t code[Q];
-        if (load_codes<Q>(code, c, k)) {
-            dom = adjoint_node_eq6<Q, T, T0>(gprev, lam_in, lam_out, k, c, g, bc, omega, grad_acc);
-        } else {
-            // Interior node: every load of f^t and of the gathered lambda
-            // depends only on the table, so all 2 Q are in flight together.
-            const size_t NF = (size_t)c.nf;
-            const int32_t k32 = (int32_t)k;
-            T f[Q], mu[Q];
-#pragma unroll
-            for (int i = 0; i < Q; ++i) {
-                const int o = L::opp(i);
-                if (T0) {
-                    f[i] = T(0);
-                } else {
-                    const bool fl = i > 0 && code[i] >= 0;
-                    f[i] = (gprev + (size_t)(fl ? i : o) * NF)[fl ? code[i] : k32];
-                }
-                const bool ml = i > 0 && code[o] >= 0;
-                mu[i] = (lam_in + (size_t)(ml ? i : o) * NF)[ml ? code[o] : k32];
-            }
-            T drho, rho, u[3];
-            moments<Q, T>(f, drho, rho, u);
-            const T G[3] = {T(0), T(0), T(0)};
-            dom = adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF, bc);
-        }
-    }
-    // one FP64 partial per warp (its sum in T), accumulated in place across
-    // time steps: no block barrier, so a warp that finishes early frees its
-    // slot at once instead of waiting for the slowest warp of the block
-    T dw = dom;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
-    if ((threadIdx.x & 31) == 0 && k < c.nf) partial[k >> 5] += (double)dw;  // lane 0: k = first node of the warp
+    if (k < c.nf) dom = adjoint_cmp_node<Q, T, T0>(gprev, lam_in, lam_out, k, c, g, bc, omega, grad_acc);
+    add_warp_partial<T>(dom, k < c.nf, k, partial);
 }
 
 // Reverse of the extrapolated Eq. 6 velocity in the compact layout: the
@@ -562,6 +582,129 @@ __global__ void __launch_bounds__(kCmpThreads)
         }
         if (xin) grad_acc[row] += dg;
     }
+}
+
+// ------------------------------------------------- batches, packed layout
+
+static_assert(kBatchCmpAlign == kCmpThreads, "one thread block per aligned node range of a batch instance");
+
+// The per-instance boundary data of a batch block (batches run BGK with the
+// node-velocity Eq. 6).
+__device__ __forceinline__ Bc batch_bc(const BCmpInst& I, const double* rho_in, double rho_out, uint32_t* status)
+{
+    Bc bc;
+    bc.rho_in = rho_in + I.in_off;
+    bc.profile = I.n_in > 1 ? 1 : 0;
+    bc.rho_out = rho_out;
+    bc.status = status;
+    return bc;
+}
+
+// One step over a packed batch: the block's instance gives the sizes, tau,
+// the inlet densities and (DIN / DOUT) the offset of its dense arrays; the
+// node update is step_cmp_node, so every instance gets bit for bit what a
+// single compact plan computes.
+template <int Q, typename T, int MODE, bool DIN, bool DOUT>
+__global__ void __launch_bounds__(kCmpThreads, 4)
+    k_bstep_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c, const BCmpInst* __restrict__ insts,
+                const int* __restrict__ blk_inst, const double* __restrict__ rho_in, const double* __restrict__ tau,
+                double rho_out, uint32_t* status)
+{
+    pdl_enter();
+    const int i = blk_inst[blockIdx.x];
+    const BCmpInst I = insts[i];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= I.k0 + I.nf) return;  // padding of the instance's last block
+    const Bc bc = batch_bc(I, rho_in, rho_out, status);
+    const T omega = T(1) / T(tau[i]);
+    step_cmp_node<Q, T, MODE, DIN, DOUT>(DIN ? src + I.f_off : src, DOUT ? dst + I.f_off : dst, k, c, I.g, bc, omega);
+}
+
+// One adjoint step over a packed batch (adjoint_cmp_node); the warp partials
+// of instance i occupy slots [k0 / 32, (k0 + nf + 31) / 32).
+template <int Q, typename T, bool T0>
+__global__ void __launch_bounds__(kCmpThreads, 4)
+    k_badjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c,
+                   const BCmpInst* __restrict__ insts, const int* __restrict__ blk_inst,
+                   const double* __restrict__ rho_in, const double* __restrict__ tau, double rho_out,
+                   uint32_t* status, double* __restrict__ grad_acc, double* __restrict__ partial)
+{
+    pdl_enter();
+    const int i = blk_inst[blockIdx.x];
+    const BCmpInst I = insts[i];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = k < I.k0 + I.nf;
+    const Bc bc = batch_bc(I, rho_in, rho_out, status);
+    const T omega = T(1) / T(tau[i]);
+    T dom = T(0);
+    if (live) dom = adjoint_cmp_node<Q, T, T0>(gprev, lam_in, lam_out, k, c, I.g, bc, omega, grad_acc + I.acc_off);
+    add_warp_partial<T>(dom, live, k, partial);
+}
+
+// The caller's packed dense arrays -> the packed compact state.
+template <typename T>
+__global__ void __launch_bounds__(kCmpThreads)
+    k_bgather_cmp(const T* __restrict__ dense, T* __restrict__ cmp, Cmp c, const BCmpInst* __restrict__ insts,
+                  const int* __restrict__ blk_inst, int q)
+{
+    const BCmpInst I = insts[blk_inst[blockIdx.x]];
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= I.k0 + I.nf) return;
+    const long long n = c.idx[k];
+    for (int d = 0; d < q; ++d) cmp[(long long)d * c.nf + k] = dense[I.f_off + (long long)d * I.g.N + n];
+}
+
+// One instance's tables (built by compact_build) into the packed arrays:
+// dense indices as they are, neighbour codes shifted by the instance's k0.
+__global__ void __launch_bounds__(256) k_bpack_cmp(const int32_t* __restrict__ idx_l, const int32_t* __restrict__ nbr_l,
+                                                   long long nf, int q, long long k0, long long nfp,
+                                                   int32_t* __restrict__ idx, int32_t* __restrict__ nbr)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    idx[k0 + k] = idx_l[k];
+    for (int d = 0; d < q - 1; ++d) {
+        const int32_t code = nbr_l[(long long)d * nf + k];
+        nbr[(long long)d * nfp + k0 + k] = code >= 0 ? (int32_t)(code + k0) : code;
+    }
+}
+
+template <int Q, typename T>
+void launch_bstep(const BCmpArgs& a, int mode, const void* src, void* dst, bool dout, const double* rho_in,
+                  const double* tau, double rho_out, cudaStream_t s)
+{
+    const T* x = static_cast<const T*>(src);
+    T* y = static_cast<T*>(dst);
+    const dim3 grid(a.n_blocks), block(kCmpThreads);
+    if (mode == kStreamCollide)
+        launch_k(a.pdl, k_bstep_cmp<Q, T, kStreamCollide, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, rho_in, tau, rho_out, a.status);
+    else if (mode == kCollideOnly)
+        launch_k(a.pdl, k_bstep_cmp<Q, T, kCollideOnly, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, rho_in, tau, rho_out, a.status);
+    else if (dout)
+        launch_k(a.pdl, k_bstep_cmp<Q, T, kStreamOnly, false, true>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, rho_in, tau, rho_out, a.status);
+    else
+        launch_k(a.pdl, k_bstep_cmp<Q, T, kStreamOnly, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, rho_in, tau, rho_out, a.status);
+}
+
+template <int Q, typename T>
+void launch_badjoint(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out,
+                     const double* rho_in, const double* tau, double rho_out, double* grad_acc, double* partial,
+                     cudaStream_t s)
+{
+    const T* gp = static_cast<const T*>(gprev);
+    const T* li = static_cast<const T*>(lam_in);
+    T* lo = static_cast<T*>(lam_out);
+    const dim3 grid(a.n_blocks), block(kCmpThreads);
+    if (t0)
+        launch_k(a.pdl, k_badjoint_cmp<Q, T, true>, grid, block, 0, s, gp, li, lo, a.c, a.insts, a.blk_inst, rho_in,
+                 tau, rho_out, a.status, grad_acc, partial);
+    else
+        launch_k(a.pdl, k_badjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, a.c, a.insts, a.blk_inst, rho_in,
+                 tau, rho_out, a.status, grad_acc, partial);
 }
 
 // CTAs of `kernel` that fit on the GPU at once (the grid of a grid-stride launch).
@@ -715,6 +858,57 @@ lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* com
     else
         k_cmp_gather<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
                                                     p.cmp, p.geo.N, p.q);
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status bstep_launch_cmp(const BCmpArgs& a, int mode, const void* src, void* dst, bool dense_out,
+                            const double* rho_in, const double* tau, double rho_out, cudaStream_t s)
+{
+    if (a.n_blocks == 0) return LBM_OK;
+    if (a.q == 9 && a.prec == 4) launch_bstep<9, float>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
+    else if (a.q == 9 && a.prec == 8) launch_bstep<9, double>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
+    else if (a.q == 19 && a.prec == 4) launch_bstep<19, float>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
+    else if (a.q == 19 && a.prec == 8)
+        launch_bstep<19, double>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status badjoint_launch_cmp(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out,
+                               const double* rho_in, const double* tau, double rho_out, double* grad_acc,
+                               double* partial, cudaStream_t s)
+{
+    if (a.n_blocks == 0) return LBM_OK;
+    if (a.q == 9 && a.prec == 4)
+        launch_badjoint<9, float>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
+    else if (a.q == 9 && a.prec == 8)
+        launch_badjoint<9, double>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
+    else if (a.q == 19 && a.prec == 4)
+        launch_badjoint<19, float>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
+    else if (a.q == 19 && a.prec == 8)
+        launch_badjoint<19, double>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status bgather_launch_cmp(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s)
+{
+    if (a.n_blocks == 0) return LBM_OK;
+    const dim3 grid(a.n_blocks), block(kCmpThreads);
+    if (a.prec == 4)
+        k_bgather_cmp<float><<<grid, block, 0, s>>>(static_cast<const float*>(dense), static_cast<float*>(compact), a.c,
+                                                    a.insts, a.blk_inst, a.q);
+    else
+        k_bgather_cmp<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
+                                                     a.c, a.insts, a.blk_inst, a.q);
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status bpack_launch_cmp(const Cmp& local, int q, long long k0, long long nfp, int32_t* idx, int32_t* nbr,
+                            cudaStream_t s)
+{
+    if (local.nf == 0) return LBM_OK;
+    k_bpack_cmp<<<(unsigned)((local.nf + 255) / 256), 256, 0, s>>>(local.idx, local.nbr, local.nf, q, k0, nfp, idx, nbr);
     return cuda_status(cudaGetLastError());
 }
 

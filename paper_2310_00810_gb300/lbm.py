@@ -38,6 +38,7 @@ ENTRY_POINTS = (
     "lbm_spline_profile", "lbm_spline_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
+    "lbm_batch_compact_size", "lbm_batch_compact_bind", "lbm_batch_get_status",
     "unet_param_layout", "unet_workspace_size", "unet_pack_input", "unet_prepare_weights", "unet_forward",
     "unet_backward", "unet_adam",
 )
@@ -121,6 +122,9 @@ def load():
                 "lbm_batch_forward": [vp, vp, vp, f64, vp, vp, vp],
                 "lbm_batch_loss_grad": [vp, vp, vp, vp, vp, vp, vp, vp],
                 "lbm_batch_adjoint": [vp, vp, vp, f64, vp, vp, vp, vp, vp],
+                "lbm_batch_compact_size": [vp, vp, C.POINTER(C.c_size_t)],
+                "lbm_batch_compact_bind": [vp, vp, vp, vp, vp],
+                "lbm_batch_get_status": [vp, vp, C.POINTER(C.c_int)],
                 "lbm_error_string": [C.c_int],
                 "unet_param_layout": [i32, vp, vp, vp, vp],
                 "unet_workspace_size": [vp, C.POINTER(C.c_size_t)],
@@ -543,11 +547,13 @@ class Solver:
 class Batch:
     """Many independent lattices of different sizes advanced together
     (lbm_batch_*).  ``sizes``: list of (nx, ny, nz); ``geometries``: one
-    lbm_init_geometry keyword dict per instance.  Packed device buffers are
-    allocated with torch; ``view_*`` give per-instance views into them."""
+    lbm_init_geometry keyword dict per instance; ``layout``: "dense" or
+    "compact" (every instance's fluid nodes packed, lbm_batch_compact_bind).
+    Packed device buffers are allocated with torch; ``view_*`` give
+    per-instance views into them."""
 
     def __init__(self, q, sizes, precision=4, n_steps=1, ckpt_stride=0, loss_kind=LBM_LOSS_VEC,
-                 loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST, geometries=None, device="cuda"):
+                 loss_norm=LBM_NORM_SUM, inlet_kind=LBM_INLET_CONST, geometries=None, device="cuda", layout="dense"):
         import numpy as np
 
         self.device = torch.device(device)
@@ -586,12 +592,47 @@ class Batch:
                                               _ptr(self.info), _ptr(self.ws), _stream(None)),
                "lbm_batch_init_geometry")
 
+        self.layout, self.tables = "dense", None
+        self.set_layout(layout)
+
     def _run(self, fn):
         cur = torch.cuda.current_stream(self.device)
         self.stream.wait_stream(cur)
         with torch.cuda.stream(self.stream):
             fn()
         cur.wait_stream(self.stream)
+
+    def set_layout(self, layout: str) -> None:
+        """Dense or packed fluid-only ("compact") internal states (the same
+        results; the packed arrays the caller sees do not change)."""
+        if layout == self.layout:
+            return
+        if layout == "compact":
+            import numpy as np
+
+            torch.cuda.current_stream(self.device).synchronize()
+            nf = self.info.view(self.n, 4)[:, 3].cpu().numpy().astype(np.int64)
+            nbytes = C.c_size_t()
+            _check(load().lbm_batch_compact_size(self.handle, nf.ctypes.data_as(C.c_void_p), C.byref(nbytes)),
+                   "lbm_batch_compact_size")
+            tables = torch.empty(max(nbytes.value, 256), dtype=torch.uint8, device=self.device)
+            self._run(lambda: _check(load().lbm_batch_compact_bind(self.handle, nf.ctypes.data_as(C.c_void_p),
+                                                                   _ptr(tables), _ptr(self.ws),
+                                                                   _stream(self.stream)), "lbm_batch_compact_bind"))
+            self.tables = tables
+        elif layout == "dense":
+            self._run(lambda: _check(load().lbm_batch_compact_bind(self.handle, None, None, _ptr(self.ws),
+                                                                   _stream(self.stream)), "lbm_batch_compact_bind"))
+            self.tables = None
+        else:
+            raise ValueError(f"layout must be dense or compact, not {layout!r}")
+        self.layout = layout
+
+    def status(self) -> int:
+        """Reads and clears the batch's device status word."""
+        st = C.c_int()
+        _check(load().lbm_batch_get_status(self.handle, _ptr(self.ws), C.byref(st)), "lbm_batch_get_status")
+        return st.value
 
     # sizes of the packed buffers
     def new_state(self):

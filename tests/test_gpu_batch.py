@@ -96,3 +96,103 @@ def test_batch_gradient_matches_oracle():
         assert abs(loss[i].item() - Lw) <= 1e-10 * Lw
         np.testing.assert_allclose(b.view_inlet(g_in, i).cpu().numpy(), gw, rtol=1e-9, atol=0)
         assert abs(g_tau[i].item() - gtw) <= 1e-9 * abs(gtw)
+
+
+def _batch_case(case, profile, layout):
+    q, prec, sizes = CASES[case]
+    T = 40 if q == 9 else 16
+    inlet = lbm.LBM_INLET_PROFILE if profile else lbm.LBM_INLET_CONST
+    geoms = []
+    for i, (nx, ny, nz) in enumerate(sizes):
+        if q == 9:
+            geoms.append(dict(kind=lbm.LBM_GEOM_DISKS, seed=60 + i, r_min=3, r_max=6, target_porosity=0.7,
+                              inlet_buffer=4))
+        else:
+            geoms.append(dict(kind=lbm.LBM_GEOM_SPHERES, seed=60 + i, r_min=2, r_max=2, target_porosity=0.75,
+                              inlet_buffer=4))
+    b = lbm.Batch(q, sizes, precision=prec, n_steps=T, inlet_kind=inlet, geometries=geoms, layout=layout)
+    rho_in = b.new_inlet()
+    ut = b.new_velocity()
+    taus = []
+    for i, (nx, ny, nz) in enumerate(sizes):
+        n_in = ny * nz if profile else 1
+        b.view_inlet(rho_in, i).copy_(dev(1.0 + (W.inlet_profile(n_in, seed=70 + i) if profile
+                                                 else np.array([1e-3 * (1 + i)]))))
+        b.view_velocity(ut, i).copy_(dev(W.perturbation((b.d,) + b.shape(i), seed=80 + i, scale=1e-3)))
+        taus.append(0.75 + 0.05 * i)
+    return b, geoms, T, inlet, rho_in, ut, dev(taus)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("profile", [False, True])
+def test_packed_fluid_only_batch_is_bitwise_single_compact_plans(case, profile):
+    """The packed fluid-only batch runs the compact per-node code of a single
+    plan: populations, lambda and gradients equal bit for bit (the loss, a
+    differently ordered FP64 sum, to 1e-12)."""
+    q, prec, sizes = CASES[case]
+    b, geoms, T, inlet, rho_in, ut, tau = _batch_case(case, profile, "compact")
+    f = b.forward(rho_in, tau, 1.0)
+    loss, lam = b.loss_grad(f, ut)
+    g_in, g_tau = b.adjoint(rho_in, tau, 1.0, lam)
+    torch.cuda.synchronize()
+    assert b.status() == lbm.LBM_OK
+    for i, (nx, ny, nz) in enumerate(sizes):
+        s = lbm.Solver(q, nx, ny, nz, precision=prec, n_steps=T, inlet_kind=inlet, geometry=geoms[i],
+                       layout="compact")
+        fi = s.forward(b.view_inlet(rho_in, i).contiguous(), tau[i:i + 1].contiguous(), 1.0)
+        assert torch.equal(fi, b.view_state(f, i))
+        Li, lami = s.loss_grad(fi, b.view_velocity(ut, i).contiguous())
+        gi, gti = s.adjoint(b.view_inlet(rho_in, i).contiguous(), tau[i:i + 1].contiguous(), 1.0, lami)
+        assert abs(Li.item() - loss[i].item()) <= 1e-12 * abs(Li.item())
+        assert torch.equal(gi, b.view_inlet(g_in, i))
+        assert gti.item() == g_tau[i].item()
+
+
+def test_packed_batch_matches_oracle_and_switches_back():
+    """FP64 packed batch against the oracle; switching back to the dense
+    layout gives the dense batch's result."""
+    sizes = [(96, 40, 1), (64, 24, 1), (72, 20, 1)]
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=90 + i, r_min=3, r_max=5, target_porosity=0.72, inlet_buffer=4)
+             for i in range(3)]
+    b = lbm.Batch(9, sizes, precision=8, n_steps=30, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms,
+                  layout="compact")
+    rho_in = b.new_inlet()
+    ut = b.new_velocity()
+    for i in range(3):
+        b.view_inlet(rho_in, i).copy_(dev(1.0 + W.inlet_profile(sizes[i][1], seed=91 + i)))
+        b.view_velocity(ut, i).copy_(dev(W.perturbation((2,) + b.shape(i), seed=92 + i, scale=1e-3)))
+    tau = dev([0.8, 0.9, 0.7])
+    f = b.forward(rho_in, tau, 1.0)
+    loss, lam = b.loss_grad(f, ut)
+    g_in, g_tau = b.adjoint(rho_in, tau, 1.0, lam)
+    for i in range(3):
+        m = b.view_mask(i).cpu().numpy()
+        Lw, gw, gtw = O.gradient(9, m, b.view_inlet(rho_in, i).cpu().numpy(), 1.0, [0.8, 0.9, 0.7][i], 30,
+                                 b.view_velocity(ut, i).cpu().numpy(), ckpt_stride=6)
+        assert abs(loss[i].item() - Lw) <= 1e-10 * Lw
+        np.testing.assert_allclose(b.view_inlet(g_in, i).cpu().numpy(), gw, rtol=1e-9, atol=0)
+        assert abs(g_tau[i].item() - gtw) <= 1e-9 * abs(gtw)
+    b.set_layout("dense")
+    f2 = b.forward(rho_in, tau, 1.0)
+    for i in range(3):
+        fl = ~b.view_mask(i).bool()
+        np.testing.assert_allclose(b.view_state(f2, i)[:, fl].cpu().numpy(), b.view_state(f, i)[:, fl].cpu().numpy(),
+                                   rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("layout", ["dense", "compact"])
+def test_batch_status_word_reports_nonfinite(layout):
+    sizes = [(64, 24, 1), (96, 32, 1)]
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=30 + i, r_min=3, r_max=5, target_porosity=0.75, inlet_buffer=4)
+             for i in range(2)]
+    b = lbm.Batch(9, sizes, precision=4, n_steps=20, inlet_kind=lbm.LBM_INLET_CONST, geometries=geoms,
+                  layout=layout)
+    rho_in = b.new_inlet()
+    rho_in.fill_(1.001)
+    b.view_inlet(rho_in, 1).fill_(float("nan"))
+    tau = dev([0.8, 0.8])
+    f = b.forward(rho_in, tau, 1.0)
+    b.loss_grad(f, b.new_velocity())
+    torch.cuda.synchronize()
+    assert b.status() == lbm.LBM_ERR_NONFINITE
+    assert b.status() == lbm.LBM_OK  # reading clears the word

@@ -60,7 +60,7 @@ def test_fresh_buffers_give_the_fresh_plan_result(q, layout):
     d = s.plan.d
     for call in range(3):
         n_in = s.plan.n_in
-        rin = _dev(1.0 + (W.inlet_profile(n_in, seed=70 + call) if n_in > 1 else [1e-3 * (1 + call)]))
+        rin = _dev(1.0 + (W.inlet_profile(n_in, seed=70 + call) if n_in > 1 else np.array([1e-3 * (1 + call)])))
         tau = _dev([0.8 + 0.05 * call])
         ut = _dev(W.perturbation((d, *s.plan.shape), seed=80 + call, scale=1e-4))
         got = _evaluate(s, rin, tau, ut)
