@@ -55,6 +55,8 @@ def parse():
                          "unet: training throughput of the learned initialiser")
     ap.add_argument("--unet-batch", type=int, default=16)
     ap.add_argument("--lattice", default="disks8192x4096", help="workload name for --mode kernels")
+    ap.add_argument("--layout", default=None, choices=[None, "dense", "compact"],
+                    help="state layout for --mode kernels (default: compact for D3Q19, dense for D2Q9)")
     ap.add_argument("--launches", type=int, default=20)
     ap.add_argument("--no-invert", action="store_true", help="skip the time-to-1e-3 inversion leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
@@ -537,7 +539,7 @@ def learned_init_leg(device, n_train, epochs, n_eval, time_limit):
             "held_out": rows}
 
 
-def batch_leg(device, count, rank, steps=2):
+def batch_leg(device, count, rank, steps=2, layout="dense"):
     """The batched inversions: `count` independent D2Q9 FP32 lattices with
     nx = 32 U{4..32}, ny = nx / 2, seeded disks (porosity U[0.5, 0.7]),
     T = 5000, one gradient evaluation (forward + loss + checkpointed adjoint)
@@ -553,7 +555,7 @@ def batch_leg(device, count, rank, steps=2):
     geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=sd, r_min=6, r_max=12, target_porosity=por)
              for nx, ny, por, sd in spec]
     b = lbm.Batch(9, sizes, precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms,
-                  device=device)
+                  device=device, layout=layout)
     rho_in = b.new_inlet()
     for i, (nx, ny, _, sd) in enumerate(spec):
         b.view_inlet(rho_in, i).copy_(torch.as_tensor(1.0 + W.inlet_profile(ny, seed=2000 + sd), device=device))
@@ -829,7 +831,9 @@ def run_kernels(args):
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm_peak = json.load(open(peaks))["hbm_gbs"] if os.path.exists(peaks) else 6800.0
     print(json.dumps({"mode": "kernels", "lattice": args.lattice,
-                      "kernels": kernel_rooflines(device, hbm_peak, args.lattice, args.launches)}), flush=True)
+                      "layout": args.layout,
+                      "kernels": kernel_rooflines(device, hbm_peak, args.lattice, args.launches, args.layout)}),
+          flush=True)
 
 
 def run_unet(args):

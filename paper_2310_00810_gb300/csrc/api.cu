@@ -234,6 +234,7 @@ void set_dense(lbm_plan* p)
 {
     p->info.cmp = Cmp{0, nullptr, nullptr};
     p->info.cmp_map = nullptr;
+    p->info.cmp_inst = nullptr;
     p->info.state_bytes = p->dense_state_bytes;
     p->info.n_partial = p->dense_n_partial;
     layout(p);
@@ -546,9 +547,11 @@ lbm_status lbm_compact_bind(lbm_plan* p, int64_t n_fluid, void* d_tables, void* 
     if (!d_tables || !aligned256(d_tables)) return LBM_ERR_INVALID_ARG;
     Cmp c{0, nullptr, nullptr};
     const int32_t* cmap = nullptr;
-    LBM_TRY(compact_build(p->info, n_fluid, d_tables, &c, &cmap, static_cast<cudaStream_t>(stream)));
+    const BCmpInst* inst = nullptr;
+    LBM_TRY(compact_build(p->info, n_fluid, d_tables, &c, &cmap, &inst, static_cast<cudaStream_t>(stream)));
     p->info.cmp = c;
     p->info.cmp_map = cmap;
+    p->info.cmp_inst = inst;
     p->info.state_bytes = (size_t)p->info.q * (size_t)n_fluid * (size_t)p->info.prec;
     p->info.n_partial = std::max(p->dense_n_partial, (int)((n_fluid + 31) / 32));  // one slot per warp
     layout(p);

@@ -755,7 +755,8 @@ lbm_status lbm_batch_adjoint(lbm_batch* b, const double* d_rho_in, const double*
         if (cudaMemsetAsync(ws + b->o_part, 0, sizeof(double) * b->n_part, st_) != cudaSuccess) return LBM_ERR_CUDA;
         const void* lam_cur = d_lambda;
         int lam_next = 0;
-        if (b->cmp) {  // lambda^T into the packed compact layout
+        if (b->cmp) {  // lambda^T into the packed compact layout; its padding slots must start at zero
+            if (cudaMemsetAsync(ws + b->o_lam[1], 0, b->cmp_state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;
             lbm_status st = bgather_launch_cmp(ca, d_lambda, ws + b->o_lam[1], st_);
             if (st != LBM_OK) return st;
             lam_cur = ws + b->o_lam[1];
@@ -853,6 +854,10 @@ lbm_status lbm_batch_compact_bind(lbm_batch* b, const int64_t* n_fluid, void* d_
     std::vector<int> blk((size_t)(nfp / kBatchCmpAlign));
     // each instance's tables are built in the workspace's state buffers (free at this point), then
     // packed; compact_build checks the fluid count against the link words (and synchronises)
+    // padding nodes: bounce-back in every direction (their loads stay at their own index)
+    static_assert(kCmpBB == -1, "padding codes are written as all-ones bytes");
+    if (nfp > 0 && cudaMemsetAsync(nbr, 0xFF, sizeof(int32_t) * (size_t)(b->q - 1) * (size_t)nfp, s) != cudaSuccess)
+        return LBM_ERR_CUDA;
     unsigned char* scratch = ws + b->o_ping[0];
     const size_t cap = b->o_ckpt - b->o_ping[0];
     for (int i = 0; i < b->n; ++i) {
@@ -862,7 +867,7 @@ lbm_status lbm_batch_compact_bind(lbm_batch* b, const int64_t* n_fluid, void* d_
         if (compact_table_bytes(I, c.nf) > cap) return LBM_ERR_INVALID_ARG;
         Cmp local{0, nullptr, nullptr};
         const int32_t* cmap = nullptr;
-        lbm_status st = compact_build(I, c.nf, scratch, &local, &cmap, s);
+        lbm_status st = compact_build(I, c.nf, scratch, &local, &cmap, nullptr, s);
         if (st != LBM_OK) return st;
         st = bpack_launch_cmp(local, b->q, c.k0, nfp, idx, nbr, s);
         if (st != LBM_OK) return st;

@@ -61,6 +61,8 @@ struct Cmp {
     const int32_t* nbr;    // nbr[(i - 1) * nf + k], i = 1..Q-1: compact index of x - c_i, or kCmpBB / kCmpABB
 };
 
+struct BCmpInst;
+
 // Everything a launch needs to know about the lattice and its precision.
 struct PlanInfo {
     int q, d, prec;
@@ -94,6 +96,7 @@ struct PlanInfo {
     size_t state_bytes;   // bytes of one internal state (Q N, or Q nf in the compact layout)
     Cmp cmp;
     const int32_t* cmp_map;  // cmap[n]: compact index of dense node n, or -1 for a solid node (compact layout)
+    const BCmpInst* cmp_inst;  // the lattice as a one-instance pack (compact layout; device)
 };
 
 // Grid barrier words of the persistent sweeps (in the status section).
@@ -272,7 +275,7 @@ lbm_status bgather_launch_cmp(const BCmpArgs& a, const void* dense, void* compac
 lbm_status bpack_launch_cmp(const Cmp& local, int q, long long k0, long long nfp, int32_t* idx, int32_t* nbr,
                             cudaStream_t s);
 lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, const int32_t** cmap_out,
-                         cudaStream_t s);
+                         const BCmpInst** inst_out, cudaStream_t s);
 lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* dst, bool dense_in, bool dense_out,
                            const Bc& bc, const double* tau, cudaStream_t s);
 lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,

@@ -29,6 +29,12 @@
 
 namespace lbm {
 
+#define LBM_CMP_TRY(expr)                 \
+    do {                                  \
+        lbm_status st__ = (expr);         \
+        if (st__ != LBM_OK) return st__;  \
+    } while (0)
+
 namespace {
 
 constexpr int kCmpThreads = 256;
@@ -37,7 +43,7 @@ constexpr int kScanNodes = 1024;  // nodes per block of the table-building scan 
 size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 struct TableLayout {
-    size_t idx, nbr, cmap, blk, total_slot, bytes;
+    size_t inst, idx, nbr, cmap, blk, total_slot, bytes;
 };
 
 TableLayout table_layout(const PlanInfo& p, long long nf)
@@ -45,6 +51,8 @@ TableLayout table_layout(const PlanInfo& p, long long nf)
     TableLayout t;
     const long long nblk = (p.geo.N + kScanNodes - 1) / kScanNodes;
     size_t o = 0;
+    t.inst = o;  // the lattice as a pack of one (BCmpInst)
+    o += a256(sizeof(BCmpInst));
     t.idx = o;
     o += a256(sizeof(int32_t) * (size_t)nf);
     t.nbr = o;
@@ -294,84 +302,69 @@ __device__ __forceinline__ void store_node(T* __restrict__ dst, const T (&v)[Q],
     for (int i = 0; i < Q; ++i) dst[(size_t)i * S + n] = v[i];
 }
 
+__device__ __forceinline__ int block_instance(const int* __restrict__ blk_inst, long long k)
+{
+    return blk_inst ? blk_inst[k / kCmpThreads] : 0;
+}
+
+// The instance's boundary data: its inlet densities, on top of the call's
+// options and status word (tmpl.rho_in is the base of the inlet array).
+__device__ __forceinline__ Bc instance_bc(const Bc& tmpl, const BCmpInst& I)
+{
+    Bc bc = tmpl;
+    bc.rho_in = tmpl.rho_in + I.in_off;
+    bc.profile = I.n_in > 1 ? 1 : 0;
+    return bc;
+}
+
 // Update of a node with an Eq. 6 link (x = 0 or nx - 1), out of line so that
 // its extra live values (the node's own populations and velocity) do not
 // raise the register count, and lower the occupancy, of the interior path.
 template <int Q, typename T, int MODE, bool DOUT>
-__device__ __noinline__ void step_node_eq6(const T* __restrict__ src, T* __restrict__ dst, long long k, Cmp c, Geo g,
-                                           Bc bc, T omega)
+__device__ __noinline__ void step_node_eq6(const T* __restrict__ src, T* __restrict__ dst, long long k, Cmp c,
+                                           const BCmpInst* __restrict__ Ip, Bc tmpl, T omega)
 {
+    const Geo g = Ip->g;
+    const Bc bc = instance_bc(tmpl, *Ip);
     int32_t code[Q];
     load_codes<Q>(code, c, k);
     T v[Q];
     pull_cmp<Q, T>(v, src, k, c.nf, code, true, c, g, bc);
     if (MODE != kStreamOnly) collide_any<Q, T>(v, omega, bc);
-    store_node<Q, T, DOUT>(dst, v, k, c, g);
+    store_node<Q, T, DOUT>(DOUT ? dst + Ip->f_off : dst, v, k, c, g);
 }
 
 // One node of a step (MODE: stream-collide, collide-only or stream-only,
-// step.cu).  DIN: the collide-only input is a dense [Q][N] state; DOUT: the
-// output is written into a dense [Q][N] state (solid entries are left to the
-// caller).  Shared by the single-lattice and the batched kernels.
+// step.cu) of instance *Ip.  DIN: the collide-only input is the instance's
+// dense [Q][N] array; DOUT: the output is written into it (solid entries are
+// left to the caller).  Interior nodes need only the call's options (tmpl);
+// the instance's sizes and inlet data are read on the Eq. 6 path alone.
 template <int Q, typename T, int MODE, bool DIN, bool DOUT>
 __device__ __forceinline__ void step_cmp_node(const T* __restrict__ src, T* __restrict__ dst, long long k, const Cmp& c,
-                                              const Geo& g, const Bc& bc, T omega)
+                                              const BCmpInst* __restrict__ Ip, const Bc& tmpl, T omega)
 {
     T v[Q];
     if (MODE == kCollideOnly) {
-        const long long n = DIN ? (long long)c.idx[k] : k;
-        const size_t S = DIN ? (size_t)g.N : (size_t)c.nf;
+        if (DIN) {
+            const long long n = c.idx[k], N = Ip->g.N;
+            const T* s = src + Ip->f_off;
 #pragma unroll
-        for (int i = 0; i < Q; ++i) v[i] = src[(size_t)i * S + n];
+            for (int i = 0; i < Q; ++i) v[i] = s[(size_t)i * (size_t)N + n];
+        } else {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) v[i] = src[(size_t)i * (size_t)c.nf + k];
+        }
     } else {
         int32_t code[Q];
         if (load_codes<Q>(code, c, k)) {
-            step_node_eq6<Q, T, MODE, DOUT>(src, dst, k, c, g, bc, omega);
+            step_node_eq6<Q, T, MODE, DOUT>(src, dst, k, c, Ip, tmpl, omega);
             return;
         }
-        pull_cmp<Q, T>(v, src, k, c.nf, code, false, c, g, bc);
+        pull_cmp<Q, T>(v, src, k, c.nf, code, false, c, Ip->g, tmpl);  // interior: no sizes or inlet data used
     }
-    if (MODE != kStreamOnly) collide_any<Q, T>(v, omega, bc);
-    store_node<Q, T, DOUT>(dst, v, k, c, g);
-}
-
-template <int Q, typename T, int MODE, bool DIN, bool DOUT>
-__global__ void __launch_bounds__(kCmpThreads, 4) k_step_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c,
-                                                             Geo g, Bc bc, const double* __restrict__ tau)
-{
-    pdl_enter();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= c.nf) return;
-    const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
-    step_cmp_node<Q, T, MODE, DIN, DOUT>(src, dst, k, c, g, bc, omega);
-}
-
-// Grid-stride form of the interior stream-collide step: a thread walks the
-// nodes k, k + stride, ... and loads the table entries of its next node
-// before the populations of the current one, so the table latency of node
-// k + stride overlaps the population loads of node k.
-template <int Q, typename T, int MINB>
-__global__ void __launch_bounds__(kCmpThreads, MINB) k_step_cmp_gs(const T* __restrict__ src, T* __restrict__ dst, Cmp c,
-                                                                Geo g, Bc bc, const double* __restrict__ tau)
-{
-    pdl_enter();
-    const T omega = T(1) / T(*tau);
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int32_t nxt[Q];
-    bool bnd_next = k < c.nf ? load_codes<Q>(nxt, c, k) : false;
-    for (; k < c.nf; k += stride) {
-        const bool bnd = bnd_next;
-        T v[Q];
-        if (!bnd) pull_cmp<Q, T>(v, src, k, c.nf, nxt, false, c, g, bc);  // population loads issued first
-        if (k + stride < c.nf) bnd_next = load_codes<Q>(nxt, c, k + stride);  // then the next node's table
-        if (bnd) {
-            step_node_eq6<Q, T, kStreamCollide, false>(src, dst, k, c, g, bc, omega);
-            continue;
-        }
-        collide_any<Q, T>(v, omega, bc);
-        store_node<Q, T, false>(dst, v, k, c, g);
-    }
+    if (MODE != kStreamOnly) collide_any<Q, T>(v, omega, tmpl);
+    if (DOUT) store_node<Q, T, true>(dst + Ip->f_off, v, k, c, Ip->g);
+    else store_node<Q, T, false>(dst, v, k, c, Ip->g);
 }
 
 // Transpose of the collision (adjoint.cu, step 3) at one node, from f^t (its
@@ -427,10 +420,14 @@ __device__ __forceinline__ T adjoint_collision(const T (&f)[Q], const T (&mu)[Q]
 // node) and returns its dL/domega term.
 template <int Q, typename T, bool T0>
 __device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T* __restrict__ lam_in,
-                                                T* __restrict__ lam_out, long long k, Cmp c, Geo g, Bc bc, T omega,
-                                                double* __restrict__ grad_acc)
+                                           T* __restrict__ lam_out, long long k, Cmp c,
+                                           const BCmpInst* __restrict__ Ip, Bc tmpl, T omega,
+                                           double* __restrict__ grad_acc_base)
 {
     using L = Lattice<Q>;
+    const Geo g = Ip->g;
+    const Bc bc = instance_bc(tmpl, *Ip);
+    double* __restrict__ grad_acc = grad_acc_base + Ip->acc_off;
     const size_t NF = (size_t)c.nf;
     int32_t code[Q];
     load_codes<Q>(code, c, k);
@@ -479,16 +476,18 @@ __device__ __noinline__ T adjoint_node_eq6(const T* __restrict__ gprev, const T*
 // Adjoint step in the compact layout: the gather form of adjoint.cu.  The
 // forward copies f*_j(x) to x + c_j, the node that pulls direction j from x;
 // its compact index is nbr of direction opp(j) at k (x + c_j = x - c_opp(j)).
-// One node; returns its dL/domega term.  Shared by the single-lattice and the
-// batched kernels.
+// One node of instance *Ip; returns its dL/domega term.  As in step_cmp_node,
+// interior nodes use the call's options only.
 template <int Q, typename T, bool T0>
 __device__ __forceinline__ T adjoint_cmp_node(const T* __restrict__ gprev, const T* __restrict__ lam_in,
-                                              T* __restrict__ lam_out, long long k, const Cmp& c, const Geo& g,
-                                              const Bc& bc, T omega, double* __restrict__ grad_acc)
+                                              T* __restrict__ lam_out, long long k, const Cmp& c,
+                                              const BCmpInst* __restrict__ Ip, const Bc& tmpl, T omega,
+                                              double* __restrict__ grad_acc)
 {
     using L = Lattice<Q>;
     int32_t code[Q];
-    if (load_codes<Q>(code, c, k)) return adjoint_node_eq6<Q, T, T0>(gprev, lam_in, lam_out, k, c, g, bc, omega, grad_acc);
+    if (load_codes<Q>(code, c, k))
+        return adjoint_node_eq6<Q, T, T0>(gprev, lam_in, lam_out, k, c, Ip, tmpl, omega, grad_acc);
     // Interior node: every load of f^t and of the gathered lambda depends
     // only on the table, so all 2 Q are in flight together.
     const size_t NF = (size_t)c.nf;
@@ -509,7 +508,7 @@ __device__ __forceinline__ T adjoint_cmp_node(const T* __restrict__ gprev, const
     T drho, rho, u[3];
     moments<Q, T>(f, drho, rho, u);
     const T G[3] = {T(0), T(0), T(0)};
-    return adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF, bc);
+    return adjoint_collision<Q, T>(f, mu, drho, rho, u, G, omega, lam_out, k, NF, tmpl);
 }
 
 // One FP64 partial per warp (its sum in T), accumulated in place across time
@@ -523,20 +522,6 @@ __device__ __forceinline__ void add_warp_partial(T dom, bool live, long long k, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) dw += __shfl_xor_sync(0xffffffffu, dw, o);
     if ((threadIdx.x & 31) == 0 && live) partial[k >> 5] += (double)dw;
-}
-
-template <int Q, typename T, bool T0>
-__global__ void __launch_bounds__(kCmpThreads, 4)
-    k_adjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c, Geo g,
-                  Bc bc, const double* __restrict__ tau, double* __restrict__ grad_acc,
-                  double* __restrict__ partial)
-{
-    pdl_enter();
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const T omega = T(1) / T(*tau);  // in T: FP64 arithmetic is slow on this part
-    T dom = T(0);
-    if (k < c.nf) dom = adjoint_cmp_node<Q, T, T0>(gprev, lam_in, lam_out, k, c, g, bc, omega, grad_acc);
-    add_warp_partial<T>(dom, k < c.nf, k, partial);
 }
 
 // Reverse of the extrapolated Eq. 6 velocity in the compact layout: the
@@ -584,71 +569,117 @@ __global__ void __launch_bounds__(kCmpThreads)
     }
 }
 
-// ------------------------------------------------- batches, packed layout
+// CTAs of `kernel` that fit on the GPU at once (the grid of a grid-stride launch).
+template <class K>
+unsigned resident_ctas(K kernel)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCmpThreads, 0);
+    return (unsigned)(std::max(per_sm, 1) * std::max(sms, 1));
+}
+
+// --------------------------------------------- the kernels, lattices and batches
+//
+// The kernels below serve a single lattice and a packed batch alike.  A
+// block's nodes belong to one instance (blk_inst[block]; a single lattice
+// passes no block table and is instance 0), whose entry gives its sizes, the
+// offsets of its inlet data and dense arrays, and its tau.  A single lattice
+// is a pack of one, so a batch instance gets bit for bit what a single plan
+// computes: the same kernels run the same per-node code.
 
 static_assert(kBatchCmpAlign == kCmpThreads, "one thread block per aligned node range of a batch instance");
 
-// The per-instance boundary data of a batch block (batches run BGK with the
-// node-velocity Eq. 6).
-__device__ __forceinline__ Bc batch_bc(const BCmpInst& I, const double* rho_in, double rho_out, uint32_t* status)
-{
-    Bc bc;
-    bc.rho_in = rho_in + I.in_off;
-    bc.profile = I.n_in > 1 ? 1 : 0;
-    bc.rho_out = rho_out;
-    bc.status = status;
-    return bc;
-}
-
-// One step over a packed batch: the block's instance gives the sizes, tau,
-// the inlet densities and (DIN / DOUT) the offset of its dense arrays; the
-// node update is step_cmp_node, so every instance gets bit for bit what a
-// single compact plan computes.
+// One step.  MODE: stream-collide, collide-only or stream-only (step.cu);
+// DIN / DOUT: the input / output is the instance's dense [Q][N] array.
+// Padding nodes of a batch carry bounce-back codes in every direction and
+// start at zero (the rest state), so they stay exactly zero: they run through
+// the interior path like any node, and only a dense read or write needs
+// them skipped.
 template <int Q, typename T, int MODE, bool DIN, bool DOUT>
 __global__ void __launch_bounds__(kCmpThreads, 4)
-    k_bstep_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c, const BCmpInst* __restrict__ insts,
-                const int* __restrict__ blk_inst, const double* __restrict__ rho_in, const double* __restrict__ tau,
-                double rho_out, uint32_t* status)
+    k_step_cmp(const T* __restrict__ src, T* __restrict__ dst, Cmp c, const BCmpInst* __restrict__ insts,
+               const int* __restrict__ blk_inst, Bc tmpl, const double* __restrict__ tau)
 {
     pdl_enter();
-    const int i = blk_inst[blockIdx.x];
-    const BCmpInst I = insts[i];
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= I.k0 + I.nf) return;  // padding of the instance's last block
-    const Bc bc = batch_bc(I, rho_in, rho_out, status);
-    const T omega = T(1) / T(tau[i]);
-    step_cmp_node<Q, T, MODE, DIN, DOUT>(DIN ? src + I.f_off : src, DOUT ? dst + I.f_off : dst, k, c, I.g, bc, omega);
+    if (k >= c.nf) return;
+    const int i = block_instance(blk_inst, k);
+    const BCmpInst* Ip = insts + i;
+    if ((DIN || DOUT) && k >= Ip->k0 + Ip->nf) return;
+    const T omega = T(1) / T(tau[i]);  // in T: FP64 arithmetic is slow on this part
+    step_cmp_node<Q, T, MODE, DIN, DOUT>(src, dst, k, c, Ip, tmpl, omega);
 }
 
-// One adjoint step over a packed batch (adjoint_cmp_node); the warp partials
-// of instance i occupy slots [k0 / 32, (k0 + nf + 31) / 32).
+// Grid-stride form of the interior stream-collide step: a thread walks the
+// nodes k, k + stride, ... and loads the table entries of its next node
+// before the populations of the current one, so the table latency of node
+// k + stride overlaps the population loads of node k.  The nodes of a block
+// stay in one kCmpThreads-aligned range per iteration, so its instance is
+// uniform across the block (padding nodes of a batch run like any node, see
+// k_step_cmp).  Compact indices fit in 32 bits (checked when the tables are
+// built).
+template <int Q, typename T, int MINB>
+__global__ void __launch_bounds__(kCmpThreads, MINB)
+    k_step_cmp_gs(const T* __restrict__ src, T* __restrict__ dst, Cmp c, const BCmpInst* __restrict__ insts,
+                  const int* __restrict__ blk_inst, Bc tmpl, const double* __restrict__ tau)
+{
+    pdl_enter();
+    const int nf = (int)c.nf, stride = (int)(gridDim.x * blockDim.x);
+    int k = (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    int32_t nxt[Q];
+    bool bnd_next = k < nf ? load_codes<Q>(nxt, c, k) : false;
+    int cur = -1;
+    T omega = T(0);
+    for (; k < nf; k += stride) {
+        const bool bnd = bnd_next;
+        T v[Q];
+        if (!bnd) pull_cmp<Q, T>(v, src, k, c.nf, nxt, false, c, insts->g, tmpl);  // population loads first
+        if (k + stride < nf) bnd_next = load_codes<Q>(nxt, c, k + stride);         // then the next node's table
+        const int i = block_instance(blk_inst, k);
+        if (i != cur) {
+            cur = i;
+            omega = T(1) / T(tau[i]);
+        }
+        if (bnd) {
+            step_node_eq6<Q, T, kStreamCollide, false>(src, dst, k, c, insts + i, tmpl, omega);
+            continue;
+        }
+        collide_any<Q, T>(v, omega, tmpl);
+        store_node<Q, T, false>(dst, v, k, c, insts->g);
+    }
+}
+
+// One adjoint step; the warp partials of an instance occupy slots
+// [k0 / 32, (k0 + nf + 31) / 32).  Padding nodes of a batch (see k_step_cmp;
+// lambda's padding starts at zero too) stay zero and add exactly 0 to the
+// dL/domega sum.
 template <int Q, typename T, bool T0>
 __global__ void __launch_bounds__(kCmpThreads, 4)
-    k_badjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c,
-                   const BCmpInst* __restrict__ insts, const int* __restrict__ blk_inst,
-                   const double* __restrict__ rho_in, const double* __restrict__ tau, double rho_out,
-                   uint32_t* status, double* __restrict__ grad_acc, double* __restrict__ partial)
+    k_adjoint_cmp(const T* __restrict__ gprev, const T* __restrict__ lam_in, T* __restrict__ lam_out, Cmp c,
+                  const BCmpInst* __restrict__ insts, const int* __restrict__ blk_inst, Bc tmpl,
+                  const double* __restrict__ tau, double* __restrict__ grad_acc, double* __restrict__ partial)
 {
     pdl_enter();
-    const int i = blk_inst[blockIdx.x];
-    const BCmpInst I = insts[i];
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = k < I.k0 + I.nf;
-    const Bc bc = batch_bc(I, rho_in, rho_out, status);
-    const T omega = T(1) / T(tau[i]);
     T dom = T(0);
-    if (live) dom = adjoint_cmp_node<Q, T, T0>(gprev, lam_in, lam_out, k, c, I.g, bc, omega, grad_acc + I.acc_off);
-    add_warp_partial<T>(dom, live, k, partial);
+    if (k < c.nf) {
+        const int i = block_instance(blk_inst, k);
+        const T omega = T(1) / T(tau[i]);  // in T: FP64 arithmetic is slow on this part
+        dom = adjoint_cmp_node<Q, T, T0>(gprev, lam_in, lam_out, k, c, insts + i, tmpl, omega, grad_acc);
+    }
+    add_warp_partial<T>(dom, k < c.nf, k, partial);
 }
 
-// The caller's packed dense arrays -> the packed compact state.
+// The caller's dense arrays (packed, for a batch) -> the compact state.
 template <typename T>
 __global__ void __launch_bounds__(kCmpThreads)
-    k_bgather_cmp(const T* __restrict__ dense, T* __restrict__ cmp, Cmp c, const BCmpInst* __restrict__ insts,
-                  const int* __restrict__ blk_inst, int q)
+    k_cmp_gather(const T* __restrict__ dense, T* __restrict__ cmp, Cmp c, const BCmpInst* __restrict__ insts,
+                 const int* __restrict__ blk_inst, int q)
 {
-    const BCmpInst I = insts[blk_inst[blockIdx.x]];
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const BCmpInst I = insts[block_instance(blk_inst, k)];
     if (k >= I.k0 + I.nf) return;
     const long long n = c.idx[k];
     for (int d = 0; d < q; ++d) cmp[(long long)d * c.nf + k] = dense[I.f_off + (long long)d * I.g.N + n];
@@ -669,120 +700,125 @@ __global__ void __launch_bounds__(256) k_bpack_cmp(const int32_t* __restrict__ i
     }
 }
 
-template <int Q, typename T>
-void launch_bstep(const BCmpArgs& a, int mode, const void* src, void* dst, bool dout, const double* rho_in,
-                  const double* tau, double rho_out, cudaStream_t s)
-{
-    const T* x = static_cast<const T*>(src);
-    T* y = static_cast<T*>(dst);
-    const dim3 grid(a.n_blocks), block(kCmpThreads);
-    if (mode == kStreamCollide)
-        launch_k(a.pdl, k_bstep_cmp<Q, T, kStreamCollide, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
-                 a.blk_inst, rho_in, tau, rho_out, a.status);
-    else if (mode == kCollideOnly)
-        launch_k(a.pdl, k_bstep_cmp<Q, T, kCollideOnly, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
-                 a.blk_inst, rho_in, tau, rho_out, a.status);
-    else if (dout)
-        launch_k(a.pdl, k_bstep_cmp<Q, T, kStreamOnly, false, true>, grid, block, 0, s, x, y, a.c, a.insts,
-                 a.blk_inst, rho_in, tau, rho_out, a.status);
-    else
-        launch_k(a.pdl, k_bstep_cmp<Q, T, kStreamOnly, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
-                 a.blk_inst, rho_in, tau, rho_out, a.status);
-}
-
-template <int Q, typename T>
-void launch_badjoint(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out,
-                     const double* rho_in, const double* tau, double rho_out, double* grad_acc, double* partial,
-                     cudaStream_t s)
-{
-    const T* gp = static_cast<const T*>(gprev);
-    const T* li = static_cast<const T*>(lam_in);
-    T* lo = static_cast<T*>(lam_out);
-    const dim3 grid(a.n_blocks), block(kCmpThreads);
-    if (t0)
-        launch_k(a.pdl, k_badjoint_cmp<Q, T, true>, grid, block, 0, s, gp, li, lo, a.c, a.insts, a.blk_inst, rho_in,
-                 tau, rho_out, a.status, grad_acc, partial);
-    else
-        launch_k(a.pdl, k_badjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, a.c, a.insts, a.blk_inst, rho_in,
-                 tau, rho_out, a.status, grad_acc, partial);
-}
-
-// CTAs of `kernel` that fit on the GPU at once (the grid of a grid-stride launch).
-template <class K>
-unsigned resident_ctas(K kernel)
-{
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kCmpThreads, 0);
-    return (unsigned)(std::max(per_sm, 1) * std::max(sms, 1));
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kCmpThreads) k_cmp_gather(const T* __restrict__ dense, T* __restrict__ cmp, Cmp c,
-                                                            long long N, int q)
-{
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= c.nf) return;
-    const long long n = c.idx[k];
-    for (int i = 0; i < q; ++i) cmp[(long long)i * c.nf + k] = dense[(long long)i * N + n];
-}
-
 unsigned cmp_grid(long long nf) { return (unsigned)((nf + kCmpThreads - 1) / kCmpThreads); }
+
+// The launch of a single lattice: a pack of one (no block table).
+BCmpArgs single_args(const PlanInfo& p, uint32_t* status)
+{
+    BCmpArgs a = {};
+    a.c = p.cmp;
+    a.insts = p.cmp_inst;
+    a.blk_inst = nullptr;
+    a.n_blocks = cmp_grid(p.cmp.nf);
+    a.q = p.q;
+    a.prec = p.prec;
+    a.pdl = p.pdl;
+    a.status = status;
+    return a;
+}
 
 // The sweeps use: stream-collide compact -> compact; collide-only from a
 // dense or compact state into compact; stream-only into compact or into the
 // caller's dense array.
 template <int Q, typename T>
-void launch_step(const PlanInfo& p, int mode, const void* src, void* dst, bool din, bool dout, const Bc& bc,
+void launch_step(const BCmpArgs& a, int mode, const void* src, void* dst, bool din, bool dout, const Bc& tmpl,
                  const double* tau, cudaStream_t s)
 {
-    const T* a = static_cast<const T*>(src);
-    T* b = static_cast<T*>(dst);
-    const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
+    const T* x = static_cast<const T*>(src);
+    T* y = static_cast<T*>(dst);
+    const dim3 grid(a.n_blocks), block(kCmpThreads);
     // D2Q9 FP32: the grid-stride form with table prefetch (measured faster);
     // D3Q19 and FP64 keep one node per thread (the prefetched table spills)
     if constexpr (Q == 9 && std::is_same<T, float>::value) {
         if (mode == kStreamCollide) {
             static const unsigned resident = resident_ctas(k_step_cmp_gs<Q, T, 3>);
-            launch_k(p.pdl, k_step_cmp_gs<Q, T, 3>, dim3(std::min<unsigned>(resident, grid.x)), block, 0, s, a, b,
-                     p.cmp, p.geo, bc, tau);
+            launch_k(a.pdl, k_step_cmp_gs<Q, T, 3>, dim3(std::min<unsigned>(resident, grid.x)), block, 0, s, x, y, a.c,
+                     a.insts, a.blk_inst, tmpl, tau);
             return;
         }
     }
     if (mode == kStreamCollide)
-        launch_k(p.pdl, k_step_cmp<Q, T, kStreamCollide, false, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc,
-                 tau);
+        launch_k(a.pdl, k_step_cmp<Q, T, kStreamCollide, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, tmpl, tau);
     else if (mode == kCollideOnly && din)
-        launch_k(p.pdl, k_step_cmp<Q, T, kCollideOnly, true, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc, tau);
+        launch_k(a.pdl, k_step_cmp<Q, T, kCollideOnly, true, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, tmpl, tau);
     else if (mode == kCollideOnly)
-        launch_k(p.pdl, k_step_cmp<Q, T, kCollideOnly, false, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc,
-                 tau);
+        launch_k(a.pdl, k_step_cmp<Q, T, kCollideOnly, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, tmpl, tau);
     else if (dout)
-        launch_k(p.pdl, k_step_cmp<Q, T, kStreamOnly, false, true>, grid, block, 0, s, a, b, p.cmp, p.geo, bc, tau);
+        launch_k(a.pdl, k_step_cmp<Q, T, kStreamOnly, false, true>, grid, block, 0, s, x, y, a.c, a.insts, a.blk_inst,
+                 tmpl, tau);
     else
-        launch_k(p.pdl, k_step_cmp<Q, T, kStreamOnly, false, false>, grid, block, 0, s, a, b, p.cmp, p.geo, bc, tau);
+        launch_k(a.pdl, k_step_cmp<Q, T, kStreamOnly, false, false>, grid, block, 0, s, x, y, a.c, a.insts,
+                 a.blk_inst, tmpl, tau);
 }
 
 template <int Q, typename T>
-void launch_adjoint(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
+void launch_adjoint(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& tmpl,
                     const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
     const T* gp = static_cast<const T*>(gprev);
     const T* li = static_cast<const T*>(lam_in);
     T* lo = static_cast<T*>(lam_out);
-    const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
+    const dim3 grid(a.n_blocks), block(kCmpThreads);
     if (t0)
-        launch_k(p.pdl, k_adjoint_cmp<Q, T, true>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
-                 partial);
+        launch_k(a.pdl, k_adjoint_cmp<Q, T, true>, grid, block, 0, s, gp, li, lo, a.c, a.insts, a.blk_inst, tmpl, tau,
+                 grad_acc, partial);
     else
-        launch_k(p.pdl, k_adjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, p.cmp, p.geo, bc, tau, grad_acc,
-                 partial);
-    if (bc.uw_extrap && !t0) {  // at t = 0 the fluid is at rest and the pass adds nothing
-        const long long rows = (long long)p.geo.ny * p.geo.nz;
-        launch_k(p.pdl, k_adjoint_uw_cmp<Q, T>, dim3((unsigned)((rows + kCmpThreads - 1) / kCmpThreads)), block, 0, s,
-                 gp, li, lo, p.cmp, p.cmp_map, p.geo, bc, grad_acc);
-    }
+        launch_k(a.pdl, k_adjoint_cmp<Q, T, false>, grid, block, 0, s, gp, li, lo, a.c, a.insts, a.blk_inst, tmpl,
+                 tau, grad_acc, partial);
+}
+
+lbm_status step_any(const BCmpArgs& a, int mode, const void* src, void* dst, bool din, bool dout, const Bc& tmpl,
+                    const double* tau, cudaStream_t s)
+{
+    if (a.n_blocks == 0) return LBM_OK;
+    if (a.q == 9 && a.prec == 4) launch_step<9, float>(a, mode, src, dst, din, dout, tmpl, tau, s);
+    else if (a.q == 9 && a.prec == 8) launch_step<9, double>(a, mode, src, dst, din, dout, tmpl, tau, s);
+    else if (a.q == 19 && a.prec == 4) launch_step<19, float>(a, mode, src, dst, din, dout, tmpl, tau, s);
+    else if (a.q == 19 && a.prec == 8) launch_step<19, double>(a, mode, src, dst, din, dout, tmpl, tau, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status adjoint_any(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out,
+                       const Bc& tmpl, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
+{
+    if (a.n_blocks == 0) return LBM_OK;
+    if (a.q == 9 && a.prec == 4) launch_adjoint<9, float>(a, t0, gprev, lam_in, lam_out, tmpl, tau, grad_acc, partial, s);
+    else if (a.q == 9 && a.prec == 8)
+        launch_adjoint<9, double>(a, t0, gprev, lam_in, lam_out, tmpl, tau, grad_acc, partial, s);
+    else if (a.q == 19 && a.prec == 4)
+        launch_adjoint<19, float>(a, t0, gprev, lam_in, lam_out, tmpl, tau, grad_acc, partial, s);
+    else if (a.q == 19 && a.prec == 8)
+        launch_adjoint<19, double>(a, t0, gprev, lam_in, lam_out, tmpl, tau, grad_acc, partial, s);
+    else return LBM_ERR_UNSUPPORTED;
+    return cuda_status(cudaGetLastError());
+}
+
+lbm_status gather_any(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s)
+{
+    if (a.n_blocks == 0) return LBM_OK;
+    const dim3 grid(a.n_blocks), block(kCmpThreads);
+    if (a.prec == 4)
+        k_cmp_gather<float><<<grid, block, 0, s>>>(static_cast<const float*>(dense), static_cast<float*>(compact), a.c,
+                                                   a.insts, a.blk_inst, a.q);
+    else
+        k_cmp_gather<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
+                                                    a.c, a.insts, a.blk_inst, a.q);
+    return cuda_status(cudaGetLastError());
+}
+
+// The call's options on a batch: node-velocity Eq. 6 and BGK.
+Bc batch_tmpl(const double* rho_in, double rho_out, uint32_t* status)
+{
+    Bc bc;
+    bc.rho_in = rho_in;
+    bc.profile = 0;
+    bc.rho_out = rho_out;
+    bc.status = status;
+    return bc;
 }
 
 }  // namespace
@@ -790,10 +826,11 @@ void launch_adjoint(const PlanInfo& p, int t0, const void* gprev, const void* la
 size_t compact_table_bytes(const PlanInfo& p, long long nf) { return table_layout(p, nf).bytes; }
 
 lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, const int32_t** cmap_out,
-                         cudaStream_t s)
+                         const BCmpInst** inst_out, cudaStream_t s)
 {
     const TableLayout t = table_layout(p, nf);
     unsigned char* base = static_cast<unsigned char*>(tables);
+    BCmpInst* inst = reinterpret_cast<BCmpInst*>(base + t.inst);
     int32_t* idx = reinterpret_cast<int32_t*>(base + t.idx);
     int32_t* nbr = reinterpret_cast<int32_t*>(base + t.nbr);
     int32_t* cmap = reinterpret_cast<int32_t*>(base + t.cmap);
@@ -801,11 +838,20 @@ lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out
     long long* total = reinterpret_cast<long long*>(base + t.total_slot);
     const long long N = p.geo.N;
     const long long nblk = (N + kScanNodes - 1) / kScanNodes;
+    BCmpInst one = {};
+    one.g = p.geo;
+    one.k0 = 0;
+    one.nf = nf;
+    one.f_off = 0;
+    one.in_off = 0;
+    one.acc_off = 0;
+    one.n_in = p.n_in;
+    if (cudaMemcpyAsync(inst, &one, sizeof(one), cudaMemcpyHostToDevice, s) != cudaSuccess) return LBM_ERR_CUDA;
     k_cmp_count<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, blk);
     k_cmp_scan<<<1, 1024, 0, s>>>(blk, nblk, total);
     long long got = -1;
     if (cudaMemcpyAsync(&got, total, sizeof(got), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ERR_CUDA;  // also ends the copy of `one`
     if (got != nf) return LBM_ERR_INVALID_ARG;
     k_cmp_index<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, blk, cmap, idx, nf);
     if (nf > 0) {
@@ -818,6 +864,7 @@ lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out
     out->idx = idx;
     out->nbr = nbr;
     *cmap_out = cmap;
+    if (inst_out) *inst_out = inst;
     return LBM_OK;
 }
 
@@ -825,83 +872,60 @@ lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* d
                            const Bc& bc, const double* tau, cudaStream_t s)
 {
     if (p.cmp.nf == 0) return LBM_OK;
-    if (p.q == 9 && p.prec == 4) launch_step<9, float>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
-    else if (p.q == 9 && p.prec == 8) launch_step<9, double>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
-    else if (p.q == 19 && p.prec == 4) launch_step<19, float>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
-    else if (p.q == 19 && p.prec == 8) launch_step<19, double>(p, mode, src, dst, dense_in, dense_out, bc, tau, s);
-    else return LBM_ERR_UNSUPPORTED;
-    return cuda_status(cudaGetLastError());
+    return step_any(single_args(p, bc.status), mode, src, dst, dense_in, dense_out, bc, tau, s);
 }
 
 lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,
                               const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s)
 {
     if (p.cmp.nf == 0) return LBM_OK;
-    if (p.q == 9 && p.prec == 4) launch_adjoint<9, float>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
-    else if (p.q == 9 && p.prec == 8)
-        launch_adjoint<9, double>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
-    else if (p.q == 19 && p.prec == 4)
-        launch_adjoint<19, float>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
-    else if (p.q == 19 && p.prec == 8)
-        launch_adjoint<19, double>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
-    else return LBM_ERR_UNSUPPORTED;
+    LBM_CMP_TRY(adjoint_any(single_args(p, bc.status), t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s));
+    if (bc.uw_extrap && !t0) {  // at t = 0 the fluid is at rest and the pass adds nothing
+        const long long rows = (long long)p.geo.ny * p.geo.nz;
+        const dim3 grid((unsigned)((rows + kCmpThreads - 1) / kCmpThreads)), block(kCmpThreads);
+        if (p.q == 9 && p.prec == 4)
+            launch_k(p.pdl, k_adjoint_uw_cmp<9, float>, grid, block, 0, s, static_cast<const float*>(gprev),
+                     static_cast<const float*>(lam_in), static_cast<float*>(lam_out), p.cmp, p.cmp_map, p.geo, bc,
+                     grad_acc);
+        else if (p.q == 9)
+            launch_k(p.pdl, k_adjoint_uw_cmp<9, double>, grid, block, 0, s, static_cast<const double*>(gprev),
+                     static_cast<const double*>(lam_in), static_cast<double*>(lam_out), p.cmp, p.cmp_map, p.geo, bc,
+                     grad_acc);
+        else if (p.prec == 4)
+            launch_k(p.pdl, k_adjoint_uw_cmp<19, float>, grid, block, 0, s, static_cast<const float*>(gprev),
+                     static_cast<const float*>(lam_in), static_cast<float*>(lam_out), p.cmp, p.cmp_map, p.geo, bc,
+                     grad_acc);
+        else
+            launch_k(p.pdl, k_adjoint_uw_cmp<19, double>, grid, block, 0, s, static_cast<const double*>(gprev),
+                     static_cast<const double*>(lam_in), static_cast<double*>(lam_out), p.cmp, p.cmp_map, p.geo, bc,
+                     grad_acc);
+    }
     return cuda_status(cudaGetLastError());
 }
 
 lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s)
 {
     if (p.cmp.nf == 0) return LBM_OK;
-    const dim3 grid(cmp_grid(p.cmp.nf)), block(kCmpThreads);
-    if (p.prec == 4)
-        k_cmp_gather<float><<<grid, block, 0, s>>>(static_cast<const float*>(dense), static_cast<float*>(compact),
-                                                   p.cmp, p.geo.N, p.q);
-    else
-        k_cmp_gather<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
-                                                    p.cmp, p.geo.N, p.q);
-    return cuda_status(cudaGetLastError());
+    return gather_any(single_args(p, nullptr), dense, compact, s);
 }
 
 lbm_status bstep_launch_cmp(const BCmpArgs& a, int mode, const void* src, void* dst, bool dense_out,
                             const double* rho_in, const double* tau, double rho_out, cudaStream_t s)
 {
-    if (a.n_blocks == 0) return LBM_OK;
-    if (a.q == 9 && a.prec == 4) launch_bstep<9, float>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
-    else if (a.q == 9 && a.prec == 8) launch_bstep<9, double>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
-    else if (a.q == 19 && a.prec == 4) launch_bstep<19, float>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
-    else if (a.q == 19 && a.prec == 8)
-        launch_bstep<19, double>(a, mode, src, dst, dense_out, rho_in, tau, rho_out, s);
-    else return LBM_ERR_UNSUPPORTED;
-    return cuda_status(cudaGetLastError());
+    return step_any(a, mode, src, dst, false, dense_out, batch_tmpl(rho_in, rho_out, a.status), tau, s);
 }
 
 lbm_status badjoint_launch_cmp(const BCmpArgs& a, int t0, const void* gprev, const void* lam_in, void* lam_out,
                                const double* rho_in, const double* tau, double rho_out, double* grad_acc,
                                double* partial, cudaStream_t s)
 {
-    if (a.n_blocks == 0) return LBM_OK;
-    if (a.q == 9 && a.prec == 4)
-        launch_badjoint<9, float>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
-    else if (a.q == 9 && a.prec == 8)
-        launch_badjoint<9, double>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
-    else if (a.q == 19 && a.prec == 4)
-        launch_badjoint<19, float>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
-    else if (a.q == 19 && a.prec == 8)
-        launch_badjoint<19, double>(a, t0, gprev, lam_in, lam_out, rho_in, tau, rho_out, grad_acc, partial, s);
-    else return LBM_ERR_UNSUPPORTED;
-    return cuda_status(cudaGetLastError());
+    return adjoint_any(a, t0, gprev, lam_in, lam_out, batch_tmpl(rho_in, rho_out, a.status), tau, grad_acc, partial,
+                       s);
 }
 
 lbm_status bgather_launch_cmp(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s)
 {
-    if (a.n_blocks == 0) return LBM_OK;
-    const dim3 grid(a.n_blocks), block(kCmpThreads);
-    if (a.prec == 4)
-        k_bgather_cmp<float><<<grid, block, 0, s>>>(static_cast<const float*>(dense), static_cast<float*>(compact), a.c,
-                                                    a.insts, a.blk_inst, a.q);
-    else
-        k_bgather_cmp<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
-                                                     a.c, a.insts, a.blk_inst, a.q);
-    return cuda_status(cudaGetLastError());
+    return gather_any(a, dense, compact, s);
 }
 
 lbm_status bpack_launch_cmp(const Cmp& local, int q, long long k0, long long nfp, int32_t* idx, int32_t* nbr,
