@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--no-invert", action="store_true", help="skip the time-to-1e-3 inversion leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--no-batch-invert", action="store_true", help="skip the batched time-to-1e-3 leg")
+    ap.add_argument("--batch-invert-instances", type=int, default=8,
+                    help="instances of the batched time-to-1e-3 leg (the first of the 64-instance recipe)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 3D joint (head, tau) inversion leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser leg")
     ap.add_argument("--no-wake", action="store_true", help="skip the cylinder-wake viscosity inversion leg")
@@ -296,6 +299,8 @@ def run_native(args):
 
     inversion = None if args.no_invert else time_to_target(P, args.invert_time_limit)
     batched = None if args.no_batch else batch_leg(device, args.batch_instances, rank)
+    batched_inv = None if args.no_batch_invert else batch_invert_leg(device, args.batch_invert_instances, rank,
+                                                                      args.invert_time_limit)
     c3 = None if args.no_c3 else c3_leg(device, args.invert_time_limit)
     learned = None if args.no_learned else learned_init_leg(device, args.learned_solves, args.learned_epochs,
                                                             args.learned_eval, args.invert_time_limit / 2)
@@ -331,6 +336,7 @@ def run_native(args):
             "inversion_progress": {"adam_steps": P["t"], "rel_err_delta": rel_err},
             "time_to_1e-3": inversion,
             "batched": batched,
+            "batched_time_to_1e-3": batched_inv,
             "joint_inversion_3d": c3,
             "learned_initialiser": learned,
             "viscosity_inversion_wake": wake,
@@ -520,8 +526,12 @@ def learned_init_leg(device, n_train, epochs, n_eval, time_limit):
     t_train = time.perf_counter() - t0
     samples = epochs * (n_train // batch) * batch
     flops = 3 * unet_flops_per_sample(base, ny, nx) * samples  # forward + two backward products
-    rows = N.evaluate(net, [5000 + 20000 + i for i in range(n_eval)], nx=nx, ny=ny, steps=T, max_evals=600,
-                      time_limit=time_limit)
+    seeds = [5000 + 20000 + i for i in range(n_eval)]
+    rows = N.evaluate(net, seeds, nx=nx, ny=ny, steps=T, max_evals=600, time_limit=time_limit)
+    # the same held-out inversions, all in one packed batch started from the network's guesses: the
+    # learned initialiser with batching against the plain single-instance inversion from delta = 0
+    batched = N.evaluate_batched(net, seeds, nx=nx, ny=ny, steps=T, max_evals=600, time_limit=time_limit)
+    zero_single = float(np.mean([r["zero"]["seconds"] for r in rows]))
     mean = lambda key, f: float(np.mean([f(r[key]) for r in rows]))
     return {"workload": f"U-Net base {base}, input 2 velocity channels + mask at {nx}x{ny}, BF16 weights/activations, "
                         f"FP32 accumulation (mma.sync tensor cores); {n_train} training solves (D2Q9 FP32, T={T}, "
@@ -536,17 +546,23 @@ def learned_init_leg(device, n_train, epochs, n_eval, time_limit):
             "lbfgs_from_zero": {"gradient_evaluations": mean("zero", lambda r: r["gradient_evaluations"]),
                                 "seconds": mean("zero", lambda r: r["seconds"]),
                                 "converged": all(r["zero"]["converged"] for r in rows)},
-            "held_out": rows}
+            "held_out": rows,
+            "batched_from_unet": batched,
+            "seconds_per_instance_unet_batched": batched["seconds_per_instance"],
+            "seconds_per_instance_zero_single": round(zero_single, 3),
+            "speedup_unet_batched_vs_zero_single": round(zero_single / max(batched["seconds_per_instance"], 1e-9), 2)}
 
 
-def batch_leg(device, count, rank, steps=2, layout="dense"):
+def batch_leg(device, count, rank, steps=2, layout=None):
     """The batched inversions: `count` independent D2Q9 FP32 lattices with
     nx = 32 U{4..32}, ny = nx / 2, seeded disks (porosity U[0.5, 0.7]),
     T = 5000, one gradient evaluation (forward + loss + checkpointed adjoint)
-    of every instance per batch step, all instances in shared kernels."""
+    of every instance per batch step, all instances in shared kernels.  The
+    layout (dense register kernels or packed fluid-only) is the batch
+    autotuner's unless given."""
     import torch
 
-    from paper_2310_00810_gb300 import lbm
+    from paper_2310_00810_gb300 import autotune, lbm
     from paper_2310_00810_gb300 import workloads as W
 
     T = 5000
@@ -555,14 +571,17 @@ def batch_leg(device, count, rank, steps=2, layout="dense"):
     geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=sd, r_min=6, r_max=12, target_porosity=por)
              for nx, ny, por, sd in spec]
     b = lbm.Batch(9, sizes, precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms,
-                  device=device, layout=layout)
+                  device=device)
+    tuned = autotune.tune_batch(b) if layout is None else None
+    if layout is not None:
+        b.set_layout(layout)
     rho_in = b.new_inlet()
     for i, (nx, ny, _, sd) in enumerate(spec):
         b.view_inlet(rho_in, i).copy_(torch.as_tensor(1.0 + W.inlet_profile(ny, seed=2000 + sd), device=device))
     tau = torch.full((b.n,), 0.8, dtype=torch.float64, device=device)
     f_true = b.forward(rho_in, tau, 1.0)
     torch.cuda.synchronize(device)
-    ut = batch_macroscopic(b, f_true, device)  # observed fields; the evaluation starts from delta = 0
+    ut = b.velocity(f_true)  # observed fields; the evaluation starts from delta = 0
     rho0 = torch.ones_like(rho_in)
     f = b.new_state()
     lam = b.new_state()
@@ -585,29 +604,80 @@ def batch_leg(device, count, rank, steps=2, layout="dense"):
     torch.cuda.synchronize(device)
     sec = e0.elapsed_time(e1) * 1e-3 / steps
     nodes = sum(nx * ny for nx, ny, _ in sizes)
-    return {"instances": b.n, "nodes": nodes, "time_steps": T, "seconds_per_gradient_eval": round(sec, 4),
+    fluid = int(b.info.view(b.n, 4)[:, 3].sum().item())
+    # algorithmic population bytes of one gradient evaluation: forward 2Qs + recompute 2Qs + adjoint 3Qs per
+    # fluid node and time step
+    alg = 7 * 9 * 4 * fluid * T
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm_peak = json.load(open(peaks))["hbm_gbs"] if os.path.exists(peaks) else 6800.0
+    return {"instances": b.n, "nodes": nodes, "fluid_nodes": fluid, "time_steps": T, "layout": b.layout,
+            "tuner": None if tuned is None else {"layout": tuned["layout"], "timings_us": tuned["timings_us"],
+                                                 "cached": tuned.get("cached")},
+            "seconds_per_gradient_eval": round(sec, 4),
             "aggregate_mlups": round(nodes * T / sec / 1e6, 1),
+            "hbm_gbs_algorithmic": round(alg / sec / 1e9, 1), "hbm_frac": round(alg / sec / 1e9 / hbm_peak, 4),
             "gradient_evals_per_s_per_instance": round(1.0 / sec, 3),
             "gradient_evals_per_s_total": round(b.n / sec, 2),
             "sizes": f"nx in [{min(s[0] for s in sizes)}, {max(s[0] for s in sizes)}], ny = nx / 2"}
 
 
-def batch_macroscopic(b, f, device):
-    """Velocity fields of every instance of a batch (per-instance lbm_macroscopic on a bound plan)."""
+def batch_invert_leg(device, count, rank, time_limit, n_single=2):
+    """Time to 1e-3 relative error on the inlet profiles of `count` batched
+    instances (the first `count` of the 64-instance recipe, T = 5000): one
+    L-BFGS per instance in lock step over the autotuned packed batch, against
+    the plain single-instance inversion (autotuned plan, L-BFGS from delta = 0)
+    of `n_single` of the same instances, run one after another."""
     import torch
 
-    from paper_2310_00810_gb300 import lbm
+    from paper_2310_00810_gb300 import autotune, lbm
+    from paper_2310_00810_gb300 import invert as I
+    from paper_2310_00810_gb300 import workloads as W
 
-    ut = b.new_velocity()
+    T = 5000
+    spec = W.batch_sizes(64, seed=replica_seeds(rank)["batch"])[:count]
+    sizes = [(nx, ny, 1) for nx, ny, _, _ in spec]
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=sd, r_min=6, r_max=12, target_porosity=por)
+             for nx, ny, por, sd in spec]
+    b = lbm.Batch(9, sizes, precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms,
+                  device=device)
+    tuned = autotune.tune_batch(b)
+    truth = [W.inlet_profile(ny, seed=2000 + sd) for _, ny, _, sd in spec]
+    rho_in = b.new_inlet()
     for i in range(b.n):
-        nx, ny, nz = b.sizes[i]
-        p = lbm.Plan(b.q, nx, ny, nz, b.precision, 1)
-        o = int(b.node_off[i])
-        lbm.lbm_bind_geometry(p, b.link[o:o + nx * ny * nz])
-        u = torch.empty((b.d, ny, nx), dtype=torch.float64, device=device)
-        lbm.lbm_macroscopic(p, b.view_state(f, i).contiguous(), None, u)
-        b.view_velocity(ut, i).copy_(u)
-    return ut
+        b.view_inlet(rho_in, i).copy_(torch.as_tensor(1.0 + truth[i], device=device))
+    tau = torch.full((b.n,), 0.8, dtype=torch.float64, device=device)
+    ut = b.velocity(b.forward(rho_in, tau, 1.0))
+    inv = I.BatchInversion(b, ut, 1.0, 0.8)
+    r = inv.run_lbfgs(truth_delta=truth, tol=1e-3, max_evals=600, time_limit=time_limit)
+    singles = []
+    for i in range(min(n_single, count)):
+        nx, ny, _ = sizes[i]
+        s = lbm.Solver(9, nx, ny, precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometry=geoms[i],
+                       device=device)
+        autotune.tune(s)
+        _, u1 = s.macroscopic(s.forward(torch.as_tensor(1.0 + truth[i], device=device),
+                                        torch.tensor([0.8], dtype=torch.float64, device=device), 1.0))
+        si = I.Inversion(s, u1.contiguous(), 1.0, tau0=0.8)
+        rs = si.run_lbfgs(max_evals=600, tol=1e-3, truth_delta=truth[i], time_limit=time_limit / 2)
+        singles.append({"instance": i, "size": f"{nx}x{ny}", "seconds": round(rs.seconds, 2),
+                        "gradient_evaluations": si.evaluations, "converged": bool(rs.converged),
+                        "batched_evaluations": r["evaluations"][i]})
+        del s, si
+    single_per_instance = float(np.mean([x["seconds"] for x in singles])) if singles else None
+    batched_per_instance = r["seconds"] / b.n
+    out = {"instances": b.n, "time_steps": T, "layout": tuned["layout"], "method": "L-BFGS per instance, lock step",
+           "start": "delta = 0", "sizes": [f"{nx}x{ny}" for nx, ny, _ in sizes],
+           "rounds": r["rounds"], "seconds": round(r["seconds"], 2), "converged": r["converged"],
+           "converged_count": int(sum(1 for x in r["rel_err"] if x is not None and x <= 1e-3)),
+           "evaluations": r["evaluations"], "max_rel_err": max(x for x in r["rel_err"] if x is not None),
+           "seconds_per_instance_batched": round(batched_per_instance, 3),
+           "single_instance": singles, "seconds_per_instance_single": single_per_instance,
+           "speedup_per_instance": (round(single_per_instance / batched_per_instance, 2)
+                                    if single_per_instance else None),
+           "time_limit_s": time_limit}
+    del b, inv
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(P, args, device, barrier, world):

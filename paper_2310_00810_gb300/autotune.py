@@ -11,6 +11,12 @@ keyed by GPU name, Q, precision, lattice size and inlet kind.
 
 Timing uses a short tuning plan bound to the solver's geometry (T_tune time
 steps), with CUDA events around graph-replayed launch sequences.
+
+``tune_batch`` does the same for a batch of lattices (lbm.Batch): it times a
+whole gradient evaluation (forward, loss, checkpointed adjoint) of a short
+copy of the batch (same sizes and geometries, T_tune steps) in the dense
+layout (register kernels over row segments) and in the packed fluid-only
+layout, and keeps the faster.
 """
 from __future__ import annotations
 
@@ -183,3 +189,54 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
 def _apply(solver: lbm.Solver, result: dict) -> None:
     solver.set_layout(result.get("layout", "dense"))
     lbm.lbm_plan_set_kernels(solver.plan, **result["choice"])
+
+
+def _batch_key(b) -> str:
+    import hashlib
+
+    name = torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+    geo = hashlib.sha1(repr((b.sizes, b.geometries)).encode()).hexdigest()[:16]
+    return f"{name}|batch|q{b.q}|p{b.precision}|n{b.n}|{geo}|{b.inlet_kind}"
+
+
+def tune_batch(batch, t_tune: int = 64, repeats: int = 2, cache: str | None = DEFAULT_CACHE, use_cache: bool = True,
+               apply: bool = True) -> dict:
+    """Choose and (by default) apply the faster layout of a batch.  Returns
+    {"layout": ..., "timings_us": {...}, "us_per_time_step": ...}."""
+    key = _batch_key(batch)
+    if use_cache and cache:
+        hit = _load(cache).get(key)
+        if hit:
+            if apply:
+                batch.set_layout(hit["layout"])
+            return dict(hit, cached=True)
+    dev = batch.device
+    tb = lbm.Batch(batch.q, batch.sizes, precision=batch.precision, n_steps=t_tune, ckpt_stride=8,
+                   inlet_kind=batch.inlet_kind, geometries=batch.geometries, device=dev)
+    rho_in = tb.new_inlet().fill_(1.001)
+    tau = torch.full((tb.n,), 0.8, dtype=torch.float64, device=dev)
+    ut = tb.new_velocity()
+    f, lam = tb.new_state(), tb.new_state()
+    loss = torch.zeros(tb.n, dtype=torch.float64, device=dev)
+    g_in, g_tau = tb.new_inlet(), torch.zeros(tb.n, dtype=torch.float64, device=dev)
+
+    def run():
+        tb.forward(rho_in, tau, 1.0, f)
+        tb.loss_grad(f, ut, None, loss, lam)
+        tb.adjoint(rho_in, tau, 1.0, lam, g_in, g_tau)
+
+    timings = {}
+    best, best_t = None, float("inf")
+    for layout in ("dense", "compact"):
+        tb.set_layout(layout)
+        t = _time(run, repeats, tb.stream) / t_tune
+        timings[f"batch:{layout}"] = round(t * 1e6, 3)
+        if t < best_t:
+            best, best_t = layout, t
+    result = {"layout": best, "timings_us": timings, "us_per_time_step": round(best_t * 1e6, 3), "key": key}
+    if cache:
+        _store(cache, key, result)
+    if apply:
+        batch.set_layout(best)
+    tb.close()
+    return dict(result, cached=False)

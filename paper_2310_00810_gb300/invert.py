@@ -20,8 +20,11 @@ rule.  ``truth`` (optional) turns on the relative-error stop used for
 time-to-target measurements: |delta - delta*| / |delta*| on delta = rho_in -
 rho_out, and |nu - nu*| / |nu*| for tau.
 
-Also here: the pure L-BFGS routine ``lbfgs`` (any evaluation function), the
-density-probe and spline-knot variants of the inversion, ``SnapshotSeries``
+Also here: the pure L-BFGS routine ``lbfgs`` (any evaluation function), its
+lock-step form over many independent problems ``lbfgs_lockstep`` and the
+batched inversion ``BatchInversion`` (one batched gradient evaluation serves
+every instance's L-BFGS), the density-probe and spline-knot variants of the
+inversion, ``SnapshotSeries``
 (a loss over several observation times), and host-side recovery helpers:
 ``IterationLog`` (JSON lines), ``Checkpoint`` (exact resume), Adam state
 ``save``/``load`` and ``inject_failures`` (fault injection for tests).
@@ -29,6 +32,7 @@ density-probe and spline-knot variants of the inversion, ``SnapshotSeries``
 from __future__ import annotations
 
 import dataclasses
+import threading
 import time
 
 import numpy as np
@@ -249,6 +253,144 @@ def lbfgs(evaluate, x0, max_evals=400, memory=20, errors=None, done=None, lower=
             break
     return LbfgsResult(x, it, evals, time.perf_counter() - t_start, converged, losses, errs)
 
+
+
+def lbfgs_lockstep(evaluate_batch, x0s, errors=None, done=None, **kw) -> list:
+    """Independent L-BFGS runs (lbfgs, unchanged) over many problems in lock
+    step: every round, each unfinished run has asked for one point, and a
+    single call evaluate_batch({i: x_i}) -> {i: (loss_i, grad_i)} evaluates
+    them all (one batched gradient evaluation of a batch of lattices).  Each
+    run takes exactly the steps it would take alone with the same
+    evaluations.  errors / done: one function per run (or None); the other
+    keyword arguments go to every lbfgs (a time_limit is a shared deadline).
+    Returns one LbfgsResult per problem."""
+    n = len(x0s)
+    cond = threading.Condition()
+    pending: dict = {}
+    answers: dict = {}
+    running = set(range(n))
+    failure: list = []
+    outs: list = [None] * n
+
+    def make_eval(i):
+        def ev(x):
+            with cond:
+                pending[i] = np.array(x, np.float64)
+                cond.notify_all()
+                cond.wait_for(lambda: i in answers or failure)
+                if failure:
+                    raise RuntimeError("batched evaluation failed") from failure[0]
+                return answers.pop(i)
+
+        return ev
+
+    def worker(i):
+        try:
+            outs[i] = lbfgs(make_eval(i), x0s[i], errors=None if errors is None else errors[i],
+                            done=None if done is None else done[i], **kw)
+        except BaseException as e:  # noqa: BLE001 - reported to the coordinator
+            with cond:
+                failure.append(e)
+        finally:
+            with cond:
+                running.discard(i)
+                cond.notify_all()
+
+    threads = [threading.Thread(target=worker, args=(i,), daemon=True) for i in range(n)]
+    for t in threads:
+        t.start()
+    while True:
+        with cond:
+            cond.wait_for(lambda: failure or all(i in pending for i in running))
+            if failure or not running:
+                break
+            req = dict(pending)
+            pending.clear()
+        try:
+            res = evaluate_batch(req)
+        except BaseException as e:  # noqa: BLE001
+            with cond:
+                failure.append(e)
+                cond.notify_all()
+            break
+        with cond:
+            answers.update(res)
+            cond.notify_all()
+    for t in threads:
+        t.join()
+    if failure:
+        raise failure[0]
+    return outs
+
+
+class BatchInversion:
+    """L-BFGS inversions of every instance of a batch (lbm.Batch): the inlet
+    density profile (or constant head) of each instance from its observed
+    velocity field, with tau fixed per instance.  Each instance runs its own
+    lbfgs on the scaled parameters (as Inversion.run_lbfgs), in lock step; a
+    round is one batched forward + loss + checkpointed adjoint of all
+    instances (instances that are done keep their last point)."""
+
+    def __init__(self, batch, u_target, rho_out: float, tau, theta0=None):
+        self.b, self.rho_out = batch, float(rho_out)
+        self.u_target = u_target.contiguous()
+        dev = batch.device
+        self.tau = torch.as_tensor(np.broadcast_to(np.asarray(tau, np.float64), (batch.n,)).copy(), device=dev)
+        self.n_in = [int(batch.view_inlet(batch.new_inlet(), i).numel()) for i in range(batch.n)]
+        self.theta0 = [np.zeros(k) if theta0 is None else np.asarray(theta0[i], np.float64).copy()
+                       for i, k in enumerate(self.n_in)]
+        self.x = [t.copy() for t in self.theta0]
+        self.rho_in = batch.new_inlet()
+        self.f = batch.new_state()
+        self.lam = batch.new_state()
+        self.loss = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+        self.g_in = batch.new_inlet()
+        self.g_tau = torch.zeros(batch.n, dtype=torch.float64, device=dev)
+        self.rounds = 0
+
+    def _evaluate(self, req: dict) -> dict:
+        b = self.b
+        for i, x in req.items():
+            self.x[i] = x
+        rho = np.zeros(int(b.inlet_off[-1]))
+        for i in range(b.n):
+            o = int(b.inlet_off[i])
+            rho[o:o + self.n_in[i]] = self.rho_out + INLET_SCALE * self.x[i]
+        with torch.cuda.stream(b.stream):
+            self.rho_in.copy_(torch.from_numpy(rho), non_blocking=False)
+        b.forward(self.rho_in, self.tau, self.rho_out, self.f)
+        b.loss_grad(self.f, self.u_target, None, self.loss, self.lam)
+        b.adjoint(self.rho_in, self.tau, self.rho_out, self.lam, self.g_in, self.g_tau)
+        b.stream.synchronize()
+        self.rounds += 1
+        L = self.loss.cpu().numpy()
+        g = self.g_in.cpu().numpy()
+        out = {}
+        for i in req:
+            o = int(b.inlet_off[i])
+            out[i] = (float(L[i]), g[o:o + self.n_in[i]] * INLET_SCALE)
+        return out
+
+    def run_lbfgs(self, truth_delta=None, tol: float = 1e-3, max_evals: int = 400, memory: int = 20,
+                  time_limit: float | None = None) -> dict:
+        """Every instance to `tol` relative error on delta (truth_delta: one
+        array per instance) or max_evals / time_limit.  Returns the per-
+        instance results, the rounds (batched evaluations) and the seconds."""
+        n = self.b.n
+        td = [None] * n if truth_delta is None else [np.asarray(t, np.float64) for t in truth_delta]
+        errors = [None if td[i] is None else
+                  (lambda x, t=td[i]: (float(np.linalg.norm(INLET_SCALE * x - t) / np.linalg.norm(t)), None))
+                  for i in range(n)]
+        done = [lambda e: e[0] <= tol] * n
+        torch.cuda.synchronize(self.b.device)
+        t0 = time.perf_counter()
+        res = lbfgs_lockstep(self._evaluate, self.theta0, errors=errors, done=done, max_evals=max_evals,
+                             memory=memory, time_limit=time_limit)
+        secs = time.perf_counter() - t0
+        return {"results": res, "rounds": self.rounds, "seconds": secs,
+                "converged": all(r.converged for r in res),
+                "rel_err": [r.errs[-1][0] if r.errs else None for r in res],
+                "evaluations": [r.evaluations for r in res]}
 
 class Inversion:
     """Adam inversion of the inlet density (constant head or profile) and,

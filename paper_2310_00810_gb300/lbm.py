@@ -579,6 +579,8 @@ class Batch:
         self.link = torch.zeros(nodes, dtype=torch.int32, device=self.device)
         self.porosity = torch.zeros(self.n, dtype=torch.float64, device=self.device)
         self.info = torch.zeros(4 * self.n, dtype=torch.int64, device=self.device)
+        self.geometries = [dict(g) for g in (geometries or [{}] * self.n)]
+        self.ckpt_stride, self.loss_kind, self.loss_norm = ckpt_stride, loss_kind, loss_norm
         geoms = (lbm_geom_desc * self.n)()
         for i, g in enumerate(geometries or [{}] * self.n):
             a = dict(kind=LBM_GEOM_CHANNEL, seed=0, r_min=6, r_max=12, target_porosity=1.0, hydro_q8=256,
@@ -668,6 +670,20 @@ class Batch:
         o = int(self.inlet_off[i])
         n = self.sizes[i][1] * self.sizes[i][2] if self.inlet_kind == LBM_INLET_PROFILE else 1
         return t[o:o + n]
+
+    def velocity(self, f):
+        """Packed velocity fields (Eq. 1-2, solids 0) of a packed state: per
+        instance, lbm_macroscopic on a plan bound to its link words."""
+        u = self.new_velocity()
+        for i in range(self.n):
+            nx, ny, nz = self.sizes[i]
+            p = Plan(self.q, nx, ny, nz, self.precision, 1)
+            o = int(self.node_off[i])
+            lbm_bind_geometry(p, self.link[o:o + nx * ny * nz])
+            ui = torch.empty((self.d, *self.shape(i)), dtype=torch.float64, device=self.device)
+            self._run(lambda: lbm_macroscopic(p, self.view_state(f, i).contiguous(), None, ui, self.stream))
+            self.view_velocity(u, i).copy_(ui)
+        return u
 
     def forward(self, rho_in, tau, rho_out, f=None):
         f = self.new_state() if f is None else f

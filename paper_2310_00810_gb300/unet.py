@@ -169,8 +169,9 @@ def generate(n: int, seed0: int, nx: int = 256, ny: int = 128, steps: int = 1000
         sd = [seed0 + c0 + i for i in range(m)]
         geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=s, r_min=r_min, r_max=r_max, target_porosity=sample_recipe(s))
                  for s in sd]
+        # the packed fluid-only batch (about twice the dense batch's speed on these packings)
         b = lbm.Batch(9, [(nx, ny, 1)] * m, precision=4, n_steps=steps, inlet_kind=lbm.LBM_INLET_PROFILE,
-                      geometries=geoms, device=dev)
+                      geometries=geoms, device=dev, layout="compact")
         rho_in = b.new_inlet()
         tgt = np.zeros((m, ny), np.float32)
         for i, s in enumerate(sd):
@@ -273,3 +274,37 @@ def evaluate(net: UNet, seeds, nx: int = 256, ny: int = 128, steps: int = 10000,
                          "seconds": round(time.perf_counter() - t0, 3), "rel_err": res.rel_err_inlet}
         rows.append(row)
     return rows
+
+
+def evaluate_batched(net: UNet, seeds, nx: int = 256, ny: int = 128, steps: int = 10000, tau: float = 0.8,
+                     device="cuda", tol: float = 1e-3, max_evals: int = 400, time_limit: float = 120.0,
+                     r_min: int = 6, r_max: int = 12, from_guess: bool = True):
+    """The held-out inversions of `evaluate`, all seeds in one packed batch
+    (lock-step L-BFGS, invert.BatchInversion), started from the network's
+    guesses (or from delta = 0): rounds (batched gradient evaluations),
+    seconds for all of them, and the per-instance results."""
+    from . import autotune
+    from . import invert as I
+
+    dev = torch.device(device)
+    data = generate(len(seeds), int(seeds[0]), nx, ny, steps, chunk=len(seeds), tau=tau, device=device,
+                    r_min=r_min, r_max=r_max)
+    guess = predict(net, data.x).cpu().numpy().astype(np.float64)
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=int(s), r_min=r_min, r_max=r_max, target_porosity=sample_recipe(int(s)))
+             for s in seeds]
+    b = lbm.Batch(9, [(nx, ny, 1)] * len(seeds), precision=4, n_steps=steps, inlet_kind=lbm.LBM_INLET_PROFILE,
+                  geometries=geoms, device=dev)
+    tuned = autotune.tune_batch(b)
+    truth = [data.target[i].cpu().numpy().astype(np.float64) * 1e-3 for i in range(len(seeds))]
+    rho_in = b.new_inlet()
+    for i in range(len(seeds)):
+        b.view_inlet(rho_in, i).copy_(torch.as_tensor(1.0 + truth[i], device=dev))
+    taus = torch.full((len(seeds),), tau, dtype=torch.float64, device=dev)
+    ut = b.velocity(b.forward(rho_in, taus, 1.0))
+    theta0 = [guess[i] if from_guess else np.zeros(ny) for i in range(len(seeds))]
+    inv = I.BatchInversion(b, ut, 1.0, tau, theta0=theta0)
+    r = inv.run_lbfgs(truth_delta=truth, tol=tol, max_evals=max_evals, time_limit=time_limit)
+    return {"instances": len(seeds), "layout": tuned["layout"], "start": "network guess" if from_guess else "delta = 0",
+            "rounds": r["rounds"], "seconds": round(r["seconds"], 3), "converged": r["converged"],
+            "evaluations": r["evaluations"], "rel_err": r["rel_err"],
+            "seconds_per_instance": round(r["seconds"] / len(seeds), 3)}

@@ -201,3 +201,51 @@ def test_batch_status_word_reports_nonfinite(layout):
     torch.cuda.synchronize()
     assert b.status() == lbm.LBM_ERR_NONFINITE
     assert b.status() == lbm.LBM_OK  # reading clears the word
+
+
+def test_batched_inversions_reach_1e3_like_single_instances():
+    """Lock-step L-BFGS over a packed batch recovers every instance's inlet
+    profile to 1e-3 relative error; a single compact plan of one instance
+    (same gradients bit for bit) takes about the same evaluations."""
+    from paper_2310_00810_gb300 import invert as I
+
+    sizes = [(96, 48, 1), (128, 64, 1), (64, 32, 1)]
+    geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=400 + i, r_min=3, r_max=6, target_porosity=0.65, inlet_buffer=4)
+             for i in range(3)]
+    T = 1500
+    b = lbm.Batch(9, sizes, precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometries=geoms,
+                  layout="compact")
+    truth = [W.inlet_profile(ny, seed=500 + i) for i, (_, ny, _) in enumerate(sizes)]
+    rho_in = b.new_inlet()
+    for i in range(3):
+        b.view_inlet(rho_in, i).copy_(dev(1.0 + truth[i]))
+    tau = dev([0.8] * 3)
+    ut = b.velocity(b.forward(rho_in, tau, 1.0))
+    inv = I.BatchInversion(b, ut, 1.0, 0.8)
+    r = inv.run_lbfgs(truth_delta=truth, tol=1e-3, max_evals=400)
+    assert r["converged"], r["rel_err"]
+    assert max(r["rel_err"]) <= 1e-3
+    assert r["rounds"] == max(r["evaluations"])
+    s = lbm.Solver(9, *sizes[1][:2], precision=4, n_steps=T, inlet_kind=lbm.LBM_INLET_PROFILE, geometry=geoms[1],
+                   layout="compact")
+    f = s.forward(dev(1.0 + truth[1]), dev([0.8]), 1.0)
+    _, u1 = s.macroscopic(f)
+    single = I.Inversion(s, u1.contiguous(), 1.0, tau0=0.8)
+    rs = single.run_lbfgs(max_evals=400, tol=1e-3, truth_delta=truth[1])
+    assert rs.converged
+    assert abs(single.evaluations - r["evaluations"][1]) <= max(3, 0.2 * single.evaluations)
+
+
+def test_batch_tuner_picks_a_layout_that_keeps_results():
+    from paper_2310_00810_gb300 import autotune
+
+    b, geoms, T, inlet, rho_in, ut, tau = _batch_case("d2q9_f32", True, "dense")
+    f_dense = b.forward(rho_in, tau, 1.0).clone()
+    r = autotune.tune_batch(b, t_tune=16, cache=None)
+    assert r["layout"] in ("dense", "compact") and b.layout == r["layout"]
+    assert set(r["timings_us"]) == {"batch:dense", "batch:compact"}
+    f = b.forward(rho_in, tau, 1.0)
+    for i in range(b.n):
+        fl = ~b.view_mask(i).bool()
+        np.testing.assert_allclose(b.view_state(f, i)[:, fl].cpu().numpy(), b.view_state(f_dense, i)[:, fl].cpu().numpy(),
+                                   rtol=1e-5, atol=1e-9)

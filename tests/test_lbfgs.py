@@ -2,6 +2,7 @@
 objectives (CPU): exact line steps on a quadratic, the bound that keeps tau
 above 1/2, and recovery from non-finite trial points."""
 import numpy as np
+import pytest
 
 from paper_2310_00810_gb300 import invert as I
 
@@ -147,3 +148,49 @@ def test_adam_state_round_trip(tmp_path):
     assert other.t == 17
     for k in ("theta", "m", "v", "theta_tau", "m_tau", "v_tau", "rho_in", "tau"):
         assert torch.equal(getattr(other, k), getattr(inv, k)), k
+
+
+def test_lockstep_runs_equal_independent_runs():
+    """lbfgs_lockstep over several problems takes, per problem, exactly the
+    steps of an independent lbfgs run (same points, same evaluation count),
+    whatever the other problems do (they stop at different rounds)."""
+    rng = np.random.default_rng(7)
+    probs = []
+    for n in (3, 5, 8, 4):
+        A = rng.standard_normal((n, n))
+        H = A @ A.T + n * np.eye(n) * (0.2 + rng.random())
+        b = rng.standard_normal(n)
+        probs.append((H, b, np.linalg.solve(H, b)))
+
+    def single(i):
+        H, b, _ = probs[i]
+        return lambda x: (0.5 * x @ H @ x - b @ x, H @ x - b)
+
+    def errors(i):
+        return lambda x: (float(np.linalg.norm(x - probs[i][2]) / np.linalg.norm(probs[i][2])), None)
+
+    done = [lambda e: e[0] <= 1e-10] * len(probs)
+    x0s = [np.zeros(len(p[1])) for p in probs]
+    rounds = []
+
+    def batch(req):
+        rounds.append(sorted(req))
+        return {i: single(i)(x) for i, x in req.items()}
+
+    got = I.lbfgs_lockstep(batch, x0s, errors=[errors(i) for i in range(len(probs))], done=done, max_evals=200)
+    for i in range(len(probs)):
+        want = I.lbfgs(single(i), x0s[i], errors=errors(i), done=done[i], max_evals=200)
+        assert got[i].converged and want.converged
+        assert got[i].evaluations == want.evaluations
+        assert np.array_equal(got[i].x, want.x)
+        assert got[i].losses == want.losses
+    assert len(rounds) == max(r.evaluations for r in got)
+    assert len(rounds[-1]) < len(probs)  # the smaller problems finished earlier
+
+
+def test_lockstep_reports_an_evaluation_failure():
+    def batch(req):
+        raise I.InjectedFailure("device lost")
+
+    with pytest.raises(I.InjectedFailure):
+        I.lbfgs_lockstep(batch, [np.zeros(2), np.zeros(3)], max_evals=10)
