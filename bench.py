@@ -62,8 +62,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--no-batch-invert", action="store_true", help="skip the batched time-to-1e-3 leg")
-    ap.add_argument("--batch-invert-instances", type=int, default=8,
+    ap.add_argument("--batch-invert-instances", type=int, default=12,
                     help="instances of the batched time-to-1e-3 leg (the first of the 64-instance recipe)")
+    ap.add_argument("--batch-invert-max-nx", type=int, default=384,
+                    help="largest nx of the batched time-to-1e-3 leg's instances (1024: every size)")
     ap.add_argument("--no-c3", action="store_true", help="skip the 3D joint (head, tau) inversion leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-initialiser leg")
     ap.add_argument("--no-wake", action="store_true", help="skip the cylinder-wake viscosity inversion leg")
@@ -300,7 +302,8 @@ def run_native(args):
     inversion = None if args.no_invert else time_to_target(P, args.invert_time_limit)
     batched = None if args.no_batch else batch_leg(device, args.batch_instances, rank)
     batched_inv = None if args.no_batch_invert else batch_invert_leg(device, args.batch_invert_instances, rank,
-                                                                      args.invert_time_limit)
+                                                                      args.invert_time_limit,
+                                                                      max_nx=args.batch_invert_max_nx)
     c3 = None if args.no_c3 else c3_leg(device, args.invert_time_limit)
     learned = None if args.no_learned else learned_init_leg(device, args.learned_solves, args.learned_epochs,
                                                             args.learned_eval, args.invert_time_limit / 2)
@@ -621,12 +624,13 @@ def batch_leg(device, count, rank, steps=2, layout=None):
             "sizes": f"nx in [{min(s[0] for s in sizes)}, {max(s[0] for s in sizes)}], ny = nx / 2"}
 
 
-def batch_invert_leg(device, count, rank, time_limit, n_single=2):
+def batch_invert_leg(device, count, rank, time_limit, n_single=2, max_nx=1024):
     """Time to 1e-3 relative error on the inlet profiles of `count` batched
-    instances (the first `count` of the 64-instance recipe, T = 5000): one
-    L-BFGS per instance in lock step over the autotuned packed batch, against
-    the plain single-instance inversion (autotuned plan, L-BFGS from delta = 0)
-    of `n_single` of the same instances, run one after another."""
+    instances (the first `count` of the 64-instance recipe with nx <= max_nx,
+    T = 5000): one L-BFGS per instance in lock step over the autotuned packed
+    batch, against the plain single-instance inversion (autotuned plan, L-BFGS
+    from delta = 0) of `n_single` of the same instances, run one after
+    another."""
     import torch
 
     from paper_2310_00810_gb300 import autotune, lbm
@@ -634,7 +638,7 @@ def batch_invert_leg(device, count, rank, time_limit, n_single=2):
     from paper_2310_00810_gb300 import workloads as W
 
     T = 5000
-    spec = W.batch_sizes(64, seed=replica_seeds(rank)["batch"])[:count]
+    spec = [x for x in W.batch_sizes(64, seed=replica_seeds(rank)["batch"]) if x[0] <= max_nx][:count]
     sizes = [(nx, ny, 1) for nx, ny, _, _ in spec]
     geoms = [dict(kind=lbm.LBM_GEOM_DISKS, seed=sd, r_min=6, r_max=12, target_porosity=por)
              for nx, ny, por, sd in spec]
@@ -665,7 +669,8 @@ def batch_invert_leg(device, count, rank, time_limit, n_single=2):
         del s, si
     single_per_instance = float(np.mean([x["seconds"] for x in singles])) if singles else None
     batched_per_instance = r["seconds"] / b.n
-    out = {"instances": b.n, "time_steps": T, "layout": tuned["layout"], "method": "L-BFGS per instance, lock step",
+    out = {"instances": b.n, "selection": f"the first {b.n} instances of the 64-instance recipe with nx <= {max_nx}",
+           "time_steps": T, "layout": tuned["layout"], "method": "L-BFGS per instance, lock step",
            "start": "delta = 0", "sizes": [f"{nx}x{ny}" for nx, ny, _ in sizes],
            "rounds": r["rounds"], "seconds": round(r["seconds"], 2), "converged": r["converged"],
            "converged_count": int(sum(1 for x in r["rel_err"] if x is not None and x <= 1e-3)),
