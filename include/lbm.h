@@ -120,6 +120,9 @@ typedef struct lbm_kernel_choice {
     int32_t overlap;         /* 1: the reverse sweep recomputes segment s - 1 on a second stream while
                                 the adjoint steps of segment s run (two segment buffers) */
     int32_t adjoint_tma_rows; /* tile height of the D2Q9 TMA adjoint kernels: 4 or 8 (0: as tma_rows) */
+    int32_t steps_per_launch; /* 1, or 2: two stream-collide steps per launch (temporal blocking: a tile plus a
+                                 two-node halo in shared memory) where the dense D2Q9 FP32 TMA kernels apply,
+                                 in the forward sweep, the segment recompute and lbm_step; 0 reads as 1 */
 } lbm_kernel_choice;
 
 /* Sets / reads the plan's kernel choice (an autotuner's knob).  Cached CUDA

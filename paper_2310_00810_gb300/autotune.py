@@ -4,8 +4,8 @@ For a given lattice (size, Q, precision, geometry) it times, on the device,
 the candidate kernel families of the stream-collide and adjoint steps in the
 dense layout — TMA staging with 8- or 4-row tiles, register kernels with 4 or
 2 nodes per thread, one node per thread — then programmatic dependent launch
-on/off and the one-launch persistent sweeps, the overlapped reverse sweep (recompute on a second stream) on/off, then
-the fluid-only (compact) layout, and keeps the fastest.  Only the speed differs between candidates;
+on/off and the one-launch persistent sweeps, the overlapped reverse sweep (recompute on a second stream) on/off,
+two stream-collide steps per launch (D2Q9 FP32), then the fluid-only (compact) layout, and keeps the fastest.  Only the speed differs between candidates;
 every family and layout computes the same step.  Results are cached in JSON
 keyed by GPU name, Q, precision, lattice size and inlet kind.
 
@@ -167,6 +167,14 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
         timings[f"sweep:best,overlap={ov}"] = round(t * 1e6, 3)
         if t < best_t:
             best, best_t = c, t
+    if tq.q == 9 and tq.precision == 4 and p.nx % 4 == 0 and not best.get("persist"):
+        # two stream-collide steps per launch (temporal blocking), with either tile height
+        for rows in (8, 4):
+            c = dict(best, steps_per_launch=2, tma_rows=rows)
+            t = time_sweeps(c)
+            timings[f"sweep:best,steps_per_launch=2,rows={rows}"] = round(t * 1e6, 3)
+            if t < best_t:
+                best, best_t = c, t
     layout = "dense"
     tp.set_layout("compact")
     if tp.layout == "compact":

@@ -399,7 +399,8 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     if (!fam_ok(k->step_family) || !fam_ok(k->adjoint_family) || (k->vec != 2 && k->vec != 4) ||
         (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1) ||
         (k->overlap != 0 && k->overlap != 1) ||
-        (k->adjoint_tma_rows != 0 && k->adjoint_tma_rows != 4 && k->adjoint_tma_rows != 8))
+        (k->adjoint_tma_rows != 0 && k->adjoint_tma_rows != 4 && k->adjoint_tma_rows != 8) ||
+        k->steps_per_launch < 0 || k->steps_per_launch > 2)
         return LBM_ERR_INVALID_ARG;
     PlanInfo& I = p->info;
     I.step_family = k->step_family;
@@ -409,6 +410,7 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     I.tma_min_tiles = 1;
     I.tma_ty = k->tma_rows;
     I.adj_tma_ty = k->adjoint_tma_rows ? k->adjoint_tma_rows : k->tma_rows;
+    I.steps2 = k->steps_per_launch == 2 ? 1 : 0;
     I.pdl = k->pdl;
     I.use_persist = k->persist;
     I.overlap = k->overlap;
@@ -425,6 +427,7 @@ lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
     k->vec = I.max_vec >= 4 ? 4 : 2;
     k->tma_rows = I.tma_ty;
     k->adjoint_tma_rows = I.adj_tma_ty;
+    k->steps_per_launch = I.steps2 ? 2 : 1;
     k->pdl = I.pdl;
     k->persist = I.use_persist;
     k->overlap = I.overlap;
@@ -590,24 +593,43 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         if (T == 1) return step_launch(p->info, kStreamOnly, g0, d_f, bc, tau, s);
         return forward_persist(p->info, a, bc, tau, s);
     }
-    // the state chain g^0 .. g^{T-1}: checkpoint slots where the reverse sweep needs them, else ping-pong
+    // the state chain g^0 .. g^{T-1}: checkpoint slots where the reverse sweep needs them, else ping-pong;
+    // with two steps per launch, g^t of a pair is written only where it is a checkpoint
     auto next_state = [&](int t, const unsigned char* cur) -> unsigned char* {
         unsigned char* dst = slot(t);
         return dst ? dst : (cur == ping0 ? ping1 : ping0);
     };
+    const bool pairs = step2_possible(p->info, bc);
+    // walks the chain, calling launch(src, two, mid, dst) once per launch: two steps (mid: g^t where it is a
+    // checkpoint, else nullptr) or one
+    using Launch = std::function<lbm_status(const unsigned char*, bool, unsigned char*, unsigned char*)>;
+    auto chain = [&](const Launch& launch, unsigned char* g0, unsigned char** last_out) -> lbm_status {
+        unsigned char* cur = g0;
+        int t = 1;
+        while (t <= T - 1) {
+            const bool two = pairs && t + 1 <= T - 1;
+            unsigned char* mid = two ? slot(t) : nullptr;
+            unsigned char* dst = next_state(two ? t + 1 : t, cur);
+            LBM_TRY(launch(cur, two, mid, dst));
+            cur = dst;
+            t += two ? 2 : 1;
+        }
+        *last_out = cur;
+        return LBM_OK;
+    };
     unsigned char* g0 = slot(0) ? slot(0) : ping0;
-    unsigned char* last = g0;
-    for (int t = 1; t <= T - 1; ++t) last = next_state(t, last);
+    unsigned char* last = nullptr;
+    chain([](const unsigned char*, bool, unsigned char*, unsigned char*) { return LBM_OK; }, g0, &last);
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         LBM_TRY(write_mrt_rates(p, bc, st_));
         if (cudaMemsetAsync(g0, 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;  // g^0 = rest
-        unsigned char* cur = g0;
-        for (int t = 1; t <= T - 1; ++t) {
-            unsigned char* dst = next_state(t, cur);
-            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, tau, st_));
-            cur = dst;
-        }
-        return LBM_OK;
+        unsigned char* end = nullptr;
+        return chain(
+            [&](const unsigned char* src, bool two, unsigned char* mid, unsigned char* dst) -> lbm_status {
+                return two ? step2_launch(p->info, src, mid, dst, bc, tau, st_)
+                           : step_launch(p->info, kStreamCollide, src, dst, bc, tau, st_);
+            },
+            g0, &end);
     };
     GraphKey key;
     key.op = 1;
@@ -639,12 +661,22 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
         LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bc, tau, s));
     else
         LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, tau, s));
-    unsigned char* last = (n_steps - 1) % 2 == 0 ? ping0 : ping1;
+    // n - 1 stream-collide steps between the ping-pong buffers, two per launch where the two-step kernel applies
+    const bool pairs = step2_possible(p->info, bc);
+    const int launches = pairs ? n_steps / 2 : n_steps - 1;  // (n - 1) / 2 pairs and (n - 1) % 2 single steps
+    unsigned char* last = launches % 2 == 0 ? ping0 : ping1;
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         unsigned char* cur = ping0;
-        for (int t = 1; t < n_steps; ++t) {
+        int t = 1;
+        while (t < n_steps) {
             unsigned char* dst = cur == ping0 ? ping1 : ping0;
-            LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, tau, st_));
+            if (pairs && t + 1 < n_steps) {
+                LBM_TRY(step2_launch(p->info, cur, nullptr, dst, bc, tau, st_));
+                t += 2;
+            } else {
+                LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, tau, st_));
+                t += 1;
+            }
             cur = dst;
         }
         return LBM_OK;
@@ -760,16 +792,25 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     auto base_of = [&](int sg) -> const unsigned char* {
         return sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
     };
+    const bool pairs = step2_possible(p->info, bc);
     auto recompute = [&](int sg, cudaStream_t s_) -> lbm_status {
         const int len = std::min(k, T - sg * k);
         const unsigned char* prev = base_of(sg);
-        for (int j = 1; j < len; ++j) {
+        int j = 1;
+        while (j < len) {
             if (sg == 0 && j == 1) {
                 if (cudaMemsetAsync(seg(0, 1), 0, p->info.state_bytes, s_) != cudaSuccess) return LBM_ERR_CUDA;
+                prev = seg(sg, j);
+                j += 1;
+            } else if (pairs && j + 1 < len) {  // every segment state is needed: g^t goes to mid
+                LBM_TRY(step2_launch(p->info, prev, seg(sg, j), seg(sg, j + 1), bc, tau, s_));
+                prev = seg(sg, j + 1);
+                j += 2;
             } else {
                 LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), bc, tau, s_));
+                prev = seg(sg, j);
+                j += 1;
             }
-            prev = seg(sg, j);
         }
         return LBM_OK;
     };

@@ -81,6 +81,7 @@ struct PlanInfo {
     int step_family;  // LBM_FAMILY_* of the stream-collide kernels
     int adj_family;   // LBM_FAMILY_* of the adjoint kernels
     int pdl;          // 1: launch the sweep kernels with programmatic dependent launch
+    int steps2;       // 1: two stream-collide steps per launch where the two-step kernel applies
     int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes
     int overlap;      // 1: reverse sweep recomputes the next segment on a second stream during the adjoint steps
     int uw_extrap;    // 1: Eq. 6 with the extrapolated wall velocity (one-node-per-thread or fluid-only kernels)
@@ -205,6 +206,11 @@ bool adjoint_launch_vec(const PlanInfo& p, int t0, const void* gprev, const void
 int vec_blocks_max(const PlanInfo& p);
 bool step_launch_tma(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
                      cudaStream_t s);
+bool step2_launch_tma(const PlanInfo& p, const void* src, void* dst, void* mid, const Bc& bc, const double* tau,
+                      cudaStream_t s);
+bool step2_possible(const PlanInfo& p, const Bc& bc);
+lbm_status step2_launch(const PlanInfo& p, const void* src, void* mid, void* dst, const Bc& bc, const double* tau,
+                        cudaStream_t s);
 bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
                         const double* tau, double* grad_acc, double* partial, cudaStream_t s);
 lbm_status adjoint_launch(const PlanInfo& p, int t_is_zero, const void* gprev, const void* lam_in, void* lam_out,

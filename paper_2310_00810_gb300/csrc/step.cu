@@ -79,4 +79,27 @@ lbm_status step_launch(const PlanInfo& plan, int mode, const void* src, void* ds
     return cuda_status(cudaGetLastError());
 }
 
+// Two stream-collide steps in one launch, g^{t+1} = C S C S (g^{t-1}), and
+// g^t into mid (nullable): the temporally blocked TMA kernel of the dense
+// D2Q9 FP32 layout (node-velocity Eq. 6, BGK).  step2_possible says whether
+// it applies; step2_launch otherwise runs the two steps as two launches
+// (through mid, which must then be a state buffer).
+bool step2_possible(const PlanInfo& p, const Bc& bc)
+{
+    const PlanInfo q = with_family(p, p.step_family);
+    return p.steps2 && !p.cmp.nf && p.q == 9 && p.prec == 4 && p.geo.nx % 4 == 0 && q.use_tma && p.tma_variant == 1 &&
+           !bc.uw_extrap && !bc.mrt && (reinterpret_cast<uintptr_t>(p.geo.link) & 15u) == 0;
+}
+
+lbm_status step2_launch(const PlanInfo& p, const void* src, void* mid, void* dst, const Bc& bc, const double* tau,
+                        cudaStream_t s)
+{
+    if (step2_possible(p, bc) && step2_launch_tma(with_family(p, p.step_family), src, dst, mid, bc, tau, s))
+        return cuda_status(cudaGetLastError());
+    if (!mid) return LBM_ERR_INVALID_ARG;
+    lbm_status st = step_launch(p, kStreamCollide, src, mid, bc, tau, s);
+    if (st != LBM_OK) return st;
+    return step_launch(p, kStreamCollide, mid, dst, bc, tau, s);
+}
+
 }  // namespace lbm

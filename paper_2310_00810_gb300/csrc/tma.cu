@@ -431,6 +431,159 @@ __global__ void __launch_bounds__(H::NCONS + 32, 1)
     }
 }
 
+// D2Q9 stream-collide, two time steps per launch (temporal blocking, for
+// lattices whose state stays in L2, where a launch costs more than the bytes
+// it moves).  Per tile: TMA brings g^{t-1} over the tile plus two halo rows
+// and four halo columns on each side (x from x0 - 4 keeps the copy 16-byte
+// aligned) and the link words over the same box.  Step 1 computes g^t node by
+// node over the tile plus one halo node on each side into shared memory;
+// step 2 computes g^{t+1} on the tile with the 4-wide code of the one-step
+// kernel, reading g^t from shared memory.  mid (nullable) also receives g^t
+// on the tile (a checkpoint or a segment state).  The halo nodes of step 1
+// are computed again by the neighbouring tiles: each step is the one-step
+// kernel's arithmetic, so the result is the one-step sweep's.
+template <int TY_>
+struct Halo2x {
+    static constexpr int TX = 128, TY = TY_;
+    static constexpr int BW = TX + 8, BH = TY + 4;            // input box: x0 - 4 .. x0 + TX + 4, y0 - 2 .. y0 + TY + 2
+    static constexpr int BOX = ((BW * BH + 31) / 32) * 32;    // floats per direction, padded to 128 B
+    static constexpr int MH = TY + 2;                         // g^t rows: y0 - 1 .. y0 + TY
+    static constexpr int MBOX = ((BW * MH + 31) / 32) * 32;   // floats per direction of g^t (same columns)
+    static constexpr int LINKS = BW * BH;                     // link words of the box
+    static constexpr int GX = TX / 4;
+    static constexpr int NCONS = GX * TY;                     // threads: 4 nodes each in step 2
+    static constexpr int MID_NODES = (TX + 2) * MH;           // step-1 nodes: x0 - 1 .. x0 + TX, MH rows
+    static constexpr size_t IN_BYTES = (size_t)9 * BOX * 4;
+    static constexpr size_t LINK_BYTES = (((size_t)LINKS * 4 + 127) / 128) * 128;
+    static constexpr size_t MID_BYTES = (size_t)9 * MBOX * 4;
+    static constexpr uint32_t TX_BYTES = 9 * BW * BH * 4 + LINKS * 4;  // bytes the copies deliver
+    static constexpr size_t SMEM = IN_BYTES + LINK_BYTES + MID_BYTES + 16;
+};
+using Halo2x8 = Halo2x<8>;
+using Halo2x4 = Halo2x<4>;
+static_assert((Halo2x8::BOX * 4) % 128 == 0 && Halo2x8::IN_BYTES % 128 == 0 && Halo2x8::LINK_BYTES % 128 == 0 &&
+                  (Halo2x8::MBOX * 4) % 16 == 0 && (Halo2x8::BW * 4) % 16 == 0,
+              "TMA destinations 128-byte aligned, float4 rows");
+static_assert(Halo2x8::SMEM <= 227 * 1024 && Halo2x4::SMEM <= 227 * 1024, "shared memory per CTA");
+
+template <class H>
+__global__ void __launch_bounds__(H::NCONS, 1)
+    k_step2_tma_halo(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map_link,
+                     float* __restrict__ dst, float* __restrict__ mid, Geo g, Bc bc, const double* __restrict__ tau)
+{
+    pdl_enter();
+    using L = Lattice<9>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const float* box = reinterpret_cast<const float*>(smem);                                 // g^{t-1}, [9][BH][BW]
+    const uint32_t* lnk = reinterpret_cast<const uint32_t*>(smem + H::IN_BYTES);            // [BH][BW]
+    float* M = reinterpret_cast<float*>(smem + H::IN_BYTES + H::LINK_BYTES);                // g^t, [9][MH][BW]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + H::IN_BYTES + H::LINK_BYTES + H::MID_BYTES);
+    __shared__ int s_abort;
+    const int tid = threadIdx.x;
+    const TileGrid tg = tile_grid(g, H::TX, H::TY, 1);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        s_abort = timeout_latched(bc.status);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    volatile int* abort = &s_abort;
+    if (*abort) return;  // uniform: every thread read the same flag after the barrier
+    const uint64_t wait_ns = (uint64_t)bc.wait_us * 1000ull;
+    if (tid == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_link)) : "memory");
+    }
+    const float omega = 1.0f / (float)*tau;
+    int issued = 0;
+    int k = 0;
+    for (int t = blockIdx.x; t < tg.total; t += gridDim.x, ++k) {
+        const int x0 = (t % tg.ntx) * H::TX, y0 = (t / tg.ntx) * H::TY;
+        if (tid == 0 && !bc.test_stall) {
+            mbar_expect_tx(bar, H::TX_BYTES);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                tma_load4(smem + (size_t)i * H::BOX * 4, &map, bar, x0 - 4, y0 - 2, 0, i);
+            tma_load3(smem + H::IN_BYTES, &map_link, bar, x0 - 4, y0 - 2, 0);
+            issued = k + 1;
+        }
+        const bool ok = mbar_wait(bar, (uint32_t)k & 1u, bc.status, abort, wait_ns);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) drain_copies(bar, 1, issued);
+            return;
+        }
+        // step 1: g^t at x0 - 1 .. x0 + TX, y0 - 1 .. y0 + TY (box column bx = x - x0 + 4, box row by = y - y0 + 2)
+        for (int m = tid; m < H::MID_NODES; m += H::NCONS) {
+            const int mr = m / (H::TX + 2), mc = m % (H::TX + 2);
+            const int x = x0 - 1 + mc, y = y0 - 1 + mr;
+            const int bx = mc + 3, by = mr + 1;
+            float* mo = M + (size_t)mr * H::BW + bx;
+            if (x < 0 || x >= g.nx || y < 0 || y >= g.ny) continue;  // outside the lattice: never pulled
+            const uint32_t lw1[1] = {lnk[by * H::BW + bx]};
+            if (lw1[0] & kLinkSolid) {
+#pragma unroll
+                for (int i = 0; i < 9; ++i) mo[(size_t)i * H::MBOX] = 0.0f;
+                continue;
+            }
+            float v[9][1], own[9][1];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float* bi = box + (size_t)i * H::BOX;
+                v[i][0] = bi[(by - L::c(i, 1)) * H::BW + bx - L::c(i, 0)];
+                own[i][0] = bi[by * H::BW + bx];
+            }
+            pull_fixup_own<9, float, 1>(v, own, x, y, 0, lw1, g, bc);
+            float a[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) a[i] = v[i][0];
+            collide<9, float>(a, omega);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) mo[(size_t)i * H::MBOX] = a[i];
+        }
+        __syncthreads();
+        // step 2: g^{t+1} on the tile from g^t (rows of M start at y0 - 1, columns at x0 - 4)
+        {
+            const int gx = tid % H::GX, gy = tid / H::GX;
+            const int x = x0 + 4 * gx, y = y0 + gy;
+            float v[9][4], own[9][4];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                read_box<H::BW>(v[i], M + (size_t)i * H::MBOX, gy + 1 - L::c(i, 1), gx, L::c(i, 0));
+                read_box<H::BW>(own[i], M + (size_t)i * H::MBOX, gy + 1, gx, 0);
+            }
+            const uint4 lq = *reinterpret_cast<const uint4*>(lnk + (gy + 2) * H::BW + 4 + 4 * gx);
+            const uint32_t lw[4] = {lq.x, lq.y, lq.z, lq.w};
+            const bool live = x < g.nx && y < g.ny;
+            const bool skip = g.skip_sectors && sector_solid(lw, live);
+            if (live && !skip) {
+                const long long n0 = (long long)y * g.nx + x;
+                if (mid) {
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) Vec<float, 4>::store(mid + (long long)i * g.N + n0, own[i]);
+                }
+                pull_fixup_own<9, float, 4>(v, own, x, y, 0, lw, g, bc);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (lw[j] & kLinkSolid) {
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) v[i][j] = 0.0f;
+                    } else {
+                        float a[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) a[i] = v[i][j];
+                        collide<9, float>(a, omega);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) v[i][j] = a[i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 9; ++i) Vec<float, 4>::store(dst + (long long)i * g.N + n0, v[i]);
+            }
+        }
+        __syncthreads();  // the next tile's copies overwrite the box and the link words
+    }
+}
+
 // D2Q9 adjoint, halo form: per tile the nine boxes of g^{t-1} and the nine
 // of lambda^{t+1}, each over the tile rows plus one halo row on each side, and
 // the link words, so the pulls in both directions and every own value
@@ -768,6 +921,23 @@ bool step_tma_halo(const PlanInfo& p, int mode, const void* src, void* dst, cons
     return true;
 }
 
+template <class H>
+bool step2_tma_halo(const PlanInfo& p, const void* src, void* dst, void* mid, const Bc& bc, const double* tau,
+                    cudaStream_t s)
+{
+    const long long tiles = (long long)((p.geo.nx + H::TX - 1) / H::TX) * ((p.geo.ny + H::TY - 1) / H::TY);
+    CUtensorMap map, ml;
+    if (!make_map(&map, src, p.geo, 9, H::BW, H::BH, 1)) return false;
+    if (!make_link_map(&ml, p.geo.link, p.geo, H::BW, H::BH, 1)) return false;
+    static bool ok = allow_smem(k_step2_tma_halo<H>, H::SMEM);
+    if (!ok) return false;
+    const int per_sm = std::max(1, (int)((227 * 1024) / H::SMEM));
+    const int grid = (int)std::min<long long>(tiles, (long long)sm_count() * per_sm);
+    launch_k(p.pdl, k_step2_tma_halo<H>, dim3(grid), dim3(H::NCONS), H::SMEM, s, map, ml, static_cast<float*>(dst),
+             static_cast<float*>(mid), p.geo, bc, tau);
+    return true;
+}
+
 template <int Q>
 bool step_tma(const PlanInfo& p, int mode, const void* src, void* dst, const Bc& bc, const double* tau,
               cudaStream_t s)
@@ -867,6 +1037,14 @@ bool step_launch_tma(const PlanInfo& p, int mode, const void* src, void* dst, co
                    : step_tma_halo<Halo2D8>(p, mode, src, dst, bc, tau, s);
     }
     return p.q == 9 ? step_tma<9>(p, mode, src, dst, bc, tau, s) : step_tma<19>(p, mode, src, dst, bc, tau, s);
+}
+
+bool step2_launch_tma(const PlanInfo& p, const void* src, void* dst, void* mid, const Bc& bc, const double* tau,
+                      cudaStream_t s)
+{
+    if (p.q != 9 || !tma_ok(p, src, dst, mid)) return false;
+    return p.tma_ty == 4 ? step2_tma_halo<Halo2x4>(p, src, dst, mid, bc, tau, s)
+                         : step2_tma_halo<Halo2x8>(p, src, dst, mid, bc, tau, s);
 }
 
 bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out, const Bc& bc,
