@@ -370,6 +370,8 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     // the wait give up on purpose and check that LBM_ERR_TIMEOUT comes back)
     const char* ty = std::getenv("LBM_TMA_ROWS");
     I.tma_ty = ty && std::atoi(ty) == 4 ? 4 : 8;
+    const char* tw = std::getenv("LBM_TMA_WAVES");
+    I.tma_waves = tw ? std::max(1, std::atoi(tw)) : 1;
     I.adj_tma_ty = I.tma_ty;
     I.step_family = LBM_FAMILY_AUTO;
     I.adj_family = LBM_FAMILY_AUTO;

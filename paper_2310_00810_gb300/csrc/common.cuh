@@ -77,6 +77,7 @@ struct PlanInfo {
     int step_variant; // register stream-collide kernel: 0 link-dependent loads, 1 all loads up front
     int tma_variant;  // D2Q9 TMA stream-collide: 0 per-direction shifted boxes, 1 halo boxes + TMA link words
     int tma_ty;       // D2Q9 halo TMA tile height of the stream-collide kernels: 8 or 4 rows
+    int tma_waves;    // D2Q9 halo TMA: one-stage kernels (one tile per CTA) up to tma_waves x SMs tiles
     int adj_tma_ty;   // the same for the adjoint kernels
     int step_family;  // LBM_FAMILY_* of the stream-collide kernels
     int adj_family;   // LBM_FAMILY_* of the adjoint kernels

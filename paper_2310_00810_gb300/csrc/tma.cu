@@ -907,7 +907,9 @@ bool step_tma_halo(const PlanInfo& p, int mode, const void* src, void* dst, cons
     CUtensorMap map, ml;
     if (!make_map(&map, src, p.geo, 9, H::BW, H::BH, 1)) return false;
     if (!make_link_map(&ml, p.geo.link, p.geo, H::TX, H::TY, 1)) return false;
-    const int grid = (int)std::min<long long>(tiles, sm_count());
+    // one-stage kernels take one tile per CTA (several CTAs per SM overlap their load, compute and store
+    // phases); multi-stage kernels are persistent, one CTA per SM
+    const int grid = (int)(H::STAGES == 1 ? tiles : std::min<long long>(tiles, sm_count()));
     float* b = static_cast<float*>(dst);
     if (mode == kStreamCollide) {
         static bool ok = allow_smem(k_step_tma_halo<H, kStreamCollide>, H::SMEM);
@@ -975,7 +977,8 @@ bool adjoint_tma_halo(const PlanInfo& p, int t0, const void* gprev, const void* 
     if (t0) mg = ml;
     else if (!make_map(&mg, gprev, p.geo, 9, H::BW, H::BH, 1)) return false;
     if (!make_link_map(&mk, p.geo.link, p.geo, H::TX, H::TY, 1)) return false;
-    const int grid = (int)std::min<long long>(std::min<long long>(tiles, sm_count()), p.n_partial);
+    const int grid = (int)std::min<long long>(H::STAGES == 1 ? tiles : std::min<long long>(tiles, sm_count()),
+                                              p.n_partial);
     float* lo = static_cast<float*>(lam_out);
     if (t0) {
         static bool ok = allow_smem(k_adjoint_tma_halo<H, true>, H::SMEM);
@@ -1029,7 +1032,7 @@ bool step_launch_tma(const PlanInfo& p, int mode, const void* src, void* dst, co
 {
     if (mode == kCollideOnly || !tma_ok(p, src, dst, nullptr)) return false;
     if (p.q == 9 && p.tma_variant == 1) {
-        const bool one = halo_tiles(p, p.tma_ty) <= sm_count();
+        const bool one = halo_tiles(p, p.tma_ty) <= (long long)p.tma_waves * sm_count();
         if (p.tma_ty == 4)
             return one ? step_tma_halo<Halo2D4x1>(p, mode, src, dst, bc, tau, s)
                        : step_tma_halo<Halo2D4>(p, mode, src, dst, bc, tau, s);
@@ -1052,7 +1055,7 @@ bool adjoint_launch_tma(const PlanInfo& p, int t0, const void* gprev, const void
 {
     if (!tma_ok(p, gprev, lam_in, lam_out)) return false;
     if (p.q == 9 && p.tma_variant == 1) {
-        const bool one = halo_tiles(p, p.adj_tma_ty) <= sm_count();
+        const bool one = halo_tiles(p, p.adj_tma_ty) <= (long long)p.tma_waves * sm_count();
         if (p.adj_tma_ty == 4)
             return one ? adjoint_tma_halo<HaloAdj2D4x1>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s)
                        : adjoint_tma_halo<HaloAdj2D4>(p, t0, gprev, lam_in, lam_out, bc, tau, grad_acc, partial, s);
