@@ -738,10 +738,10 @@ def run_e2e(P, args, device, barrier, world):
 HBM_TRAFFIC = {
     ("disks8192x4096", "dense"): {"stream-collide": 4 * (343.118080e6 + 201.248512e6),
                                   "adjoint": 4 * (642.651648e6 + 217.033472e6)},
-    ("disks8192x4096", "compact"): {"stream-collide": 20132542 / 5032998 * (342.945792e6 + 147.707136e6),
-                                    "adjoint": 20132542 / 5032998 * (525.750016e6 + 161.217024e6)},
-    ("spheres512x256x256", "compact"): {"stream-collide": 15090843 / 1886221 * (293.573888e6 + 116.221696e6),
-                                        "adjoint": 15090843 / 1886221 * (534.989824e6 + 171.275264e6)},
+    ("disks8192x4096", "compact"): {"stream-collide": 20132542 / 5032998 * (342.962176e6 + 147.565568e6),
+                                    "adjoint": 20132542 / 5032998 * (527.729920e6 + 160.612096e6)},
+    ("spheres512x256x256", "compact"): {"stream-collide": 15090843 / 1886221 * (297.474816e6 + 117.429504e6),
+                                        "adjoint": 15090843 / 1886221 * (544.039168e6 + 177.216768e6)},
 }
 
 
