@@ -182,6 +182,15 @@ LBM_API lbm_status lbm_get_collision(const lbm_plan* plan, int32_t* mode, double
 LBM_API lbm_status lbm_set_periodic_y(lbm_plan* plan, int32_t on);
 LBM_API lbm_status lbm_set_velocity_inlet(lbm_plan* plan, int32_t on, double ux, double uy, double uz);
 
+/* A gradual start of the velocity inlet (the flow of section 3.4 started
+ * from rest without the impulse that makes it diverge at u_in = 0.2): the
+ * step producing f^t uses u_in r(t), r(t) = sin^2(pi t / (2 steps)) for
+ * 0 < t < steps and 1 from steps on (steps = 0: none, the default).  Time
+ * counts from the rest state of lbm_forward (lbm_step counts from its input
+ * state).  The reverse sweep needs no change: the inlet's source does not
+ * depend on the state.  Errors: INVALID_ARG for steps < 0. */
+LBM_API lbm_status lbm_set_velocity_ramp(lbm_plan* plan, int32_t steps);
+
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
  * lbm_loss_grad need: ping-pong states, the sqrt(T) checkpoints and two
  * segment buffers, adjoint ping-pong states and FP64 reduction slots. */
@@ -361,6 +370,29 @@ LBM_API lbm_status lbm_spline_grad(const lbm_plan* plan, int32_t ky, int32_t kz,
  * Gradient sums are FP64 in a fixed order (deterministic run to run). */
 LBM_API lbm_status lbm_adjoint(lbm_plan* plan, const double* d_rho_in, const double* d_tau, double rho_out,
                        const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream);
+
+/* A loss over a time window (the wake of section 3.4 observed over time):
+ * L = sum_k L_k(f^{t_k}), each L_k the plan's final-step loss (kind,
+ * normalisation, ROI of lbm_loss_grad) of the state at step t_k against the
+ * k-th target, and its gradient with respect to rho_in and tau, in ONE
+ * reverse sweep: lambda^T is the seed of the observations at T, and the seed
+ * of each observation at t_k < T is added to lambda^{t_k} right after the
+ * adjoint step that produces it (f^{t_k} comes from the recomputed segment
+ * state).  Call after lbm_forward with the same parameters.
+ *  d_f             f^T from that lbm_forward (dense, plan precision)
+ *  n_obs           number of observations (1 .. 65536)
+ *  h_obs_steps     int32[n_obs] HOST array of the steps t_k, 1 <= t_k <= T
+ *  d_u_targets     double[n_obs][D][N] the observed velocity fields
+ *  d_roi           uint8[N] region of interest (nullable: all fluid nodes)
+ *  d_scratch_f, d_scratch_lambda   dense Q N scratch states (plan precision)
+ *  d_loss          double[1] out: L
+ *  d_grad_rho_in, d_grad_tau       out, as lbm_adjoint
+ * Errors: INVALID_ARG (null pointers, n_obs or a step out of range), CUDA. */
+LBM_API lbm_status lbm_adjoint_window(lbm_plan* plan, const double* d_rho_in, const double* d_tau, double rho_out,
+                                      const void* d_f, int32_t n_obs, const int32_t* h_obs_steps,
+                                      const double* d_u_targets, const uint8_t* d_roi, void* d_scratch_f,
+                                      void* d_scratch_lambda, double* d_loss, double* d_grad_rho_in,
+                                      double* d_grad_tau, void* d_ws, void* stream);
 
 /* Moments (Eq. 1-2) in FP64: d_rho double[N] (nullable), d_u double[D N].
  * Solid nodes report rho = 0 and u = 0. */

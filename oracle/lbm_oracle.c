@@ -191,6 +191,36 @@ int SYM(set_velocity_inlet)(int on, double ux, double uy, double uz)
     return 0;
 }
 
+/* A gradual start of the velocity inlet (the flow of section 3.4 from rest):
+ * the step that produces f^t uses u_in r(t) with r(t) = sin^2(pi t / (2 t_r))
+ * for t < t_r and 1 from t_r on (t_r = 0: no ramp).  step() produces the
+ * time level g_time_next; forward() and gradient() set it step by step,
+ * set_time sets it for a lone step() call. */
+static int g_ramp_steps = 0;
+static int g_time_next = 1;
+
+int SYM(set_velocity_ramp)(int steps)
+{
+    if (steps < 0) return -1;
+    g_ramp_steps = steps;
+    return 0;
+}
+
+int SYM(set_time)(int t_next)
+{
+    g_time_next = t_next;
+    return 0;
+}
+
+static double ramp_factor(int t)
+{
+    if (g_ramp_steps <= 0 || t >= g_ramp_steps) return 1.0;
+    if (t <= 0) return 0.0;
+    const double pi = 3.14159265358979323846;
+    const double s = sin(pi * (double)t / (2.0 * (double)g_ramp_steps));
+    return s * s;
+}
+
 /* What node (x,y,z) receives in direction i: the population streaming along
  * the link from x - c_i.  Wall planes (y, z) win over pressure planes (x);
  * with periodic y a link leaving the y range re-enters on the other side. */
@@ -452,7 +482,7 @@ int SYM(step)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_t* 
                     } else if (cls == LINK_ABB_IN && g_vel_inlet) {
                         double cu = 0;
                         for (int a = 0; a < L.d; ++a) cu += L.c[i][a] * g_u_in[a];
-                        v = fstar[(long)L.opp[i] * N + n] + 6.0 * L.w[i] * cu;
+                        v = fstar[(long)L.opp[i] * N + n] + 6.0 * L.w[i] * cu * ramp_factor(g_time_next);
                     } else {
                         real_t rw = cls == LINK_ABB_IN ? inlet_rho(rho_in, inlet_profile, &D, y, z) : *rho_out;
                         v = -fstar[(long)L.opp[i] * N + n] + abb_source(&L, i, rw, u);
@@ -494,6 +524,7 @@ int SYM(forward)(int q, int nx, int ny, int nz, const uint8_t* mask, const real_
         rest_state(&L, N, a);
     for (int t = 0; t < T; ++t) {
         if (tape) memcpy(tape + (long)t * QN, a, sizeof(real_t) * (size_t)QN);
+        g_time_next = t + 1;
         int rc = SYM(step)(q, nx, ny, nz, mask, a, b, rho_in, inlet_profile, rho_out, tau);
         if (rc) {
             free(a);
@@ -847,6 +878,7 @@ int orc_gradient(int q, int nx, int ny, int nz, const uint8_t* mask, const doubl
         rest_state(&L, N, a);
     for (int t = 0; t < T; ++t) {
         if (t % k == 0) memcpy(ckpt + (long)(t / k) * QN, a, sizeof(double) * (size_t)QN);
+        g_time_next = t + 1;
         if ((rc = orc_step(q, nx, ny, nz, mask, a, b, rho_in, inlet_profile, rho_out, tau))) goto done;
         double* tmp = a;
         a = b;
@@ -869,10 +901,12 @@ int orc_gradient(int q, int nx, int ny, int nz, const uint8_t* mask, const doubl
     for (int s = n_seg - 1; s >= 0; --s) {
         int t0 = s * k, len = (t0 + k <= T) ? k : T - t0;
         memcpy(seg, ckpt + (long)s * QN, sizeof(double) * (size_t)QN);
-        for (int j = 1; j < len; ++j)
+        for (int j = 1; j < len; ++j) {
+            g_time_next = t0 + j;
             if ((rc = orc_step(q, nx, ny, nz, mask, seg + (long)(j - 1) * QN, seg + (long)j * QN, rho_in,
                                inlet_profile, rho_out, tau)))
                 goto done;
+        }
         for (int j = len - 1; j >= 0; --j) {
             if ((rc = orc_adjoint_step(q, nx, ny, nz, mask, seg + (long)j * QN, lam, lam2, rho_in, inlet_profile,
                                        rho_out, tau, g_rho_in, &g_omega)))
@@ -892,6 +926,111 @@ done:
     free(b);
     free(lam);
     free(lam2);
+    return rc;
+}
+
+/* A loss over a time window: L = sum_k L_k(f^{t_k}), L_k the final-step
+ * loss (loss(): kind, normalisation, ROI) of state f^{t_k} against the k-th
+ * target u_targets[k][D N], observation steps 0 <= t_k <= T (the wake of
+ * section 3.4 observed over time).  Its gradient with respect to rho_in and
+ * tau by one reverse sweep: lam^T = dL/df^T (nonzero if T is observed), and
+ * for t = T - 1 .. 0, lam^t = J_t^T lam^{t+1} (adjoint_step), plus dL_k/df^t
+ * when t = t_k.  Same checkpoint schedule as orc_gradient. */
+int orc_gradient_window(int q, int nx, int ny, int nz, const uint8_t* mask, const double* rho_in, int inlet_profile,
+                        const double* rho_out, const double* tau, int T, int n_obs, const int* obs_t,
+                        const double* u_targets, const uint8_t* roi, int loss_kind, int loss_norm, int ckpt_stride,
+                        double* loss_out, double* g_rho_in, double* g_tau)
+{
+    lattice L;
+    if (lattice_make(q, &L)) return -1;
+    if (T < 1 || n_obs < 1) return -1;
+    for (int o = 0; o < n_obs; ++o)
+        if (obs_t[o] < 0 || obs_t[o] > T) return -1;
+    long N = (long)nx * ny * nz, QN = (long)q * N, DN = (long)L.d * N;
+    int n_in = inlet_profile ? ny * nz : 1;
+    int k = ckpt_stride > 0 ? ckpt_stride : T;
+    int n_seg = (T + k - 1) / k;
+    int rc = 0;
+    double* ckpt = (double*)malloc(sizeof(double) * (size_t)QN * (size_t)n_seg);
+    double* seg = (double*)malloc(sizeof(double) * (size_t)QN * (size_t)k);
+    double* a = (double*)malloc(sizeof(double) * (size_t)QN);
+    double* b = (double*)malloc(sizeof(double) * (size_t)QN);
+    double* lam = (double*)malloc(sizeof(double) * (size_t)QN);
+    double* lam2 = (double*)malloc(sizeof(double) * (size_t)QN);
+    double* seed = (double*)malloc(sizeof(double) * (size_t)QN);
+    if (!ckpt || !seg || !a || !b || !lam || !lam2 || !seed) {
+        rc = -2;
+        goto done;
+    }
+    *loss_out = 0.0;
+    rest_state(&L, N, a);
+    /* forward: checkpoints, and the loss terms of the observed states */
+    for (int t = 0; t <= T; ++t) {
+        for (int o = 0; o < n_obs; ++o)
+            if (obs_t[o] == t) {
+                double lk = 0.0;
+                if ((rc = orc_loss(q, nx, ny, nz, mask, a, u_targets + (long)o * DN, roi, loss_kind, loss_norm, &lk,
+                                   NULL)))
+                    goto done;
+                *loss_out += lk;
+            }
+        if (t == T) break;
+        if (t % k == 0) memcpy(ckpt + (long)(t / k) * QN, a, sizeof(double) * (size_t)QN);
+        g_time_next = t + 1;
+        if ((rc = orc_step(q, nx, ny, nz, mask, a, b, rho_in, inlet_profile, rho_out, tau))) goto done;
+        double* tmp = a;
+        a = b;
+        b = tmp;
+    }
+    /* lam^T: the seeds of the observations at T (a holds f^T) */
+    for (long i = 0; i < QN; ++i) lam[i] = 0.0;
+    for (int o = 0; o < n_obs; ++o)
+        if (obs_t[o] == T) {
+            double lk = 0.0;
+            if ((rc = orc_loss(q, nx, ny, nz, mask, a, u_targets + (long)o * DN, roi, loss_kind, loss_norm, &lk, seed)))
+                goto done;
+            for (long i = 0; i < QN; ++i) lam[i] += seed[i];
+        }
+    /* reverse sweep, one segment at a time, last segment first */
+    for (int i = 0; i < n_in; ++i) g_rho_in[i] = 0;
+    double g_omega = 0;
+    for (int s = n_seg - 1; s >= 0; --s) {
+        int t0 = s * k, len = (t0 + k <= T) ? k : T - t0;
+        memcpy(seg, ckpt + (long)s * QN, sizeof(double) * (size_t)QN);
+        for (int j = 1; j < len; ++j) {
+            g_time_next = t0 + j;
+            if ((rc = orc_step(q, nx, ny, nz, mask, seg + (long)(j - 1) * QN, seg + (long)j * QN, rho_in,
+                               inlet_profile, rho_out, tau)))
+                goto done;
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const double* ft = seg + (long)j * QN; /* f^t, t = t0 + j */
+            if ((rc = orc_adjoint_step(q, nx, ny, nz, mask, ft, lam, lam2, rho_in, inlet_profile, rho_out, tau,
+                                       g_rho_in, &g_omega)))
+                goto done;
+            double* tmp = lam;
+            lam = lam2;
+            lam2 = tmp;
+            for (int o = 0; o < n_obs; ++o)
+                if (obs_t[o] == t0 + j) {
+                    double lk = 0.0;
+                    if ((rc = orc_loss(q, nx, ny, nz, mask, ft, u_targets + (long)o * DN, roi, loss_kind, loss_norm,
+                                       &lk, seed)))
+                        goto done;
+                    for (long i = 0; i < QN; ++i) lam[i] += seed[i];
+                }
+        }
+    }
+    *g_tau = -g_omega / ((*tau) * (*tau));
+
+done:
+    free(ckpt);
+    free(seg);
+    free(a);
+    free(b);
+    free(lam);
+    free(lam2);
+    free(seed);
     return rc;
 }
 

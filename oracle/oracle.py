@@ -139,20 +139,41 @@ def set_velocity_inlet(u) -> None:
         _check(fn(0 if u is None else 1, *v), "set_velocity_inlet")
 
 
-class wake_options:
-    """``with wake_options(periodic_y=True, velocity_inlet=(0.05, 0)): ...``"""
+def set_velocity_ramp(steps: int) -> None:
+    """Gradual start of the velocity inlet over `steps` steps (0: none): the
+    step producing f^t uses u_in sin^2(pi t / (2 steps)) for t < steps (both builds)."""
+    for cs in (False, True):
+        lib = _lib(cs)
+        fn = lib.orc_cs_set_velocity_ramp if cs else lib.orc_set_velocity_ramp
+        _check(fn(int(steps)), "set_velocity_ramp")
 
-    def __init__(self, periodic_y=False, velocity_inlet=None):
-        self.p, self.u = periodic_y, velocity_inlet
+
+def set_time(t_next: int) -> None:
+    """The time level a lone step() call produces (forward and gradient set
+    it themselves); matters only with a velocity ramp (both builds)."""
+    for cs in (False, True):
+        lib = _lib(cs)
+        fn = lib.orc_cs_set_time if cs else lib.orc_set_time
+        _check(fn(int(t_next)), "set_time")
+
+
+class wake_options:
+    """``with wake_options(periodic_y=True, velocity_inlet=(0.05, 0), ramp=500): ...``"""
+
+    def __init__(self, periodic_y=False, velocity_inlet=None, ramp=0):
+        self.p, self.u, self.r = periodic_y, velocity_inlet, ramp
 
     def __enter__(self):
         set_periodic_y(self.p)
         set_velocity_inlet(self.u)
+        set_velocity_ramp(self.r)
         return self
 
     def __exit__(self, *exc):
         set_periodic_y(False)
         set_velocity_inlet(None)
+        set_velocity_ramp(0)
+        set_time(1)
         return False
 
 
@@ -364,6 +385,28 @@ def gradient(q, mask, rho_in, rho_out, tau, T, u_target, roi=None, kind=LOSS_VEC
                                _p(L), _p(g_in), _p(g_tau), _p(fT)), "gradient")
     g = g_in if prof else g_in[0]
     return (L[0], g, g_tau[0], fT) if return_fT else (L[0], g, g_tau[0])
+
+
+def gradient_window(q, mask, rho_in, rho_out, tau, T, obs_steps, u_targets, roi=None, kind=LOSS_VEC,
+                    norm=NORM_SUM, ckpt_stride=0):
+    """Loss over a time window, L = sum_k L_k(f^{t_k}) (u_targets[k] the k-th
+    target [D, ...], obs_steps the t_k in 0..T), and its gradient by one
+    reverse sweep: (L, dL/drho_in, dL/dtau)."""
+    nx, ny, nz = _dims(q, mask.shape)
+    m = np.ascontiguousarray(mask, np.uint8)
+    rin, rout, t = _real_args(rho_in, rho_out, tau, np.float64)
+    prof = 1 if rin.size > 1 else 0
+    obs = np.ascontiguousarray(obs_steps, np.int32)
+    ut = np.ascontiguousarray(u_targets, np.float64)
+    assert ut.shape[0] == obs.size
+    r = None if roi is None else np.ascontiguousarray(roi, np.uint8)
+    L = np.zeros(1)
+    g_in = np.zeros(rin.size)
+    g_tau = np.zeros(1)
+    _check(_lib().orc_gradient_window(q, nx, ny, nz, _p(m), _p(rin), prof, _p(rout), _p(t), int(T), int(obs.size),
+                                      _p(obs), _p(ut), _p(r), kind, norm, int(ckpt_stride), _p(L), _p(g_in),
+                                      _p(g_tau)), "gradient_window")
+    return L[0], (g_in if prof else g_in[0]), g_tau[0]
 
 
 def adam(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):

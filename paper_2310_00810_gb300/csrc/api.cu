@@ -174,6 +174,7 @@ Bc make_bc(const lbm_plan* p, const double* rho_in, double rho_out, void* ws)
     bc.vel_inlet = p->info.vel_inlet;
     bc.wait_us = p->info.wait_us;
     bc.test_stall = p->info.test_stall ? 1 : 0;
+    bc.ramp_steps = p->info.vel_inlet ? p->info.ramp_steps : 0;
     return bc;
 }
 
@@ -487,6 +488,14 @@ lbm_status lbm_set_velocity_inlet(lbm_plan* p, int32_t on, double ux, double uy,
     return LBM_OK;
 }
 
+lbm_status lbm_set_velocity_ramp(lbm_plan* p, int32_t steps)
+{
+    if (!p || steps < 0) return LBM_ERR_INVALID_ARG;
+    p->info.ramp_steps = steps;
+    drop_graphs(p);
+    return LBM_OK;
+}
+
 lbm_status lbm_get_collision(const lbm_plan* p, int32_t* mode, double* rates)
 {
     if (!p || !mode) return LBM_ERR_INVALID_ARG;
@@ -604,7 +613,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     const bool pairs = step2_possible(p->info, bc);
     // walks the chain, calling launch(src, two, mid, dst) once per launch: two steps (mid: g^t where it is a
     // checkpoint, else nullptr) or one
-    using Launch = std::function<lbm_status(const unsigned char*, bool, unsigned char*, unsigned char*)>;
+    using Launch = std::function<lbm_status(const unsigned char*, bool, unsigned char*, unsigned char*, int)>;
     auto chain = [&](const Launch& launch, unsigned char* g0, unsigned char** last_out) -> lbm_status {
         unsigned char* cur = g0;
         int t = 1;
@@ -612,7 +621,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             const bool two = pairs && t + 1 <= T - 1;
             unsigned char* mid = two ? slot(t) : nullptr;
             unsigned char* dst = next_state(two ? t + 1 : t, cur);
-            LBM_TRY(launch(cur, two, mid, dst));
+            LBM_TRY(launch(cur, two, mid, dst, t));
             cur = dst;
             t += two ? 2 : 1;
         }
@@ -621,15 +630,16 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     };
     unsigned char* g0 = slot(0) ? slot(0) : ping0;
     unsigned char* last = nullptr;
-    chain([](const unsigned char*, bool, unsigned char*, unsigned char*) { return LBM_OK; }, g0, &last);
+    chain([](const unsigned char*, bool, unsigned char*, unsigned char*, int) { return LBM_OK; }, g0, &last);
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         LBM_TRY(write_mrt_rates(p, bc, st_));
         if (cudaMemsetAsync(g0, 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;  // g^0 = rest
         unsigned char* end = nullptr;
         return chain(
-            [&](const unsigned char* src, bool two, unsigned char* mid, unsigned char* dst) -> lbm_status {
-                return two ? step2_launch(p->info, src, mid, dst, bc, tau, st_)
-                           : step_launch(p->info, kStreamCollide, src, dst, bc, tau, st_);
+            [&](const unsigned char* src, bool two, unsigned char* mid, unsigned char* dst, int t) -> lbm_status {
+                // the launch producing g^t streams into time level t (the velocity inlet's ramp)
+                return two ? step2_launch(p->info, src, mid, dst, at_time(bc, t), tau, st_)
+                           : step_launch(p->info, kStreamCollide, src, dst, at_time(bc, t), tau, st_);
             },
             g0, &end);
     };
@@ -639,7 +649,7 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     key.ptr[1] = p->link;
     key.scalar = rho_out;
     LBM_TRY(run_sequence(p, key, s, issue));
-    return final_stream(p, last, d_f, bc, tau, s);  // f^T = S(g^{T-1}) into the caller's array
+    return final_stream(p, last, d_f, at_time(bc, T), tau, s);  // f^T = S(g^{T-1}) into the caller's array
 }
 
 lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out, const void* d_f_in,
@@ -673,10 +683,10 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
         while (t < n_steps) {
             unsigned char* dst = cur == ping0 ? ping1 : ping0;
             if (pairs && t + 1 < n_steps) {
-                LBM_TRY(step2_launch(p->info, cur, nullptr, dst, bc, tau, st_));
+                LBM_TRY(step2_launch(p->info, cur, nullptr, dst, at_time(bc, t), tau, st_));
                 t += 2;
             } else {
-                LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, bc, tau, st_));
+                LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, at_time(bc, t), tau, st_));
                 t += 1;
             }
             cur = dst;
@@ -694,7 +704,7 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
         key.n = n_steps;
         LBM_TRY(run_sequence(p, key, s, issue));
     }
-    return final_stream(p, last, d_f_out, bc, tau, s);
+    return final_stream(p, last, d_f_out, at_time(bc, n_steps), tau, s);
 }
 
 lbm_status lbm_loss_grad(lbm_plan* p, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
@@ -757,13 +767,26 @@ lbm_status lbm_spline_grad(const lbm_plan* p, int32_t ky, int32_t kz, const doub
                               static_cast<cudaStream_t>(stream));
 }
 
-lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
-                       const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream)
+// The reverse sweep of lbm_adjoint and lbm_adjoint_window: lambda^T from
+// d_lambda, or (win) from the window's observations at T; with a window, the
+// seed of each observation at t < T is added to lambda^t right after the
+// adjoint step that produces it, and the observations' losses are summed
+// into win->d_loss.
+struct Window {
+    int n_obs;
+    const int32_t* steps;     // host, 1..T
+    const double* targets;    // [n_obs][D][N]
+    const uint8_t* roi;       // nullable
+    const void* f_T;          // f^T of the preceding forward sweep (dense)
+    void* scr_f;              // dense scratch state: f^t of an observation
+    void* scr_lam;            // dense scratch state: its seed
+    double* d_loss;
+};
+
+static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
+                                const void* d_lambda, const Window* win, double* d_grad_rho_in, double* d_grad_tau,
+                                void* d_ws, cudaStream_t s)
 {
-    LBM_TRY(check_common(p, d_ws));
-    LBM_TRY(check_layout_options(p));
-    if (!d_rho_in || !d_tau || !d_lambda || !d_grad_rho_in || !d_grad_tau || !d_ws) return LBM_ERR_INVALID_ARG;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* ws = bytes(d_ws);
     p->last_ws = d_ws;
     const double* rho_in = nullptr;
@@ -774,7 +797,7 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     const size_t st = align256(p->info.state_bytes);
     double* grad_acc = reinterpret_cast<double*>(ws + p->ws.grad_acc);
     double* partial = reinterpret_cast<double*>(ws + p->ws.partial);
-    if (persist_ok(p->info)) {
+    if (persist_ok(p->info) && !win) {
         // one cooperative launch for all segments: recompute, then adjoint steps backwards
         if (cudaMemsetAsync(grad_acc, 0, sizeof(double) * (size_t)p->info.n_acc, s) != cudaSuccess)
             return LBM_ERR_CUDA;
@@ -805,11 +828,12 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
                 prev = seg(sg, j);
                 j += 1;
             } else if (pairs && j + 1 < len) {  // every segment state is needed: g^t goes to mid
-                LBM_TRY(step2_launch(p->info, prev, seg(sg, j), seg(sg, j + 1), bc, tau, s_));
+                LBM_TRY(step2_launch(p->info, prev, seg(sg, j), seg(sg, j + 1), at_time(bc, sg * k + j - 1), tau,
+                                     s_));
                 prev = seg(sg, j + 1);
                 j += 2;
-            } else {
-                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), bc, tau, s_));
+            } else {  // seg(sg, j) holds g^{sg k + j - 1}
+                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), at_time(bc, sg * k + j - 1), tau, s_));
                 prev = seg(sg, j);
                 j += 1;
             }
@@ -820,6 +844,22 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     void* lam_T = ws + p->ws.lam[1];
     const void* lam_cur = lam_T;
     int lam_next = 0;
+    double* loss_tmp = reinterpret_cast<double*>(ws + p->ws.status + kScalarTmp);
+    // one observation of the window at time t: its loss into d_loss, its seed dL_t/df^t added to lam (internal
+    // layout); f^t = S(g^{t-1}) is streamed from src into the dense scratch first (or is f^T itself)
+    auto observe = [&](int o, int t, const unsigned char* src, void* lam, cudaStream_t s_) -> lbm_status {
+        const void* ft = win->f_T;
+        if (t < T) {
+            LBM_TRY(final_stream(p, src, win->scr_f, at_time(bc, t), tau, s_));
+            ft = win->scr_f;
+        }
+        const size_t dn = (size_t)p->info.d * (size_t)p->info.geo.N;
+        LBM_TRY(loss_launch(p->info, ft, win->targets + (size_t)o * dn, win->roi, p->desc.loss_kind,
+                            p->desc.loss_norm, loss_tmp, win->scr_lam, ws, p->ws, s_));
+        LBM_TRY(accumulate_launch(win->d_loss, loss_tmp, s_));
+        return p->info.cmp.nf ? compact_gather_add_launch(p->info, win->scr_lam, lam, s_)
+                              : add_state_launch(p->info, lam, win->scr_lam, s_);
+    };
     auto adjoint_steps = [&](int sg, cudaStream_t s_) -> lbm_status {
         const int len = std::min(k, T - sg * k);
         for (int j = len - 1; j >= 0; --j) {
@@ -827,6 +867,9 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
             const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
             void* lam_out = ws + p->ws.lam[lam_next];
             LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, tau, grad_acc, partial, s_));
+            if (win)  // src holds g^{t-1}, t = sg k + j
+                for (int o = 0; o < win->n_obs; ++o)
+                    if (win->steps[o] == sg * k + j && !at_rest) LBM_TRY(observe(o, sg * k + j, src, lam_out, s_));
             lam_cur = lam_out;
             lam_next ^= 1;
         }
@@ -838,10 +881,18 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         for (auto& e : p->ev)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LBM_ERR_CUDA;
     }
-    if (p->info.cmp.nf)  // lambda^T into the compact layout
+    if (win) {  // lambda^T: the seeds of the observations at T
+        if (cudaMemsetAsync(win->d_loss, 0, sizeof(double), s) != cudaSuccess ||
+            cudaMemsetAsync(lam_T, 0, p->info.state_bytes, s) != cudaSuccess)
+            return LBM_ERR_CUDA;
+        LBM_TRY(write_mrt_rates(p, bc, s));
+        for (int o = 0; o < win->n_obs; ++o)
+            if (win->steps[o] == T) LBM_TRY(observe(o, T, nullptr, lam_T, s));
+    } else if (p->info.cmp.nf) {  // lambda^T into the compact layout
         LBM_TRY(compact_gather_launch(p->info, d_lambda, lam_T, s));
-    else if (cudaMemcpyAsync(lam_T, d_lambda, p->dense_state_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    } else if (cudaMemcpyAsync(lam_T, d_lambda, p->dense_state_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
         return LBM_ERR_CUDA;
+    }
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         LBM_TRY(write_mrt_rates(p, bc, st_));
         lam_cur = lam_T;
@@ -881,14 +932,55 @@ lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         return LBM_OK;
     };
     GraphKey key;
-    key.op = 3;
+    key.op = win ? 4 : 3;
     key.ptr[0] = d_ws;
     key.ptr[1] = p->link;
     key.scalar = rho_out;
+    if (win) {  // the observations' buffers and steps are part of the launch sequence
+        key.ptr[2] = win->targets;
+        key.ptr[3] = win->roi;
+        key.ptr[4] = win->scr_f;
+        key.ptr[5] = win->scr_lam;
+        key.ptr[6] = win->d_loss;
+        unsigned long long h = 1469598103934665603ull;  // FNV-1a over the step list
+        for (int o = 0; o < win->n_obs; ++o) {
+            h ^= (unsigned long long)(uint32_t)win->steps[o];
+            h *= 1099511628211ull;
+        }
+        key.n = (long long)(h ^ (unsigned long long)win->n_obs);
+    }
     LBM_TRY(run_sequence(p, key, s, issue));
     // the gradients into the caller's arrays
     return finish_gradients_launch(p->info, grad_acc, partial, tau, d_grad_rho_in, d_grad_tau,
                                    reinterpret_cast<uint32_t*>(ws + p->ws.status), s);
+}
+
+lbm_status lbm_adjoint(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
+                       const void* d_lambda, double* d_grad_rho_in, double* d_grad_tau, void* d_ws, void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    LBM_TRY(check_layout_options(p));
+    if (!d_rho_in || !d_tau || !d_lambda || !d_grad_rho_in || !d_grad_tau || !d_ws) return LBM_ERR_INVALID_ARG;
+    return reverse_sweep(p, d_rho_in, d_tau, rho_out, d_lambda, nullptr, d_grad_rho_in, d_grad_tau, d_ws,
+                         static_cast<cudaStream_t>(stream));
+}
+
+lbm_status lbm_adjoint_window(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out,
+                              const void* d_f, int32_t n_obs, const int32_t* h_obs_steps,
+                              const double* d_u_targets, const uint8_t* d_roi, void* d_scratch_f,
+                              void* d_scratch_lambda, double* d_loss, double* d_grad_rho_in, double* d_grad_tau,
+                              void* d_ws, void* stream)
+{
+    LBM_TRY(check_common(p, d_ws));
+    LBM_TRY(check_layout_options(p));
+    if (!d_rho_in || !d_tau || !d_f || !h_obs_steps || !d_u_targets || !d_scratch_f || !d_scratch_lambda ||
+        !d_loss || !d_grad_rho_in || !d_grad_tau || !d_ws || n_obs < 1 || n_obs > 65536)
+        return LBM_ERR_INVALID_ARG;
+    for (int o = 0; o < n_obs; ++o)
+        if (h_obs_steps[o] < 1 || h_obs_steps[o] > p->desc.n_steps) return LBM_ERR_INVALID_ARG;
+    Window w{n_obs, h_obs_steps, d_u_targets, d_roi, d_f, d_scratch_f, d_scratch_lambda, d_loss};
+    return reverse_sweep(p, d_rho_in, d_tau, rho_out, nullptr, &w, d_grad_rho_in, d_grad_tau, d_ws,
+                         static_cast<cudaStream_t>(stream));
 }
 
 lbm_status lbm_macroscopic(lbm_plan* p, const void* d_f, double* d_rho, double* d_u, void* stream)

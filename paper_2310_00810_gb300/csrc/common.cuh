@@ -50,7 +50,27 @@ struct Bc {
     uint32_t* status;      // device status word (bounded waits latch LBM_ERR_TIMEOUT here)
     uint32_t wait_us = 2000000u;  // time bound of each mbarrier wait of the TMA kernels, in microseconds
     char test_stall = 0;   // 1: TMA producers issue no copies, so every consumer wait runs out (tests only)
+    int t_level = 0;       // the time level this launch's streaming produces (f^t_level)
+    int ramp_steps = 0;    // the velocity inlet starts gradually: u_in r(t_level), r = 1 from ramp_steps on
 };
+
+// The gradual start of the velocity inlet: r(t) = sin^2(pi t / (2 R)) for
+// 0 < t < R, 0 at t <= 0 and 1 from R on (R <= 0: no ramp).
+__device__ __forceinline__ double inlet_ramp(const Bc& bc)
+{
+    if (bc.ramp_steps <= 0 || bc.t_level >= bc.ramp_steps) return 1.0;
+    if (bc.t_level <= 0) return 0.0;
+    const double s = sin(3.14159265358979323846 * (double)bc.t_level / (2.0 * (double)bc.ramp_steps));
+    return s * s;
+}
+
+// The boundary data of a launch whose streaming produces time level t.
+inline Bc at_time(const Bc& bc, int t)
+{
+    Bc b = bc;
+    b.t_level = t;
+    return b;
+}
 
 // Fluid-only ("compact") layout tables (compact.cu).  nf = 0: dense layout.
 constexpr int32_t kCmpBB = -1;   // neighbour code: halfway bounce-back link
@@ -89,6 +109,7 @@ struct PlanInfo {
     int mrt;          // 1: D2Q9 MRT collision (one-node-per-thread or fluid-only kernels)
     int vel_inlet;    // 1: velocity inlet instead of Eq. 6 at x = -1/2 (fluid-only kernels)
     double u_in[3];   // its velocity
+    int ramp_steps;   // its gradual start (0: none)
     double mrt_rates[3];  // s_e, s_eps, s_q of the MRT collision
     unsigned spin_limit;  // grid-barrier spin limit of the persistent sweeps
     unsigned wait_us;     // time bound of each mbarrier wait of the TMA kernels (microseconds)
@@ -288,6 +309,9 @@ lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* d
 lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,
                               const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s);
 lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s);
+lbm_status compact_gather_add_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s);
+lbm_status add_state_launch(const PlanInfo& p, void* dst, const void* src, cudaStream_t s);
+lbm_status accumulate_launch(double* dst, const double* src, cudaStream_t s);
 
 lbm_status probe_launch(const PlanInfo& p, const void* f, long long n_probe, const int64_t* node,
                         const double* rho_target, double weight, double* d_loss, void* lambda, uint32_t* status,

@@ -257,7 +257,7 @@ __device__ __forceinline__ void pull_cmp(T (&v)[Q], const T* __restrict__ src, l
                 double cu = 0.0;
 #pragma unroll
                 for (int a = 0; a < L::D; ++a) cu += (double)L::c(i, a) * uin[a];
-                v[i] = loc[L::opp(i)] + T(6.0 * L::w(i) * cu);
+                v[i] = loc[L::opp(i)] + T(6.0 * L::w(i) * cu * inlet_ramp(bc));
             } else {
                 const T cu = cdot<Q, T>(i, u);
                 v[i] = -loc[L::opp(i)] + T(2.0 * L::w(i)) * (drw + rwT * (T(4.5) * cu * cu - T(1.5) * uu));
@@ -672,8 +672,9 @@ __global__ void __launch_bounds__(kCmpThreads, 4)
     add_warp_partial<T>(dom, k < c.nf, k, partial);
 }
 
-// The caller's dense arrays (packed, for a batch) -> the compact state.
-template <typename T>
+// The caller's dense arrays (packed, for a batch) -> the compact state
+// (ADD: added to it).
+template <typename T, bool ADD>
 __global__ void __launch_bounds__(kCmpThreads)
     k_cmp_gather(const T* __restrict__ dense, T* __restrict__ cmp, Cmp c, const BCmpInst* __restrict__ insts,
                  const int* __restrict__ blk_inst, int q)
@@ -682,7 +683,11 @@ __global__ void __launch_bounds__(kCmpThreads)
     const BCmpInst I = insts[block_instance(blk_inst, k)];
     if (k >= I.k0 + I.nf) return;
     const long long n = c.idx[k];
-    for (int d = 0; d < q; ++d) cmp[(long long)d * c.nf + k] = dense[I.f_off + (long long)d * I.g.N + n];
+    for (int d = 0; d < q; ++d) {
+        const T v = dense[I.f_off + (long long)d * I.g.N + n];
+        if (ADD) cmp[(long long)d * c.nf + k] += v;
+        else cmp[(long long)d * c.nf + k] = v;
+    }
 }
 
 // One instance's tables (built by compact_build) into the packed arrays:
@@ -797,16 +802,18 @@ lbm_status adjoint_any(const BCmpArgs& a, int t0, const void* gprev, const void*
     return cuda_status(cudaGetLastError());
 }
 
-lbm_status gather_any(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s)
+lbm_status gather_any(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s, bool add = false)
 {
     if (a.n_blocks == 0) return LBM_OK;
     const dim3 grid(a.n_blocks), block(kCmpThreads);
-    if (a.prec == 4)
-        k_cmp_gather<float><<<grid, block, 0, s>>>(static_cast<const float*>(dense), static_cast<float*>(compact), a.c,
-                                                   a.insts, a.blk_inst, a.q);
-    else
-        k_cmp_gather<double><<<grid, block, 0, s>>>(static_cast<const double*>(dense), static_cast<double*>(compact),
-                                                    a.c, a.insts, a.blk_inst, a.q);
+    const float* df = static_cast<const float*>(dense);
+    const double* dd = static_cast<const double*>(dense);
+    float* cf = static_cast<float*>(compact);
+    double* cd = static_cast<double*>(compact);
+    if (a.prec == 4 && add) k_cmp_gather<float, true><<<grid, block, 0, s>>>(df, cf, a.c, a.insts, a.blk_inst, a.q);
+    else if (a.prec == 4) k_cmp_gather<float, false><<<grid, block, 0, s>>>(df, cf, a.c, a.insts, a.blk_inst, a.q);
+    else if (add) k_cmp_gather<double, true><<<grid, block, 0, s>>>(dd, cd, a.c, a.insts, a.blk_inst, a.q);
+    else k_cmp_gather<double, false><<<grid, block, 0, s>>>(dd, cd, a.c, a.insts, a.blk_inst, a.q);
     return cuda_status(cudaGetLastError());
 }
 
@@ -907,6 +914,12 @@ lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* com
 {
     if (p.cmp.nf == 0) return LBM_OK;
     return gather_any(single_args(p, nullptr), dense, compact, s);
+}
+
+lbm_status compact_gather_add_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s)
+{
+    if (p.cmp.nf == 0) return LBM_OK;
+    return gather_any(single_args(p, nullptr), dense, compact, s, true);
 }
 
 lbm_status bstep_launch_cmp(const BCmpArgs& a, int mode, const void* src, void* dst, bool dense_out,

@@ -7,6 +7,8 @@
 // deterministic run to run.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include <mutex>
 
 #include "device.cuh"
@@ -309,6 +311,33 @@ lbm_status loss_launch_noalloc(const PlanInfo& p, const void* f, const double* u
 #undef LBM_NOALLOC_LOSS
     // no status word on this path: a non-finite loss shows as NaN/Inf in d_loss
     k_loss_final<<<1, kReduceThreads, 0, s>>>(partial, p.n_blocks, d_loss, nullptr);
+    return cuda_status(cudaGetLastError());
+}
+
+// ------------------------------------------- sums of a time-window loss
+
+__global__ void k_accumulate(double* __restrict__ dst, const double* __restrict__ src) { *dst += *src; }
+
+template <typename T>
+__global__ void k_add_state(T* __restrict__ dst, const T* __restrict__ src, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] += src[i];
+}
+
+lbm_status accumulate_launch(double* dst, const double* src, cudaStream_t s)
+{
+    k_accumulate<<<1, 1, 0, s>>>(dst, src);
+    return cuda_status(cudaGetLastError());
+}
+
+// dst += src over a dense state (Q N values of the plan's precision).
+lbm_status add_state_launch(const PlanInfo& p, void* dst, const void* src, cudaStream_t s)
+{
+    const long long n = (long long)p.q * p.geo.N;
+    const unsigned grid = (unsigned)std::min<long long>((n + 255) / 256, 4096);
+    if (p.prec == 4) k_add_state<float><<<grid, 256, 0, s>>>(static_cast<float*>(dst), static_cast<const float*>(src), n);
+    else k_add_state<double><<<grid, 256, 0, s>>>(static_cast<double*>(dst), static_cast<const double*>(src), n);
     return cuda_status(cudaGetLastError());
 }
 

@@ -34,6 +34,7 @@ ENTRY_POINTS = (
     "lbm_plan_create", "lbm_plan_destroy", "lbm_plan_set_kernels", "lbm_plan_get_kernels", "lbm_workspace_size", "lbm_init_geometry", "lbm_bind_geometry",
     "lbm_compact_size", "lbm_compact_bind", "lbm_set_abb_velocity", "lbm_get_abb_velocity",
     "lbm_set_collision", "lbm_get_collision", "lbm_set_periodic_y", "lbm_set_velocity_inlet",
+    "lbm_set_velocity_ramp", "lbm_adjoint_window",
     "lbm_forward", "lbm_step", "lbm_loss_grad", "lbm_loss_grad_noalloc", "lbm_probe_loss_grad", "lbm_spline_basis",
     "lbm_spline_profile", "lbm_spline_grad", "lbm_adjoint", "lbm_macroscopic", "lbm_darcy", "lbm_adam_step",
     "lbm_get_status", "lbm_error_string", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_layout",
@@ -100,6 +101,8 @@ def load():
                 "lbm_set_collision": [vp, i32, f64, f64, f64],
                 "lbm_set_periodic_y": [vp, i32],
                 "lbm_set_velocity_inlet": [vp, i32, f64, f64, f64],
+                "lbm_set_velocity_ramp": [vp, i32],
+                "lbm_adjoint_window": [vp, vp, vp, f64, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp],
                 "lbm_get_collision": [vp, C.POINTER(C.c_int32), vp],
                 "lbm_get_abb_velocity": [vp, C.POINTER(C.c_int32)],
                 "lbm_probe_loss_grad": [vp, vp, C.c_int64, vp, vp, f64, vp, vp, vp, vp],
@@ -285,6 +288,28 @@ def lbm_set_velocity_inlet(plan: Plan, u) -> None:
     """u = (ux, uy[, uz]) turns the velocity inlet on; None turns it off (Eq. 6)."""
     v = [0.0, 0.0, 0.0] if u is None else [float(a) for a in u] + [0.0] * (3 - len(u))
     _check(load().lbm_set_velocity_inlet(plan.handle, 0 if u is None else 1, *v), "lbm_set_velocity_inlet")
+
+
+def lbm_set_velocity_ramp(plan: Plan, steps: int) -> None:
+    """Gradual start of the velocity inlet over `steps` steps (0: none)."""
+    _check(load().lbm_set_velocity_ramp(plan.handle, int(steps)), "lbm_set_velocity_ramp")
+
+
+def lbm_adjoint_window(plan: Plan, rho_in, tau, rho_out: float, f_T, steps, u_targets, roi, scratch_f,
+                       scratch_lam, loss, grad_rho_in, grad_tau, ws, stream=None) -> None:
+    """Window loss sum_k L(f^{t_k}) and its gradient in one reverse sweep
+    (after lbm_forward); steps: host int sequence, u_targets [n_obs, D, ...]."""
+    import numpy as np
+
+    st = np.ascontiguousarray(np.asarray(steps, np.int32))
+    n = int(st.size)
+    _check(load().lbm_adjoint_window(plan.handle, _ptr(rho_in, torch.float64, plan.n_in), _ptr(tau, torch.float64, 1),
+                                     float(rho_out), _ptr(f_T, plan.dtype, plan.q * plan.N), n,
+                                     st.ctypes.data_as(C.c_void_p), _ptr(u_targets, torch.float64, n * plan.d * plan.N),
+                                     _ptr(roi, torch.uint8, plan.N), _ptr(scratch_f, plan.dtype, plan.q * plan.N),
+                                     _ptr(scratch_lam, plan.dtype, plan.q * plan.N), _ptr(loss, torch.float64, 1),
+                                     _ptr(grad_rho_in, torch.float64, plan.n_in), _ptr(grad_tau, torch.float64, 1),
+                                     _ptr(ws, torch.uint8), _stream(stream)), "lbm_adjoint_window")
 
 
 def lbm_get_collision(plan: Plan):
@@ -525,6 +550,24 @@ class Solver:
         g_tau = torch.zeros(1, dtype=torch.float64, device=self.device) if g_tau is None else g_tau
         self.run(lambda: lbm_adjoint(self.plan, rho_in, tau, rho_out, lam, g_in, g_tau, self.ws))
         return g_in, g_tau
+
+    def set_velocity_ramp(self, steps: int) -> None:
+        """The velocity inlet starts gradually over `steps` steps."""
+        lbm_set_velocity_ramp(self.plan, steps)
+
+    def adjoint_window(self, rho_in, tau, rho_out, f_T, steps, u_targets, roi=None):
+        """(L, dL/drho_in, dL/dtau) of the window loss sum_k L(f^{t_k}) against
+        u_targets [n_obs, D, ...] at the host steps t_k, after forward() with
+        the same parameters returned f_T."""
+        if not hasattr(self, "_win_scratch") or self._win_scratch[0].numel() != self.plan.q * self.plan.N:
+            self._win_scratch = (self.new_state(), self.new_state())
+        loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        g_in = torch.zeros(self.plan.n_in, dtype=torch.float64, device=self.device)
+        g_tau = torch.zeros(1, dtype=torch.float64, device=self.device)
+        a, b = self._win_scratch
+        self.run(lambda: lbm_adjoint_window(self.plan, rho_in, tau, rho_out, f_T, steps, u_targets.contiguous(), roi,
+                                            a, b, loss, g_in, g_tau, self.ws))
+        return loss, g_in, g_tau
 
     def macroscopic(self, f):
         rho = torch.empty(self.plan.shape, dtype=torch.float64, device=self.device)

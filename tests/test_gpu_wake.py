@@ -29,6 +29,8 @@ def _oracle_defaults():
     yield
     O.set_periodic_y(False)
     O.set_velocity_inlet(None)
+    O.set_velocity_ramp(0)
+    O.set_time(1)
     O.set_collision(O.COLL_BGK)
 
 
@@ -180,3 +182,97 @@ def test_velocity_inlet_in_a_walled_channel():
     with O.wake_options(periodic_y=False, velocity_inlet=(0.04, 0.0)):
         _, uw = O.macroscopic(9, m, O.forward(9, m, 1.0, 1.0, 0.7, T))
     assert rel(u.cpu().numpy(), uw) < 1e-11
+
+
+# ------------------------------------- gradual start and a loss over a time window
+
+
+@pytest.mark.parametrize("precision", [8, 4])
+def test_ramped_wake_forward_and_gradient_match_the_oracle(precision):
+    m = cylinder(64, 24, 16, 12.3, 6)
+    T, R, tau = 60, 40, 0.7
+    s = wake_solver(m, precision, T, stride=7)
+    s.set_velocity_ramp(R)
+    ut = W.perturbation((2,) + m.shape, seed=41, scale=2e-3)
+    roi = np.zeros(m.shape, np.uint8)
+    roi[:, 30:] = 1
+    f = s.forward(dev([1.0]), dev([tau]), 1.0)
+    _, u = s.macroscopic(f)
+    L, lam = s.loss_grad(f, dev(ut), dev(roi, torch.uint8))
+    _, g_tau = s.adjoint(dev([1.0]), dev([tau]), 1.0, lam)
+    O.set_collision(O.COLL_MRT, *RATES)
+    with O.wake_options(periodic_y=True, velocity_inlet=(0.05, 0.0), ramp=R):
+        _, uw = O.macroscopic(9, m, O.forward(9, m, 1.0, 1.0, tau, T))
+        Lw, _, gw = O.gradient(9, m, 1.0, 1.0, tau, T, ut, roi=roi, ckpt_stride=7)
+    tol_u, tol_g = (1e-11, 1e-9) if precision == 8 else (1e-4, 1e-3)
+    assert rel(u.cpu().numpy(), uw) < tol_u
+    assert abs(L.item() - Lw) <= tol_u * abs(Lw)
+    assert abs(g_tau.item() - gw) <= tol_g * abs(gw)
+    # the ramp changes the flow (a check that it is applied at all)
+    s0 = wake_solver(m, precision, T, stride=7)
+    _, u0 = s0.macroscopic(s0.forward(dev([1.0]), dev([tau]), 1.0))
+    assert rel(u0.cpu().numpy(), uw) > 1e-2
+
+
+WINDOW = [(True, 8), (True, 4), (False, 8), (False, 4)]
+
+
+@pytest.mark.parametrize("wake,precision", WINDOW, ids=[f"{'wake' if w else 'pressure'}-fp{8 * p}" for w, p in WINDOW])
+def test_window_loss_gradient_matches_the_oracle(wake, precision):
+    """One reverse sweep of lbm_adjoint_window against the oracle's window
+    gradient: observations inside segments, on a segment boundary and at T."""
+    T, stride, tau = 48, 7, 0.75
+    obs = [14, 21, 33, 48]
+    if wake:
+        m = cylinder(64, 24, 16, 12.3, 6)
+        s = wake_solver(m, precision, T, stride=stride)
+        s.set_velocity_ramp(30)
+        rin = np.array([1.0])
+        opts = dict(periodic_y=True, velocity_inlet=(0.05, 0.0), ramp=30)
+        O.set_collision(O.COLL_MRT, *RATES)
+    else:
+        g = dict(kind=lbm.LBM_GEOM_DISKS, seed=12, r_min=3, r_max=5, target_porosity=0.75, inlet_buffer=4)
+        s = lbm.Solver(9, 72, 32, precision=precision, n_steps=T, ckpt_stride=stride,
+                       inlet_kind=lbm.LBM_INLET_PROFILE, geometry=g, layout="dense")
+        m = s.mask_field.cpu().numpy()
+        rin = 1.0 + W.inlet_profile(32, seed=13)
+        opts = {}
+    ut = W.perturbation((len(obs), 2) + m.shape, seed=42, scale=2e-3)
+    roi = np.ones(m.shape, np.uint8)
+    roi[:, :10] = 0
+    f = s.forward(dev(rin), dev([tau]), 1.0)
+    L, g_in, g_tau = s.adjoint_window(dev(rin), dev([tau]), 1.0, f, obs, dev(ut), dev(roi, torch.uint8))
+    assert s.status() == lbm.LBM_OK
+    with O.wake_options(**opts):
+        Lw, gw, gtw = O.gradient_window(9, m, rin if rin.size > 1 else rin[0], 1.0, tau, T, obs, ut, roi=roi,
+                                        ckpt_stride=stride)
+    tol_l, tol_g = (1e-11, 1e-9) if precision == 8 else (1e-4, 1e-3)
+    assert abs(L.item() - Lw) <= tol_l * abs(Lw)
+    assert abs(g_tau.item() - gtw) <= tol_g * abs(gtw)
+    if not wake:
+        assert rel(g_in.cpu().numpy(), gw) < tol_g
+
+
+@pytest.mark.parametrize("layout", ["dense", "compact"])
+def test_window_with_one_observation_at_T_is_the_adjoint_bit_for_bit(layout):
+    g = dict(kind=lbm.LBM_GEOM_DISKS, seed=14, r_min=3, r_max=5, target_porosity=0.75, inlet_buffer=4)
+    s = lbm.Solver(9, 72, 32, precision=4, n_steps=30, ckpt_stride=6, inlet_kind=lbm.LBM_INLET_PROFILE,
+                   geometry=g, layout=layout)
+    rin = dev(1.0 + W.inlet_profile(32, seed=15))
+    ut = dev(W.perturbation((1, 2, 32, 72), seed=16, scale=2e-3))
+    f = s.forward(rin, dev([0.8]), 1.0)
+    L, lam = s.loss_grad(f, ut[0])
+    g_in, g_tau = s.adjoint(rin, dev([0.8]), 1.0, lam)
+    Lw, g_in_w, g_tau_w = s.adjoint_window(rin, dev([0.8]), 1.0, f, [30], ut)
+    assert Lw.item() == L.item()
+    assert torch.equal(g_in_w, g_in) and torch.equal(g_tau_w, g_tau)
+
+
+def test_window_rejects_steps_outside_the_sweep():
+    s = wake_solver(cylinder(32, 16, 8, 8.3, 4), 8, 10)
+    f = s.forward(dev([1.0]), dev([0.8]), 1.0)
+    ut = dev(np.zeros((1, 2, 16, 32)))
+    for bad in ([0], [11]):
+        with pytest.raises(lbm.LBMError) as e:
+            s.adjoint_window(dev([1.0]), dev([0.8]), 1.0, f, bad, ut)
+        assert e.value.status == lbm.LBM_ERR_INVALID_ARG
