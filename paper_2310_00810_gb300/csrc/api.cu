@@ -866,7 +866,9 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
             const unsigned char* src = j == 0 ? base_of(sg) : seg(sg, j);
             const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
             void* lam_out = ws + p->ws.lam[lam_next];
-            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, bc, tau, grad_acc, partial, s_));
+            // the adjoint step at t re-forms f^t = S(g^{t-1}) at the inlet nodes: streaming level t
+            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, at_time(bc, sg * k + j), tau, grad_acc,
+                                   partial, s_));
             if (win)  // src holds g^{t-1}, t = sg k + j
                 for (int o = 0; o < win->n_obs; ++o)
                     if (win->steps[o] == sg * k + j && !at_rest) LBM_TRY(observe(o, sg * k + j, src, lam_out, s_));
