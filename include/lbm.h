@@ -187,8 +187,10 @@ LBM_API lbm_status lbm_set_velocity_inlet(lbm_plan* plan, int32_t on, double ux,
  * step producing f^t uses u_in r(t), r(t) = sin^2(pi t / (2 steps)) for
  * 0 < t < steps and 1 from steps on (steps = 0: none, the default).  Time
  * counts from the rest state of lbm_forward (lbm_step counts from its input
- * state).  The reverse sweep needs no change: the inlet's source does not
- * depend on the state.  Errors: INVALID_ARG for steps < 0. */
+ * state).  The inlet's source does not depend on the state, so no gradient
+ * flows through it; the reverse sweep re-forms f^t at inlet nodes with the
+ * same r(t) (each adjoint launch carries its step's time level).
+ * Errors: INVALID_ARG for steps < 0. */
 LBM_API lbm_status lbm_set_velocity_ramp(lbm_plan* plan, int32_t steps);
 
 /* Bytes of device workspace lbm_forward / lbm_adjoint / lbm_step /
