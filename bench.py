@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--layout", default=None, choices=[None, "dense", "compact"],
                     help="state layout for --mode kernels (default: compact for D3Q19, dense for D2Q9)")
     ap.add_argument("--launches", type=int, default=20)
+    ap.add_argument("--aa", type=int, default=0, choices=[0, 1],
+                    help="--mode kernels: the in-place (AA-pattern) schedule of the fluid-only layout")
     ap.add_argument("--no-invert", action="store_true", help="skip the time-to-1e-3 inversion leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched leg")
     ap.add_argument("--batch-instances", type=int, default=64)
@@ -779,12 +781,14 @@ HBM_TRAFFIC = {
 }
 
 
-def kernel_rooflines(device, hbm_peak, name, n_launch, layout=None):
+def kernel_rooflines(device, hbm_peak, name, n_launch, layout=None, aa=0):
     """Stream-collide and adjoint kernels alone on workload `name` (a lattice
     larger than L2 for the HBM roofline) in the given state layout: CUDA
     events around n_launch back-to-back launches of each.  Algorithmic bytes
     count fluid nodes: 2 Q s per stream-collide update, 3 Q s per adjoint
-    update, plus the 4-byte link word of every node."""
+    update, plus the 4-byte link word of every node.  aa = 1: the in-place
+    schedule of the fluid-only layout (its gather and local steps alternate;
+    the times are their average)."""
     import torch
 
     from paper_2310_00810_gb300 import lbm
@@ -795,6 +799,8 @@ def kernel_rooflines(device, hbm_peak, name, n_launch, layout=None):
                    geometry=dict(kind=wl.geom_kind, seed=wl.seed, r_min=wl.r_min, r_max=wl.r_max,
                                  target_porosity=wl.porosity), device=device, layout=layout)
     nf, N, q, sz = int(s.info[3].item()), wl.nodes, wl.q, wl.precision
+    if aa:
+        s.set_kernels(**dict(lbm.lbm_plan_get_kernels(s.plan), aa=1))
     rho_in = torch.tensor([1.001], dtype=torch.float64, device=device)
     tau = torch.tensor([wl.tau], dtype=torch.float64, device=device)
     a = s.new_state().zero_()
@@ -825,8 +831,9 @@ def kernel_rooflines(device, hbm_peak, name, n_launch, layout=None):
     for kern, t, per in (("stream-collide", t_sc, 2 * q * sz), ("adjoint", t_adj, 3 * q * sz)):
         byts = per * nf + 4 * N
         ach = byts / t / 1e9
-        tr = HBM_TRAFFIC.get((name, s.layout), {}).get(kern)
-        out[kern] = {"bound": "hbm", "kernel": f"{kern} on {name} ({s.layout} layout)", "achieved": round(ach, 1),
+        tr = None if aa else HBM_TRAFFIC.get((name, s.layout), {}).get(kern)
+        sched = ", in place" if aa and s.layout == "compact" else ""
+        out[kern] = {"bound": "hbm", "kernel": f"{kern} on {name} ({s.layout} layout{sched})", "achieved": round(ach, 1),
                      "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
                      "frac_of_nominal_8tbs": round(ach / 8000.0, 4),
                      "traffic": round(tr) if tr else None, "bytes_per_launch": byts,
@@ -941,7 +948,9 @@ def run_kernels(args):
     hbm_peak = json.load(open(peaks))["hbm_gbs"] if os.path.exists(peaks) else 6800.0
     print(json.dumps({"mode": "kernels", "lattice": args.lattice,
                       "layout": args.layout,
-                      "kernels": kernel_rooflines(device, hbm_peak, args.lattice, args.launches, args.layout)}),
+                      "aa": args.aa,
+                      "kernels": kernel_rooflines(device, hbm_peak, args.lattice, args.launches, args.layout,
+                                                  args.aa)}),
           flush=True)
 
 

@@ -123,6 +123,17 @@ typedef struct lbm_kernel_choice {
     int32_t steps_per_launch; /* 1, or 2: two stream-collide steps per launch (temporal blocking: a tile plus a
                                  two-node halo in shared memory) where the dense D2Q9 FP32 TMA kernels apply,
                                  in the forward sweep, the segment recompute and lbm_step; 0 reads as 1 */
+    int32_t aa;              /* 1: in-place (AA-pattern) streaming in the fluid-only layout (the dense layout
+                                ignores it).  The forward sweep and lbm_step advance one state buffer in place
+                                and the reverse sweep updates lambda in place: a step from a state stored in
+                                its natural layout gathers through the neighbour table and writes the swapped
+                                layout, the next step reads and writes each node's own slots (no table), so
+                                every other step moves no table bytes.  Checkpoints and segment states keep
+                                one buffer each, as before.  The workspace loses one forward and one adjoint
+                                state (re-query lbm_workspace_size after a change: it grows back when aa is
+                                cleared).  Results equal those of the two-buffer pull.  lbm_adjoint needs the
+                                checkpoints of an lbm_forward run with the same setting (else INVALID_ARG).
+                                Not with LBM_ABB_U_EXTRAP (the sweeps return UNSUPPORTED). */
 } lbm_kernel_choice;
 
 /* Sets / reads the plan's kernel choice (an autotuner's knob).  Cached CUDA

@@ -5,7 +5,8 @@ the candidate kernel families of the stream-collide and adjoint steps in the
 dense layout — TMA staging with 8- or 4-row tiles, register kernels with 4 or
 2 nodes per thread, one node per thread — then programmatic dependent launch
 on/off and the one-launch persistent sweeps, the overlapped reverse sweep (recompute on a second stream) on/off,
-two stream-collide steps per launch (D2Q9 FP32), then the fluid-only (compact) layout, and keeps the fastest.  Only the speed differs between candidates;
+two stream-collide steps per launch (D2Q9 FP32), then the fluid-only (compact) layout with two-buffer or
+in-place streaming, and keeps the fastest.  Only the speed differs between candidates;
 every family and layout computes the same step.  Results are cached in JSON
 keyed by GPU name, Q, precision, lattice size and inlet kind.
 
@@ -179,9 +180,17 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
     tp.set_layout("compact")
     if tp.layout == "compact":
         for pdl in (1, 0):
-            c = dict(best, pdl=pdl, persist=0, overlap=1)
+            c = dict(best, pdl=pdl, persist=0, overlap=1, steps_per_launch=1, aa=0)
             t = time_sweeps(c)
             timings[f"sweep:compact,pdl={pdl}"] = round(t * 1e6, 3)
+            if t < best_t:
+                best, best_t, layout = c, t, "compact"
+        if not solver_uw_extrap(solver):
+            # in-place streaming (one state buffer; every other step reads no table)
+            base = best if layout == "compact" else dict(best, persist=0, overlap=1, steps_per_launch=1)
+            c = dict(base, aa=1)
+            t = time_sweeps(c)
+            timings["sweep:compact,in_place"] = round(t * 1e6, 3)
             if t < best_t:
                 best, best_t, layout = c, t, "compact"
     result = {"choice": best, "layout": layout, "timings_us": timings, "us_per_time_step": round(best_t * 1e6, 3),
@@ -194,9 +203,17 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
     return dict(result, cached=False)
 
 
+def solver_uw_extrap(solver: lbm.Solver) -> bool:
+    """Whether the plan's Eq. 6 takes the extrapolated wall velocity (the in-place schedule does not)."""
+    return lbm.lbm_get_abb_velocity(solver.plan) == lbm.LBM_ABB_U_EXTRAP
+
+
 def _apply(solver: lbm.Solver, result: dict) -> None:
     solver.set_layout(result.get("layout", "dense"))
-    lbm.lbm_plan_set_kernels(solver.plan, **result["choice"])
+    choice = dict(result["choice"])
+    if solver_uw_extrap(solver):
+        choice["aa"] = 0
+    solver.set_kernels(**choice)
 
 
 def _batch_key(b) -> str:

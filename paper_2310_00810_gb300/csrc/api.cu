@@ -73,6 +73,7 @@ struct lbm_plan {
     size_t dense_state_bytes = 0;  // Q N precision: the caller's state arrays
     int dense_n_partial = 0;       // FP64 partial slots of the dense kernels
     void* last_ws = nullptr;
+    int fwd_aa = -1;               // schedule of the last lbm_forward (1: in place): its checkpoints' layouts
     bool use_graphs = true;
     std::vector<GraphEntry> graphs;  // most recently used last
     // second stream and events of the overlapped reverse sweep (created on first use)
@@ -92,6 +93,10 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The in-place (AA-pattern) schedule runs where it is chosen and the plan
+// is in the fluid-only layout.
+bool in_place(const lbm_plan* p) { return p->info.aa && p->info.cmp.nf; }
+
 void layout(lbm_plan* p)
 {
     const size_t st = align256(p->info.state_bytes);
@@ -107,18 +112,22 @@ void layout(lbm_plan* p)
     o += align256(sizeof(double) * (size_t)p->info.n_partial);
     w.partial2 = o;
     o += align256(sizeof(double) * (size_t)p->info.n_blocks);
-    for (int i = 0; i < 2; ++i) {
-        w.ping[i] = o;
-        o += st;
-    }
-    for (int i = 0; i < 2; ++i) {
-        w.lam[i] = o;
-        o += st;
-    }
+    w.side = o;
+    o += align256((size_t)p->info.prec * 3 * 2 * (size_t)p->info.n_acc);
+    w.ping[0] = o;
+    o += st;
+    w.lam[1] = o;
+    o += st;
     w.ckpt = o;
     o += st * (size_t)(p->S - 1);
     w.seg = o;
     o += st * (size_t)p->k * 2;
+    // the second forward and adjoint buffers last: the in-place schedule has none
+    const bool one = in_place(p);
+    w.ping[1] = o;
+    o += one ? 0 : st;
+    w.lam[0] = o;
+    o += one ? 0 : st;
     w.total = o;
 }
 
@@ -155,10 +164,13 @@ lbm_status write_mrt_rates(const lbm_plan* p, const Bc& bc, cudaStream_t s)
     return cuda_status(cudaGetLastError());
 }
 
-// The periodic-y and velocity-inlet options exist in the fluid-only layout only.
+// The periodic-y and velocity-inlet options exist in the fluid-only layout
+// only; the in-place schedule keeps no neighbour velocity for the
+// extrapolated Eq. 6 velocity.
 lbm_status check_layout_options(const lbm_plan* p)
 {
     if ((p->info.geo.periodic_y || p->info.vel_inlet) && !p->info.cmp.nf) return LBM_ERR_UNSUPPORTED;
+    if (in_place(p) && p->info.uw_extrap) return LBM_ERR_UNSUPPORTED;
     return LBM_OK;
 }
 
@@ -253,11 +265,21 @@ void set_dense(lbm_plan* p)
 // writes fluid nodes only, and the dense kernels skip 32-byte sectors that
 // hold only solid nodes.
 lbm_status final_stream(const lbm_plan* p, const void* cur, void* d_f, const Bc& bc, const double* tau,
-                        cudaStream_t s)
+                        cudaStream_t s, int lin = kLayoutNatural)
 {
     if (cudaMemsetAsync(d_f, 0, p->dense_state_bytes, s) != cudaSuccess) return LBM_ERR_CUDA;
     if (!p->info.cmp.nf) return step_launch(p->info, kStreamOnly, cur, d_f, bc, tau, s);
-    return step_launch_cmp(p->info, kStreamOnly, cur, d_f, false, true, bc, tau, s);
+    return step_launch_cmp(p->info, kStreamOnly, cur, d_f, false, true, bc, tau, s, lin);
+}
+
+// One stream-collide launch of a sweep producing g^t from g^{t-1}: the
+// plan's kernels, or the in-place pair (src and dst may be one buffer).
+lbm_status sweep_step(const lbm_plan* p, const void* src, void* dst, const Bc& bc, int t, const double* tau,
+                      cudaStream_t s)
+{
+    if (!in_place(p)) return step_launch(p->info, kStreamCollide, src, dst, at_time(bc, t), tau, s);
+    return step_launch_cmp(p->info, kStreamCollide, src, dst, false, false, at_time(bc, t), tau, s,
+                           layout_at(true, t - 1), layout_at(true, t));
 }
 
 // Issues `issue(s)` through a cached CUDA graph when that is possible.
@@ -403,7 +425,7 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
         (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1) ||
         (k->overlap != 0 && k->overlap != 1) ||
         (k->adjoint_tma_rows != 0 && k->adjoint_tma_rows != 4 && k->adjoint_tma_rows != 8) ||
-        k->steps_per_launch < 0 || k->steps_per_launch > 2)
+        k->steps_per_launch < 0 || k->steps_per_launch > 2 || (k->aa != 0 && k->aa != 1))
         return LBM_ERR_INVALID_ARG;
     PlanInfo& I = p->info;
     I.step_family = k->step_family;
@@ -417,6 +439,8 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
     I.pdl = k->pdl;
     I.use_persist = k->persist;
     I.overlap = k->overlap;
+    I.aa = k->aa;
+    layout(p);  // the in-place schedule needs one forward and one adjoint buffer
     drop_graphs(p);
     return LBM_OK;
 }
@@ -434,6 +458,7 @@ lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
     k->pdl = I.pdl;
     k->persist = I.use_persist;
     k->overlap = I.overlap;
+    k->aa = I.aa;
     return LBM_OK;
 }
 
@@ -604,13 +629,18 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
         if (T == 1) return step_launch(p->info, kStreamOnly, g0, d_f, bc, tau, s);
         return forward_persist(p->info, a, bc, tau, s);
     }
-    // the state chain g^0 .. g^{T-1}: checkpoint slots where the reverse sweep needs them, else ping-pong;
-    // with two steps per launch, g^t of a pair is written only where it is a checkpoint
+    // the state chain g^0 .. g^{T-1}: checkpoint slots where the reverse sweep needs them, else ping-pong
+    // (in place: ping0 alone, g^t in the layout of its parity); with two steps per launch, g^t of a pair is
+    // written only where it is a checkpoint
+    const bool one = in_place(p);
+    p->fwd_aa = one ? 1 : 0;
+    Bc bcs = bc;
+    if (one) bcs.side_u = ws + p->ws.side;  // the Eq. 6 nodes' velocities, carried from step to step
     auto next_state = [&](int t, const unsigned char* cur) -> unsigned char* {
         unsigned char* dst = slot(t);
-        return dst ? dst : (cur == ping0 ? ping1 : ping0);
+        return dst ? dst : (one ? ping0 : (cur == ping0 ? ping1 : ping0));
     };
-    const bool pairs = step2_possible(p->info, bc);
+    const bool pairs = !one && step2_possible(p->info, bc);
     // walks the chain, calling launch(src, two, mid, dst) once per launch: two steps (mid: g^t where it is a
     // checkpoint, else nullptr) or one
     using Launch = std::function<lbm_status(const unsigned char*, bool, unsigned char*, unsigned char*, int)>;
@@ -634,12 +664,15 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         LBM_TRY(write_mrt_rates(p, bc, st_));
         if (cudaMemsetAsync(g0, 0, p->info.state_bytes, st_) != cudaSuccess) return LBM_ERR_CUDA;  // g^0 = rest
+        if (one && cudaMemsetAsync(bcs.side_u, 0, (size_t)p->info.prec * 6 * (size_t)p->info.n_acc, st_) !=
+                       cudaSuccess)
+            return LBM_ERR_CUDA;  // at rest every velocity is zero
         unsigned char* end = nullptr;
         return chain(
             [&](const unsigned char* src, bool two, unsigned char* mid, unsigned char* dst, int t) -> lbm_status {
                 // the launch producing g^t streams into time level t (the velocity inlet's ramp)
                 return two ? step2_launch(p->info, src, mid, dst, at_time(bc, t), tau, st_)
-                           : step_launch(p->info, kStreamCollide, src, dst, at_time(bc, t), tau, st_);
+                           : sweep_step(p, src, dst, bcs, t, tau, st_);
             },
             g0, &end);
     };
@@ -649,7 +682,8 @@ lbm_status lbm_forward(lbm_plan* p, const double* d_rho_in, const double* d_tau,
     key.ptr[1] = p->link;
     key.scalar = rho_out;
     LBM_TRY(run_sequence(p, key, s, issue));
-    return final_stream(p, last, d_f, at_time(bc, T), tau, s);  // f^T = S(g^{T-1}) into the caller's array
+    // f^T = S(g^{T-1}) into the caller's array
+    return final_stream(p, last, d_f, at_time(bc, T), tau, s, layout_at(one, T - 1));
 }
 
 lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, double rho_out, const void* d_f_in,
@@ -667,26 +701,29 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
     unsigned char* ping0 = ws + p->ws.ping[0];
     unsigned char* ping1 = ws + p->ws.ping[1];
     // collide the caller's state into ping0, n - 1 stream-collide launches between the ping-pong
-    // buffers (the cached part), then stream into the caller's output
+    // buffers (in place: on ping0 alone) as the cached part, then stream into the caller's output
+    const bool one = in_place(p);
+    Bc bcs = bc;
+    if (one) bcs.side_u = ws + p->ws.side;  // the collide-only launch writes the Eq. 6 nodes' velocities
     LBM_TRY(write_mrt_rates(p, bc, s));
     if (p->info.cmp.nf)
-        LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bc, tau, s));
+        LBM_TRY(step_launch_cmp(p->info, kCollideOnly, d_f_in, ping0, true, false, bcs, tau, s));
     else
         LBM_TRY(step_launch(p->info, kCollideOnly, d_f_in, ping0, bc, tau, s));
-    // n - 1 stream-collide steps between the ping-pong buffers, two per launch where the two-step kernel applies
-    const bool pairs = step2_possible(p->info, bc);
+    // n - 1 stream-collide steps, two per launch where the two-step kernel applies
+    const bool pairs = !one && step2_possible(p->info, bc);
     const int launches = pairs ? n_steps / 2 : n_steps - 1;  // (n - 1) / 2 pairs and (n - 1) % 2 single steps
-    unsigned char* last = launches % 2 == 0 ? ping0 : ping1;
+    unsigned char* last = one || launches % 2 == 0 ? ping0 : ping1;
     auto issue = [&](cudaStream_t st_) -> lbm_status {
         unsigned char* cur = ping0;
         int t = 1;
         while (t < n_steps) {
-            unsigned char* dst = cur == ping0 ? ping1 : ping0;
+            unsigned char* dst = one ? ping0 : (cur == ping0 ? ping1 : ping0);
             if (pairs && t + 1 < n_steps) {
                 LBM_TRY(step2_launch(p->info, cur, nullptr, dst, at_time(bc, t), tau, st_));
                 t += 2;
             } else {
-                LBM_TRY(step_launch(p->info, kStreamCollide, cur, dst, at_time(bc, t), tau, st_));
+                LBM_TRY(sweep_step(p, cur, dst, bcs, t, tau, st_));
                 t += 1;
             }
             cur = dst;
@@ -704,7 +741,7 @@ lbm_status lbm_step(lbm_plan* p, const double* d_rho_in, const double* d_tau, do
         key.n = n_steps;
         LBM_TRY(run_sequence(p, key, s, issue));
     }
-    return final_stream(p, last, d_f_out, at_time(bc, n_steps), tau, s);
+    return final_stream(p, last, d_f_out, at_time(bc, n_steps), tau, s, layout_at(one, n_steps - 1));
 }
 
 lbm_status lbm_loss_grad(lbm_plan* p, const void* d_f, const double* d_u_target, const uint8_t* d_roi,
@@ -794,6 +831,8 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
     LBM_TRY(stage_inputs(p, d_ws, d_rho_in, d_tau, &rho_in, &tau, s));
     const Bc bc = make_bc(p, rho_in, rho_out, d_ws);
     const int T = p->desc.n_steps, k = p->k, S = p->S;
+    // the checkpoints must come from a forward sweep of the same schedule (their layouts differ)
+    if (p->fwd_aa >= 0 && p->fwd_aa != (in_place(p) ? 1 : 0)) return LBM_ERR_INVALID_ARG;
     const size_t st = align256(p->info.state_bytes);
     double* grad_acc = reinterpret_cast<double*>(ws + p->ws.grad_acc);
     double* partial = reinterpret_cast<double*>(ws + p->ws.partial);
@@ -817,7 +856,10 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
     auto base_of = [&](int sg) -> const unsigned char* {
         return sg >= 1 ? ws + p->ws.ckpt + st * (size_t)(sg - 1) : nullptr;
     };
-    const bool pairs = step2_possible(p->info, bc);
+    // in place: g^t and lambda^t in the layout of t's parity, lambda updated in place in lam[1]; the
+    // recomputed segment states are written out of place, so they read the Eq. 6 velocities from their input
+    const bool one = in_place(p);
+    const bool pairs = !one && step2_possible(p->info, bc);
     auto recompute = [&](int sg, cudaStream_t s_) -> lbm_status {
         const int len = std::min(k, T - sg * k);
         const unsigned char* prev = base_of(sg);
@@ -833,7 +875,7 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
                 prev = seg(sg, j + 1);
                 j += 2;
             } else {  // seg(sg, j) holds g^{sg k + j - 1}
-                LBM_TRY(step_launch(p->info, kStreamCollide, prev, seg(sg, j), at_time(bc, sg * k + j - 1), tau, s_));
+                LBM_TRY(sweep_step(p, prev, seg(sg, j), bc, sg * k + j - 1, tau, s_));
                 prev = seg(sg, j);
                 j += 1;
             }
@@ -850,14 +892,14 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
     auto observe = [&](int o, int t, const unsigned char* src, void* lam, cudaStream_t s_) -> lbm_status {
         const void* ft = win->f_T;
         if (t < T) {
-            LBM_TRY(final_stream(p, src, win->scr_f, at_time(bc, t), tau, s_));
+            LBM_TRY(final_stream(p, src, win->scr_f, at_time(bc, t), tau, s_, layout_at(one, t - 1)));
             ft = win->scr_f;
         }
         const size_t dn = (size_t)p->info.d * (size_t)p->info.geo.N;
         LBM_TRY(loss_launch(p->info, ft, win->targets + (size_t)o * dn, win->roi, p->desc.loss_kind,
                             p->desc.loss_norm, loss_tmp, win->scr_lam, ws, p->ws, s_));
         LBM_TRY(accumulate_launch(win->d_loss, loss_tmp, s_));
-        return p->info.cmp.nf ? compact_gather_add_launch(p->info, win->scr_lam, lam, s_)
+        return p->info.cmp.nf ? compact_gather_add_launch(p->info, win->scr_lam, lam, s_, layout_at(one, t))
                               : add_state_launch(p->info, lam, win->scr_lam, s_);
     };
     auto adjoint_steps = [&](int sg, cudaStream_t s_) -> lbm_status {
@@ -865,10 +907,15 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
         for (int j = len - 1; j >= 0; --j) {
             const unsigned char* src = j == 0 ? base_of(sg) : seg(sg, j);
             const int at_rest = (sg == 0 && j == 0) ? 1 : 0;
-            void* lam_out = ws + p->ws.lam[lam_next];
+            const int t = sg * k + j;
+            void* lam_out = one ? lam_T : ws + p->ws.lam[lam_next];
             // the adjoint step at t re-forms f^t = S(g^{t-1}) at the inlet nodes: streaming level t
-            LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, at_time(bc, sg * k + j), tau, grad_acc,
-                                   partial, s_));
+            if (one)
+                LBM_TRY(adjoint_launch_cmp(p->info, at_rest, src, lam_cur, lam_out, at_time(bc, t), tau, grad_acc,
+                                           partial, s_, layout_at(true, t - 1), layout_at(true, t)));
+            else
+                LBM_TRY(adjoint_launch(p->info, at_rest, src, lam_cur, lam_out, at_time(bc, t), tau, grad_acc,
+                                       partial, s_));
             if (win)  // src holds g^{t-1}, t = sg k + j
                 for (int o = 0; o < win->n_obs; ++o)
                     if (win->steps[o] == sg * k + j && !at_rest) LBM_TRY(observe(o, sg * k + j, src, lam_out, s_));
@@ -891,7 +938,7 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
         for (int o = 0; o < win->n_obs; ++o)
             if (win->steps[o] == T) LBM_TRY(observe(o, T, nullptr, lam_T, s));
     } else if (p->info.cmp.nf) {  // lambda^T into the compact layout
-        LBM_TRY(compact_gather_launch(p->info, d_lambda, lam_T, s));
+        LBM_TRY(compact_gather_launch(p->info, d_lambda, lam_T, s, layout_at(one, T)));
     } else if (cudaMemcpyAsync(lam_T, d_lambda, p->dense_state_bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
         return LBM_ERR_CUDA;
     }

@@ -813,7 +813,8 @@ lbm_status lbm_batch_compact_size(const lbm_batch* b, const int64_t* n_fluid, si
         nfp += (n_fluid[i] + kBatchCmpAlign - 1) / kBatchCmpAlign * kBatchCmpAlign;
     }
     *bytes = al256(sizeof(BCmpInst) * (size_t)b->n) + al256(sizeof(int) * (size_t)(nfp / kBatchCmpAlign)) +
-             al256(sizeof(int32_t) * (size_t)nfp) + al256(sizeof(int32_t) * (size_t)(b->q - 1) * (size_t)nfp);
+             al256(sizeof(int32_t) * (size_t)nfp) + al256(sizeof(int32_t) * (size_t)(b->q - 1) * (size_t)nfp) +
+             al256(sizeof(uint32_t) * (size_t)(nfp / 32));
     return LBM_OK;
 }
 
@@ -851,6 +852,8 @@ lbm_status lbm_batch_compact_bind(lbm_batch* b, const int64_t* n_fluid, void* d_
     const size_t t_nbr = t_idx + al256(sizeof(int32_t) * (size_t)nfp);
     int32_t* idx = reinterpret_cast<int32_t*>(tb + t_idx);
     int32_t* nbr = reinterpret_cast<int32_t*>(tb + t_nbr);
+    const size_t t_eq6 = t_nbr + al256(sizeof(int32_t) * (size_t)(b->q - 1) * (size_t)nfp);
+    uint32_t* eq6 = reinterpret_cast<uint32_t*>(tb + t_eq6);
     std::vector<int> blk((size_t)(nfp / kBatchCmpAlign));
     // each instance's tables are built in the workspace's state buffers (free at this point), then
     // packed; compact_build checks the fluid count against the link words (and synchronises)
@@ -874,6 +877,10 @@ lbm_status lbm_batch_compact_bind(lbm_batch* b, const int64_t* n_fluid, void* d_
         for (long long bl = c.k0 / kBatchCmpAlign; bl < (c.k0 + c.nf + kBatchCmpAlign - 1) / kBatchCmpAlign; ++bl)
             blk[(size_t)bl] = i;
     }
+    {
+        const lbm_status st = eq6_bits_launch_cmp(b->q, nbr, nfp, eq6, s);  // padding nodes: bounce-back, bit 0
+        if (st != LBM_OK) return st;
+    }
     if (cudaMemcpyAsync(tb + t_insts, ci.data(), sizeof(BCmpInst) * ci.size(), cudaMemcpyHostToDevice, s) !=
             cudaSuccess ||
         (!blk.empty() &&
@@ -885,7 +892,7 @@ lbm_status lbm_batch_compact_bind(lbm_batch* b, const int64_t* n_fluid, void* d_
     b->nfp = nfp;
     b->cmp_state_bytes = (size_t)b->q * (size_t)nfp * (size_t)b->prec;
     BCmpArgs& a = b->ca;
-    a.c = Cmp{nfp, idx, nbr};
+    a.c = Cmp{nfp, idx, nbr, eq6};
     a.insts = reinterpret_cast<const BCmpInst*>(tb + t_insts);
     a.blk_inst = reinterpret_cast<const int*>(tb + t_blk);
     a.n_blocks = (unsigned)(nfp / kBatchCmpAlign);

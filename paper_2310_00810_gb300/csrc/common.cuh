@@ -25,8 +25,9 @@ struct Workspace {
     size_t grad_acc;    // double[n_acc]   per-inlet-node dL/drho_w accumulators
     size_t partial;     // double[n_blocks] per-block dL/domega accumulators
     size_t partial2;    // double[n_blocks] per-block loss / count partials
-    size_t ping[2];     // forward ping-pong states
-    size_t lam[2];      // adjoint ping-pong states
+    size_t side;        // in-place schedule: velocity of each Eq. 6 node's last output (2 ny nz x 3, plan precision)
+    size_t ping[2];     // forward ping-pong states (the in-place schedule uses ping[0] only)
+    size_t lam[2];      // adjoint ping-pong states (the in-place schedule uses lam[1] only)
     size_t ckpt;        // (S - 1) checkpoint states, slot s (1..S-1) at index s - 1
     size_t seg;         // two buffers of k segment states
     size_t total;
@@ -52,6 +53,7 @@ struct Bc {
     char test_stall = 0;   // 1: TMA producers issue no copies, so every consumer wait runs out (tests only)
     int t_level = 0;       // the time level this launch's streaming produces (f^t_level)
     int ramp_steps = 0;    // the velocity inlet starts gradually: u_in r(t_level), r = 1 from ramp_steps on
+    void* side_u = nullptr;  // in-place forward steps: the Eq. 6 nodes' velocities (read, then rewritten)
 };
 
 // The gradual start of the velocity inlet: r(t) = sin^2(pi t / (2 R)) for
@@ -79,6 +81,7 @@ struct Cmp {
     long long nf;          // fluid nodes stored
     const int32_t* idx;    // idx[k]: dense node index of compact node k (increasing)
     const int32_t* nbr;    // nbr[(i - 1) * nf + k], i = 1..Q-1: compact index of x - c_i, or kCmpBB / kCmpABB
+    const uint32_t* eq6;   // bit k & 31 of eq6[k >> 5]: node k has an Eq. 6 / velocity-inlet link
 };
 
 struct BCmpInst;
@@ -105,6 +108,7 @@ struct PlanInfo {
     int steps2;       // 1: two stream-collide steps per launch where the two-step kernel applies
     int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes
     int overlap;      // 1: reverse sweep recomputes the next segment on a second stream during the adjoint steps
+    int aa;           // 1: in-place (AA-pattern) streaming in the fluid-only layout
     int uw_extrap;    // 1: Eq. 6 with the extrapolated wall velocity (one-node-per-thread or fluid-only kernels)
     int mrt;          // 1: D2Q9 MRT collision (one-node-per-thread or fluid-only kernels)
     int vel_inlet;    // 1: velocity inlet instead of Eq. 6 at x = -1/2 (fluid-only kernels)
@@ -302,14 +306,30 @@ lbm_status badjoint_launch_cmp(const BCmpArgs& a, int t0, const void* gprev, con
 lbm_status bgather_launch_cmp(const BCmpArgs& a, const void* dense, void* compact, cudaStream_t s);
 lbm_status bpack_launch_cmp(const Cmp& local, int q, long long k0, long long nfp, int32_t* idx, int32_t* nbr,
                             cudaStream_t s);
+// the per-node Eq. 6 bit array of a (packed) table: bit k & 31 of bits[k >> 5]
+lbm_status eq6_bits_launch_cmp(int q, const int32_t* nbr, long long nf, uint32_t* bits, cudaStream_t s);
 lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out, const int32_t** cmap_out,
                          const BCmpInst** inst_out, cudaStream_t s);
+// Layouts of a fluid-only state (compact.cu): natural, or swapped (the
+// in-place schedule's layout of g^t and lambda^t at odd t).
+constexpr int kLayoutNatural = 0;
+constexpr int kLayoutSwapped = 1;
+// The layout of g^t (and lambda^t) in a sweep of the in-place schedule.
+inline int layout_at(bool aa, long long t) { return aa && (t & 1) ? kLayoutSwapped : kLayoutNatural; }
+// lin / lout: layouts of the input and output states (stream-collide: natural -> natural is the two-buffer pull,
+// natural -> swapped and swapped -> natural the in-place pair; stream-only into the caller's array: any lin)
 lbm_status step_launch_cmp(const PlanInfo& p, int mode, const void* src, void* dst, bool dense_in, bool dense_out,
-                           const Bc& bc, const double* tau, cudaStream_t s);
+                           const Bc& bc, const double* tau, cudaStream_t s, int lin = kLayoutNatural,
+                           int lout = kLayoutNatural);
+// lin: layout of g^{t-1} and lambda^{t+1}; lout: of lambda^t (as for the step)
 lbm_status adjoint_launch_cmp(const PlanInfo& p, int t0, const void* gprev, const void* lam_in, void* lam_out,
-                              const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s);
-lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s);
-lbm_status compact_gather_add_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s);
+                              const Bc& bc, const double* tau, double* grad_acc, double* partial, cudaStream_t s,
+                              int lin = kLayoutNatural, int lout = kLayoutNatural);
+// the caller's dense array into a compact state (lambda's layouts: swapped puts lambda_d(x) at (x - c_d, opp(d)))
+lbm_status compact_gather_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s,
+                                 int layout = kLayoutNatural);
+lbm_status compact_gather_add_launch(const PlanInfo& p, const void* dense, void* compact, cudaStream_t s,
+                                     int layout = kLayoutNatural);
 lbm_status add_state_launch(const PlanInfo& p, void* dst, const void* src, cudaStream_t s);
 lbm_status accumulate_launch(double* dst, const double* src, cudaStream_t s);
 

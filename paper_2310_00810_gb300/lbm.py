@@ -54,7 +54,7 @@ class lbm_desc(C.Structure):
 class lbm_kernel_choice(C.Structure):
     _fields_ = [("step_family", C.c_int32), ("adjoint_family", C.c_int32), ("vec", C.c_int32),
                 ("tma_rows", C.c_int32), ("pdl", C.c_int32), ("persist", C.c_int32), ("overlap", C.c_int32),
-                ("adjoint_tma_rows", C.c_int32), ("steps_per_launch", C.c_int32)]
+                ("adjoint_tma_rows", C.c_int32), ("steps_per_launch", C.c_int32), ("aa", C.c_int32)]
 
 
 class lbm_geom_desc(C.Structure):
@@ -218,9 +218,10 @@ def lbm_plan_destroy(plan: Plan) -> None:
 
 
 def lbm_plan_set_kernels(plan: Plan, step_family=LBM_FAMILY_AUTO, adjoint_family=LBM_FAMILY_AUTO, vec=4,
-                         tma_rows=8, pdl=1, persist=0, overlap=1, adjoint_tma_rows=0, steps_per_launch=1) -> None:
+                         tma_rows=8, pdl=1, persist=0, overlap=1, adjoint_tma_rows=0, steps_per_launch=1,
+                         aa=0) -> None:
     k = lbm_kernel_choice(step_family, adjoint_family, vec, tma_rows, pdl, persist, overlap, adjoint_tma_rows,
-                          steps_per_launch)
+                          steps_per_launch, aa)
     _check(load().lbm_plan_set_kernels(plan.handle, C.byref(k)), "lbm_plan_set_kernels")
 
 
@@ -509,13 +510,26 @@ class Solver:
     def new_state(self) -> torch.Tensor:
         return torch.empty((self.plan.q, *self.plan.shape), dtype=self.plan.dtype, device=self.device)
 
+    def set_kernels(self, **choice) -> None:
+        """lbm_plan_set_kernels, then a larger workspace where the choice needs one."""
+        lbm_plan_set_kernels(self.plan, **choice)
+        self._fit_ws()
+
+    def _fit_ws(self) -> None:
+        # clearing the in-place schedule (aa) after the workspace was sized for it grows the need by two states
+        need = lbm_workspace_size(self.plan)
+        if need > self.ws.numel():
+            self.ws = torch.zeros(need, dtype=torch.uint8, device=self.device)
+
     def forward(self, rho_in, tau, rho_out, f=None):
         f = self.new_state() if f is None else f
+        self._fit_ws()
         self.run(lambda: lbm_forward(self.plan, rho_in, tau, rho_out, f, self.ws))
         return f
 
     def step(self, rho_in, tau, rho_out, f_in, n_steps, f_out=None):
         f_out = torch.empty_like(f_in) if f_out is None else f_out
+        self._fit_ws()
         self.run(lambda: lbm_step(self.plan, rho_in, tau, rho_out, f_in, f_out, n_steps, self.ws))
         return f_out
 
