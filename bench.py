@@ -54,6 +54,8 @@ def parse():
                     help="kernels: time the stream-collide and adjoint kernels alone on --lattice; "
                          "unet: training throughput of the learned initialiser")
     ap.add_argument("--unet-batch", type=int, default=16)
+    ap.add_argument("--unet-engine", default="tcgen05", choices=["tcgen05", "mma_sync"],
+                    help="--mode unet: the convolutions' GEMM engine")
     ap.add_argument("--lattice", default="disks8192x4096", help="workload name for --mode kernels")
     ap.add_argument("--layout", default=None, choices=[None, "dense", "compact"],
                     help="state layout for --mode kernels (default: compact for D3Q19, dense for D2Q9)")
@@ -973,6 +975,7 @@ def run_unet(args):
     build.build()
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
+    N.unet_set_engine(N.ENGINE_TCGEN05 if args.unet_engine == "tcgen05" else N.ENGINE_MMA_SYNC)
     B, H, W, base = args.unet_batch, 128, 256, 32
     net = N.UNet(base=base, height=H, width=W, batch=B, seed=1, device=device)
     r = np.random.Generator(np.random.PCG64(2))
@@ -995,7 +998,8 @@ def run_unet(args):
     flops = 3 * unet_flops_per_sample(base, H, W) * B * args.steps
     peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak = json.load(open(peaks))["bf16_tflops"] if os.path.exists(peaks) else 1900.0
-    print(json.dumps({"mode": "unet", "samples_per_s": round(B * args.steps / dt, 1),
+    print(json.dumps({"mode": "unet", "engine": args.unet_engine, "status": N.unet_get_status(),
+                      "samples_per_s": round(B * args.steps / dt, 1),
                       "ms_per_step": round(dt / args.steps * 1e3, 3), "tflops": round(flops / dt / 1e12, 2),
                       "bf16_peak_tflops": peak, "frac": round(flops / dt / 1e12 / peak, 4),
                       "flops_per_sample_forward": unet_flops_per_sample(base, H, W)}), flush=True)

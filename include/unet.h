@@ -45,6 +45,24 @@ typedef struct unet_desc {
 
 #define UNET_IN_CHANNELS 8
 
+/* The GEMM engine of the convolutions (process-wide).  UNET_ENGINE_TCGEN05
+ * (default): the 3x3 convolutions, their input gradients and the transposed
+ * convolutions' forward products run on the Blackwell tensor cores
+ * (tcgen05.mma, BF16 operands staged by TMA in shared memory, FP32
+ * accumulator in tensor memory) where the level's width is a multiple of 16,
+ * its height of 8, the gathered channel count 32 or a multiple of 64 and the
+ * output channel count a multiple of 32; the other products, and every
+ * product with UNET_ENGINE_MMA_SYNC, run the mma.sync kernel.  Both engines
+ * accumulate in FP32 over the same terms (in different orders).
+ * Errors: INVALID_ARG for an unknown engine. */
+enum { UNET_ENGINE_MMA_SYNC = 0, UNET_ENGINE_TCGEN05 = 1 };
+LBM_API lbm_status unet_set_engine(int32_t engine);
+
+/* LBM_OK, or LBM_ERR_TIMEOUT if a bounded wait of a tensor-core kernel gave
+ * up since the last call (the kernel then skipped its output); clears the
+ * flag.  Synchronises the device. */
+LBM_API lbm_status unet_get_status(void);
+
 /* Number of FP32 parameters, and the offset and element count of parameter
  * tensor i (i = 0..n_tensors-1, the order: enc0a.w, enc0a.b, enc0b.w, enc0b.b,
  * ..., enc3b.b, up2.w, up2.b, dec2a.w, dec2a.b, dec2b.w, dec2b.b, up1..., dec0b.b,

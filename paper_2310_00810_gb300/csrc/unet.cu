@@ -25,6 +25,7 @@
 
 #include "../../include/unet.h"
 #include "common.cuh"
+#include "umma.cuh"
 
 namespace lbm {
 namespace {
@@ -443,6 +444,160 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(LA la, LB lb, EP ep, long
         }
 }
 
+// ------------------------------------------------ tcgen05 convolution GEMM
+//
+// The convolution GEMMs whose A operand is an image gathered through taps
+// (3x3 convolution and its input gradient, the 1-tap products of the
+// transposed convolution) on the Blackwell tensor cores: a CTA computes a
+// 128-pixel x BN-channel tile of C, the pixels a 16 x 8 patch of one image
+// (width a multiple of 16, height of 8).  K runs over (tap, channel chunk of
+// KC).  For each step one thread issues two TMA copies into a ring of
+// shared-memory stages: the A box (KC channels, 16 x 8 pixels shifted by the
+// tap) of a 4D map over the NHWC activations, whose out-of-image pixels and
+// channels beyond C_in the copy engine fills with zeros (the convolution's
+// zero padding), and the B box (KC columns, BN rows) of the prepared weights.
+// A second thread issues the tcgen05.mma steps (128 x BN x 16 each) into an
+// FP32 accumulator in tensor memory and releases each stage through
+// tcgen05.commit on its mbarrier.  The four warps then read the accumulator
+// back (tcgen05.ld, one pixel row per thread) through the same epilogues as
+// k_gemm.  Every wait is bounded in time: a wait that gives up sets a bit in
+// g_umma_status, the CTA stops issuing, waits (bounded) for what it issued,
+// frees its tensor memory and returns; later launches return at entry until
+// unet_get_status reads the flag.
+struct UmmaShape {
+    int H, W, C;       // A: image height, width and channels
+    int taps;          // 9 (3x3, zero padding) or 1
+    int kc_per_tap;    // channel chunks per tap
+    int N;             // output columns
+    int rows_per_phase;  // B rows per phase (the phase's weight block)
+};
+
+__device__ unsigned g_umma_status;
+constexpr unsigned kUmmaTimeout = 1u;
+constexpr uint64_t kUmmaWaitNs = 500000000ull;  // 0.5 s per wait (a copy or an MMA step takes microseconds)
+constexpr int kUmmaStages = 4;
+
+template <int KC, int BN>
+struct UmmaSmem {
+    static constexpr int A_BYTES = 128 * KC * 2, B_BYTES = BN * KC * 2, STAGE = A_BYTES + B_BYTES;
+    static constexpr int BARS = 2 * kUmmaStages + 1;
+    static constexpr int BYTES = 1024 + kUmmaStages * STAGE + BARS * 8 + 16;  // + alignment slack
+    static_assert(A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "stage tiles keep the swizzle atoms 1024-B aligned");
+};
+
+template <int KC, int BN, class EP>
+__global__ void __launch_bounds__(128, 1) k_umma_conv(const __grid_constant__ CUtensorMap ta,
+                                                      const __grid_constant__ CUtensorMap tb, EP ep, UmmaShape sh)
+{
+    using SM = UmmaSmem<KC, BN>;
+    namespace U = umma;
+    // a wait of an earlier launch gave up (flag not yet read by unet_get_status): do nothing, so that one
+    // failure costs one wait limit, not one per CTA
+    if (*reinterpret_cast<volatile unsigned*>(&g_umma_status)) return;
+    extern __shared__ unsigned char dyn[];
+    const uint32_t s0 = U::smem_addr(dyn);
+    unsigned char* base = dyn + ((1024u - (s0 & 1023u)) & 1023u);  // 1024-B aligned: the 128-byte swizzle atoms
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + kUmmaStages * SM::STAGE);
+    uint64_t* empty = full + kUmmaStages;
+    uint64_t* done = empty + kUmmaStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kUmmaStages; ++st) {
+            U::bar_init(&full[st], 1);
+            U::bar_init(&empty[st], 1);
+        }
+        U::bar_init(done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) U::tmem_alloc(tslot, BN);
+    U::fence_before_sync();
+    __syncthreads();
+    U::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    // the tile: pixels (b, y0 .. y0 + 7, x0 .. x0 + 15), columns n0 .. n0 + BN - 1 of phase ph
+    const int tw = sh.W / 16, tpi = tw * (sh.H / 8);
+    const int b = blockIdx.x / tpi, r = blockIdx.x % tpi;
+    const int y0 = (r / tw) * 8, x0 = (r % tw) * 16;
+    const int n0 = blockIdx.y * BN, ph = blockIdx.z;
+    ep.set_phase(ph);
+    const int nk = sh.taps * sh.kc_per_tap;
+    if (warp == 0 && lane == 0) {  // producer: TMA copies into the stage ring
+        int it = 0;
+        for (; it < nk; ++it) {
+            const int st = it % kUmmaStages;
+            if (it >= kUmmaStages &&
+                !U::bar_wait(&empty[st], (uint32_t)(it / kUmmaStages - 1) & 1u, abort, &g_umma_status,
+                             kUmmaTimeout, kUmmaWaitNs))
+                break;
+            const int tap = it / sh.kc_per_tap, kc = it - tap * sh.kc_per_tap;
+            const int dy = sh.taps == 9 ? tap / 3 - 1 : 0, dx = sh.taps == 9 ? tap % 3 - 1 : 0;
+            unsigned char* sa = base + st * SM::STAGE;
+            U::bar_expect_tx(&full[st], SM::STAGE);
+            U::tma_4d(sa, &ta, &full[st], kc * KC, x0 + dx, y0 + dy, b);
+            U::tma_2d(sa + SM::A_BYTES, &tb, &full[st], tap * sh.C + kc * KC, ph * sh.rows_per_phase + n0);
+        }
+        // no copy may still be writing into shared memory when the CTA exits
+        for (int j = it > kUmmaStages ? it - kUmmaStages : 0; j < it; ++j) {
+            const uint64_t t0 = U::now_ns();
+            while (!U::bar_test(&full[j % kUmmaStages], (uint32_t)(j / kUmmaStages) & 1u))
+                if (U::now_ns() - t0 > kUmmaWaitNs) break;
+        }
+    } else if (warp == 1 && lane == 0) {  // MMA issuer
+        constexpr uint32_t idesc = U::idesc_bf16_m128(BN);
+        for (int it = 0; it < nk; ++it) {
+            const int st = it % kUmmaStages;
+            if (!U::bar_wait(&full[st], (uint32_t)(it / kUmmaStages) & 1u, abort, &g_umma_status, kUmmaTimeout,
+                             kUmmaWaitNs))
+                break;
+            U::fence_after_sync();
+            const uint32_t sa = U::smem_addr(base + st * SM::STAGE), sb = sa + SM::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk)  // 16 bf16 = 32 bytes along K within the swizzle atom
+                U::mma_bf16(tmem, U::kmajor_desc<KC>(sa + 32 * kk), U::kmajor_desc<KC>(sb + 32 * kk), idesc,
+                            (it > 0 || kk > 0) ? 1u : 0u);
+            U::mma_commit(&empty[st]);  // the stage is free once these steps have read it
+        }
+        U::mma_commit(done);  // every step issued above has completed
+    }
+    // epilogue: thread t of warp w holds pixel row 32 w + t of the tile
+    U::bar_wait(done, 0, abort, &g_umma_status, kUmmaTimeout, kUmmaWaitNs);
+    __syncthreads();  // the issuing threads are past their loops: `done` is committed
+    U::fence_after_sync();
+    const bool ok = !*abort;
+    if (!ok) {  // a wait gave up: let the steps issued so far finish (bounded) before the memory is freed
+        if (threadIdx.x == 0) {
+            const uint64_t t0 = U::now_ns();
+            while (!U::bar_test(done, 0))
+                if (U::now_ns() - t0 > kUmmaWaitNs) break;
+        }
+        __syncthreads();
+    }
+    if (ok) {
+        const int row = warp * 32 + lane;
+        const long long p = ((long long)b * sh.H + y0 + row / 16) * sh.W + x0 + row % 16;
+        __syncwarp();
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+            uint32_t v[32];
+            U::tmem_load32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                const int n = n0 + c + j;
+                if (n < sh.N) ep.store(p, n, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+            }
+        }
+    }
+    U::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        U::tmem_free(tmem, BN);
+    }
+}
+
 // ------------------------------------------------------ elementwise kernels
 
 __global__ void k_sum_partials(const float* __restrict__ part, long long count, int splits, long long stride,
@@ -824,14 +979,86 @@ void gemm(cudaStream_t s, const LA& la, const LB& lb, const EP& ep, long long M,
     k_gemm<LA, LB, EP><<<grid, kGemmThreads, 0, s>>>(la, lb, ep, M, N, K, k_split, splits);
 }
 
+int g_engine = UNET_ENGINE_TCGEN05;
+
+template <int KC, int BN, class EP>
+bool launch_umma(cudaStream_t s, const CUtensorMap& ta, const CUtensorMap& tb, const EP& ep, const UmmaShape& sh,
+                 dim3 grid)
+{
+    using SM = UmmaSmem<KC, BN>;
+    static const bool attr = cudaFuncSetAttribute(k_umma_conv<KC, BN, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  SM::BYTES) == cudaSuccess;
+    if (!attr) return false;
+    k_umma_conv<KC, BN, EP><<<grid, 128, SM::BYTES, s>>>(ta, tb, ep, sh);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+template <int KC, class EP>
+bool launch_umma_bn(int bn, cudaStream_t s, const CUtensorMap& ta, const CUtensorMap& tb, const EP& ep,
+                    const UmmaShape& sh, dim3 grid)
+{
+    switch (bn) {
+    case 32: return launch_umma<KC, 32>(s, ta, tb, ep, sh, grid);
+    case 64: return launch_umma<KC, 64>(s, ta, tb, ep, sh, grid);
+    case 128: return launch_umma<KC, 128>(s, ta, tb, ep, sh, grid);
+    default: return launch_umma<KC, 256>(s, ta, tb, ep, sh, grid);
+    }
+}
+
+// The convolution product on the tensor cores (k_umma_conv), if the shapes
+// allow it: A is the batch of Bimg images x (H x W pixels, C channels at row
+// stride ld from channel off), gathered through `taps` taps; B the weights w
+// ([phases][rows_per_phase][taps C], K contiguous); N output columns per
+// phase.  false: the caller runs k_gemm instead (nothing was launched).
+template <class EP>
+bool umma_conv(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int C, int ld, int off, int taps,
+               const bf16* w, int rows_per_phase, int phases, int N, const EP& ep)
+{
+    if (g_engine != UNET_ENGINE_TCGEN05) return false;
+    if (W % 16 || H % 8 || (C % 64 && C != 32) || N % 32 || ld % 8 || off % 8 || (taps != 9 && taps != 1))
+        return false;
+    umma::EncodeTiledFn enc = umma::tensor_map_encoder();
+    if (!enc) return false;
+    const int KC = C % 64 == 0 ? 64 : 32;
+    const long long tiles_m = (long long)Bimg * (H / 8) * (W / 16);
+    // widest tile that N allows, narrowed while the grid would not fill the GPU twice over
+    int bn = 256;
+    while (bn > N) bn >>= 1;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    while (bn > 64 && tiles_m * ((N + bn - 1) / bn) * phases < 2LL * sms) bn >>= 1;
+    const CUtensorMapSwizzle sw = KC == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUtensorMap ta, tb;
+    const cuuint64_t adim[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
+    const cuuint64_t astr[3] = {(cuuint64_t)ld * 2, (cuuint64_t)W * ld * 2, (cuuint64_t)H * W * ld * 2};
+    const cuuint32_t abox[4] = {(cuuint32_t)KC, 16, 8, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    if (enc(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x + off), adim, astr, abox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t bdim[2] = {(cuuint64_t)taps * C, (cuuint64_t)phases * rows_per_phase};
+    const cuuint64_t bstr[1] = {(cuuint64_t)taps * C * 2};
+    const cuuint32_t bbox[2] = {(cuuint32_t)KC, (cuuint32_t)bn};
+    if (enc(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(w), bdim, bstr, bbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    UmmaShape sh{H, W, C, taps, (C + KC - 1) / KC, N, rows_per_phase};
+    const dim3 grid((unsigned)tiles_m, (unsigned)((N + bn - 1) / bn), (unsigned)phases);
+    return KC == 64 ? launch_umma_bn<64>(bn, s, ta, tb, ep, sh, grid) : launch_umma_bn<32>(bn, s, ta, tb, ep, sh, grid);
+}
+
 // conv3x3 (+bias, ReLU) of x (level geometry H x W, Cin channels at ld/off) into y (contiguous Cout).
 void conv_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W, int Cin, int ld, int off, bf16* y,
               int Cout)
 {
     const long long P = (long long)C.L.B * H * W;
+    EpAct ep{y, Cout, 0, C.pw(wtensor + 1), 1};
+    if (umma_conv(C.s, x, C.L.B, H, W, Cin, ld, off, 9, C.wf(layer), Cout, 1, Cout, ep)) return;
     LdIm2col<BM> la{x, H, W, Cin, ld, off, 9};
     LdRows<BN> lb{C.wf(layer), 9 * Cin, 0};
-    EpAct ep{y, Cout, 0, C.pw(wtensor + 1), 1};
     gemm(C.s, la, lb, ep, P, Cout, 9 * Cin, 1, 1);
 }
 
@@ -867,9 +1094,10 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
     k_colsum<<<nb, 256, 0, C.s>>>(g, P, Cout, Cout, 0, rows, part);
     k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
     if (dxo) {
+        EpAct ep2{dxo, Cin, 0, nullptr, 0};
+        if (umma_conv(C.s, g, C.L.B, H, W, Cout, Cout, 0, 9, C.wb(layer), Cin, 1, Cin, ep2)) return;
         LdIm2col<BM> la2{g, H, W, Cout, Cout, 0, 9};
         LdRows<BN> lb2{C.wb(layer), 9 * Cout, 0};
-        EpAct ep2{dxo, Cin, 0, nullptr, 0};
         gemm(C.s, la2, lb2, ep2, P, Cin, 9 * Cout, 1, 1);
     }
 }
@@ -879,9 +1107,10 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
 void up_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws, int Cin, bf16* y, int Cout, int ld)
 {
     const long long P = (long long)C.L.B * Hs * Ws;
+    EpUp ep{y, Hs, Ws, ld, 0, C.pw(wtensor + 1), 0};
+    if (umma_conv(C.s, x, C.L.B, Hs, Ws, Cin, Cin, 0, 1, C.wf(layer), Cout, 4, Cout, ep)) return;
     LdIm2col<BM> la{x, Hs, Ws, Cin, Cin, 0, 1};
     LdRows<BN> lb{C.wf(layer), Cin, (long long)Cout * Cin};
-    EpUp ep{y, Hs, Ws, ld, 0, C.pw(wtensor + 1), 0};
     gemm(C.s, la, lb, ep, P, Cout, Cin, 1, 4);
 }
 
@@ -919,6 +1148,23 @@ void up_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws,
 using namespace lbm;
 
 extern "C" {
+
+lbm_status unet_set_engine(int32_t engine)
+{
+    if (engine != UNET_ENGINE_MMA_SYNC && engine != UNET_ENGINE_TCGEN05) return LBM_ERR_INVALID_ARG;
+    g_engine = engine;
+    return LBM_OK;
+}
+
+lbm_status unet_get_status(void)
+{
+    unsigned flag = 0, zero = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpyFromSymbol(&flag, g_umma_status, sizeof(flag)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_umma_status, &zero, sizeof(zero)) != cudaSuccess)
+        return LBM_ERR_CUDA;
+    return flag ? LBM_ERR_TIMEOUT : LBM_OK;
+}
 
 lbm_status unet_param_layout(int32_t base, int32_t* n_tensors, int64_t* n_params, int64_t* offsets, int64_t* counts)
 {

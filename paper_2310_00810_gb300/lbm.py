@@ -41,7 +41,7 @@ ENTRY_POINTS = (
     "lbm_batch_init_geometry", "lbm_batch_forward", "lbm_batch_loss_grad", "lbm_batch_adjoint",
     "lbm_batch_compact_size", "lbm_batch_compact_bind", "lbm_batch_get_status",
     "unet_param_layout", "unet_workspace_size", "unet_pack_input", "unet_prepare_weights", "unet_forward",
-    "unet_backward", "unet_adam",
+    "unet_backward", "unet_adam", "unet_set_engine", "unet_get_status",
 )
 
 
@@ -136,6 +136,8 @@ def load():
                 "unet_forward": [vp, vp, vp, vp, vp],
                 "unet_backward": [vp, vp, vp, vp, vp, vp, vp],
                 "unet_adam": [C.c_int64, vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float, vp],
+                "unet_set_engine": [i32],
+                "unet_get_status": [],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)

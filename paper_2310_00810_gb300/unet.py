@@ -69,6 +69,20 @@ def unet_backward(desc, x, target, loss, grad, ws, stream=None):
                                         lbm._stream(stream)), "unet_backward")
 
 
+ENGINE_MMA_SYNC, ENGINE_TCGEN05 = 0, 1
+
+
+def unet_set_engine(engine: int) -> None:
+    """The convolutions' GEMM engine (process-wide): ENGINE_TCGEN05 (default, where the shapes allow it) or
+    ENGINE_MMA_SYNC."""
+    lbm._check(lbm.load().unet_set_engine(engine), "unet_set_engine")
+
+
+def unet_get_status() -> int:
+    """LBM_OK, or LBM_ERR_TIMEOUT if a bounded wait of a tensor-core kernel gave up since the last call."""
+    return lbm.load().unet_get_status()
+
+
 def unet_adam(params, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     n = params.numel()
     lbm._check(lbm.load().unet_adam(n, _ptr(params, torch.float32), _ptr(m, torch.float32, n),

@@ -90,6 +90,52 @@ def test_larger_case_matches_the_oracle_within_bf16_error():
     assert rel(gv, np.concatenate([ge[n].reshape(-1) for n in names])) < 5e-2
 
 
+@pytest.fixture
+def _engine_restored():
+    yield
+    N.unet_set_engine(N.ENGINE_TCGEN05)
+
+
+def test_base32_full_channel_counts_match_the_oracle(_engine_restored):
+    """Base 32 (channels 32, 64, 128, 256) at 128 x 64: every level has a
+    width that is a multiple of 16 and a height of 8, so the 3x3
+    convolutions, their input gradients and the transposed convolutions'
+    forward products run on the tcgen05 path (except the 8-channel input
+    layer); against the oracle with the same storage model and tolerances as
+    the larger case above."""
+    N.unet_set_engine(N.ENGINE_TCGEN05)
+    net, x, target, loss, out, grads = gpu_case(32, 64, 128, 2, seed=21)
+    assert N.unet_get_status() == lbm.LBM_OK
+    p, names = oracle_params(net)
+    gv = np.concatenate(grads)
+    Lw, g, out_w = U.loss_and_grad(p, x, target, store=bf16_round)
+    assert rel(out, out_w) < 1e-2 and abs(loss - Lw) <= 1e-2 * Lw
+    assert rel(gv, np.concatenate([g[n].reshape(-1) for n in names])) < 3e-2
+    for name, gg in zip(names, grads):
+        assert rel(gg, g[name].reshape(-1)) < 0.1, name
+
+
+@pytest.mark.parametrize("base,H,W,B", [(32, 64, 128, 2), (16, 32, 64, 3), (64, 32, 128, 1)])
+def test_tensor_core_engine_agrees_with_mma_sync(base, H, W, B, _engine_restored):
+    """The same network, input and target through both GEMM engines: outputs,
+    loss and gradients agree within the BF16-storage spread measured against
+    the oracle (the engines sum the same FP32 products in different orders)."""
+    res = {}
+    for eng in (N.ENGINE_MMA_SYNC, N.ENGINE_TCGEN05):
+        N.unet_set_engine(eng)
+        net, x, target, loss, out, grads = gpu_case(base, H, W, B, seed=31)
+        res[eng] = (loss, out, np.concatenate(grads))
+    assert N.unet_get_status() == lbm.LBM_OK
+    (l0, o0, g0), (l1, o1, g1) = res[N.ENGINE_MMA_SYNC], res[N.ENGINE_TCGEN05]
+    assert rel(o1, o0) < 1e-2 and abs(l1 - l0) <= 1e-2 * abs(l0)
+    assert rel(g1, g0) < 3e-2
+
+
+def test_engine_switch_is_checked():
+    with pytest.raises(lbm.LBMError):
+        N.unet_set_engine(7)
+
+
 def test_adam_kernel_matches_oracle():
     r = np.random.Generator(np.random.PCG64(13))
     n = 1000
