@@ -130,12 +130,24 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr)
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | (sbo << 32) | (1ull << 46) | (layout << 61);
 }
 
-// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both
-// K-major, M = 128, N = n: D format bits 4-5 (1 = F32), A and B formats bits
-// 7-9 and 10-12 (1 = BF16), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16_m128(int n)
+// Shared-memory matrix descriptor of an MN-major tile with the 128-byte
+// swizzle: K rows of 64 M (or N) elements (128 B), eight rows per 1024-byte
+// atom; sbo_bytes from one 8-row group to the next along K, lbo_bytes from
+// one 64-element block to the next along M (or N).
+__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo_bytes >> 4) << 16) |
+           ((uint64_t)(sbo_bytes >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, M = 128,
+// N = n: D format bits 4-5 (1 = F32), A and B formats bits 7-9 and 10-12
+// (1 = BF16), A and B major-ness bits 15 and 16 (0 = K-major, 1 = MN-major),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_m128(int n, bool a_mn = false, bool b_mn = false)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 // D[tmem] (+)= A[smem] B[smem]^T, one 128 x N x 16 step; issued by one thread.

@@ -598,6 +598,159 @@ __global__ void __launch_bounds__(128, 1) k_umma_conv(const __grid_constant__ CU
     }
 }
 
+// Weight gradient of a 3x3 convolution on the tensor cores:
+// dW[(tap, ci)][co] = sum_p X[p + tap][ci] G[p][co], M = 9 C_in rows, N = C_out,
+// K = the pixels.  K advances in chunks of 64 pixels (a 16 x 4 patch of one
+// image); a CTA sums a contiguous range of chunks (its split) for a 128-row x
+// BN-column tile and writes FP32 partials (EpPartial) that k_sum_partials adds
+// in a fixed order.  Both operands are MN-major: a TMA box of 64 channels x 16
+// x 4 pixels of the NHWC tensor lands as 64 rows (pixels, the K index) of 128
+// bytes (64 channels) with the 128-byte swizzle, 1024 bytes per 8 rows; the
+// A tile is two such boxes (64 rows (tap, ci) each, one tap per box: C_in is a
+// multiple of 64), the B tile BN / 64 boxes of G.  Pipeline, waits and
+// epilogue as in k_umma_conv.
+struct UmmaWgrad {
+    int H, W, Cin, N;
+    long long M;                // 9 C_in
+    int chunks_per_image;       // (H / 4) (W / 16)
+    long long chunks;           // over the batch
+    int chunks_per_split;
+};
+
+constexpr int kWgradBox = 8192;  // 64 pixels x 64 channels x 2 bytes
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ CUtensorMap tx,
+                                                       const __grid_constant__ CUtensorMap tg, EpPartial ep,
+                                                       UmmaWgrad sh)
+{
+    constexpr int A_BYTES = 2 * kWgradBox, B_BYTES = (BN / 64) * kWgradBox, STAGE = A_BYTES + B_BYTES;
+    namespace U = umma;
+    if (*reinterpret_cast<volatile unsigned*>(&g_umma_status)) return;
+    extern __shared__ unsigned char dyn[];
+    const uint32_t s0 = U::smem_addr(dyn);
+    unsigned char* base = dyn + ((1024u - (s0 & 1023u)) & 1023u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + kUmmaStages * STAGE);
+    uint64_t* empty = full + kUmmaStages;
+    uint64_t* done = empty + kUmmaStages;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kUmmaStages; ++st) {
+            U::bar_init(&full[st], 1);
+            U::bar_init(&empty[st], 1);
+        }
+        U::bar_init(done, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) U::tmem_alloc(tslot, BN);
+    U::fence_before_sync();
+    __syncthreads();
+    U::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const long long m0 = (long long)blockIdx.x * 128;
+    const int n0 = blockIdx.y * BN;
+    ep.split = blockIdx.z;
+    const long long c0 = (long long)blockIdx.z * sh.chunks_per_split;
+    const int nk = (int)max(0LL, min(sh.chunks, c0 + sh.chunks_per_split) - c0);
+    // the A tile's two 64-row blocks: tap and first channel of each, and whether it holds any row
+    int tap[2], ci[2];
+    bool live[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const long long r0 = m0 + 64 * j;
+        live[j] = r0 < sh.M;
+        tap[j] = live[j] ? (int)(r0 / sh.Cin) : 0;
+        ci[j] = live[j] ? (int)(r0 % sh.Cin) : 0;
+    }
+    const int tw = sh.W / 16;
+    if (warp == 0 && lane == 0) {  // producer
+        const uint32_t bytes = (live[0] ? kWgradBox : 0) + (live[1] ? kWgradBox : 0) + B_BYTES;
+        int it = 0;
+        for (; it < nk; ++it) {
+            const int st = it % kUmmaStages;
+            if (it >= kUmmaStages &&
+                !U::bar_wait(&empty[st], (uint32_t)(it / kUmmaStages - 1) & 1u, abort, &g_umma_status,
+                             kUmmaTimeout, kUmmaWaitNs))
+                break;
+            const long long c = c0 + it;
+            const int b = (int)(c / sh.chunks_per_image), r = (int)(c % sh.chunks_per_image);
+            const int y0 = (r / tw) * 4, x0 = (r % tw) * 16;
+            unsigned char* sa = base + st * STAGE;
+            U::bar_expect_tx(&full[st], bytes);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (live[j])
+                    U::tma_4d(sa + j * kWgradBox, &tx, &full[st], ci[j], x0 + tap[j] % 3 - 1, y0 + tap[j] / 3 - 1, b);
+#pragma unroll
+            for (int j = 0; j < BN / 64; ++j)
+                U::tma_4d(sa + A_BYTES + j * kWgradBox, &tg, &full[st], n0 + 64 * j, x0, y0, b);
+        }
+        for (int j = it > kUmmaStages ? it - kUmmaStages : 0; j < it; ++j) {
+            const uint64_t t0 = U::now_ns();
+            while (!U::bar_test(&full[j % kUmmaStages], (uint32_t)(j / kUmmaStages) & 1u))
+                if (U::now_ns() - t0 > kUmmaWaitNs) break;
+        }
+    } else if (warp == 1 && lane == 0) {  // MMA issuer
+        constexpr uint32_t idesc = U::idesc_bf16_m128(BN, true, true);
+        for (int it = 0; it < nk; ++it) {
+            const int st = it % kUmmaStages;
+            if (!U::bar_wait(&full[st], (uint32_t)(it / kUmmaStages) & 1u, abort, &g_umma_status, kUmmaTimeout,
+                             kUmmaWaitNs))
+                break;
+            U::fence_after_sync();
+            const uint32_t sa = U::smem_addr(base + st * STAGE), sb = sa + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)  // 16 pixels (two 8-row groups, 2048 bytes) per step
+                U::mma_bf16(tmem, U::mnmajor_desc(sa + 2048 * kk, kWgradBox, 1024),
+                            U::mnmajor_desc(sb + 2048 * kk, kWgradBox, 1024), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            U::mma_commit(&empty[st]);
+        }
+        U::mma_commit(done);
+    }
+    U::bar_wait(done, 0, abort, &g_umma_status, kUmmaTimeout, kUmmaWaitNs);
+    __syncthreads();
+    U::fence_after_sync();
+    const bool ok = !*abort;
+    if (!ok) {
+        if (threadIdx.x == 0) {
+            const uint64_t t0 = U::now_ns();
+            while (!U::bar_test(done, 0))
+                if (U::now_ns() - t0 > kUmmaWaitNs) break;
+        }
+        __syncthreads();
+    }
+    if (ok) {
+        const long long m = m0 + warp * 32 + lane;
+        __syncwarp();
+#pragma unroll 1
+        for (int c = 0; c < BN; c += 32) {
+            uint32_t v[32];
+            if (nk > 0) {
+                U::tmem_load32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+            } else {  // an empty split: its partial is zero
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0u;
+            }
+            if (m < sh.M) {
+#pragma unroll
+                for (int j = 0; j < 32; j += 2) {
+                    const int n = n0 + c + j;
+                    if (n < sh.N) ep.store(m, n, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+                }
+            }
+        }
+    }
+    U::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        U::tmem_free(tmem, BN);
+    }
+}
+
 // ------------------------------------------------------ elementwise kernels
 
 __global__ void k_sum_partials(const float* __restrict__ part, long long count, int splits, long long stride,
@@ -1050,6 +1203,68 @@ bool umma_conv(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int C, int
     return KC == 64 ? launch_umma_bn<64>(bn, s, ta, tb, ep, sh, grid) : launch_umma_bn<32>(bn, s, ta, tb, ep, sh, grid);
 }
 
+template <int BN>
+bool launch_wgrad(cudaStream_t s, const CUtensorMap& tx, const CUtensorMap& tg, const EpPartial& ep,
+                  const UmmaWgrad& sh, dim3 grid)
+{
+    constexpr int bytes = 1024 + kUmmaStages * (2 * kWgradBox + (BN / 64) * kWgradBox) + (2 * kUmmaStages + 1) * 8 + 16;
+    static const bool attr =
+        cudaFuncSetAttribute(k_umma_wgrad<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    if (!attr) return false;
+    k_umma_wgrad<BN><<<grid, 128, bytes, s>>>(tx, tg, ep, sh);
+    return cudaGetLastError() == cudaSuccess;
+}
+
+// The weight gradient of a 3x3 convolution (k_umma_wgrad) into FP32 partials
+// part[split][9 Cin][Cout] (at most part_cap floats): x is the layer input
+// (Bimg images H x W, Cin channels at row stride ld from channel off), g the
+// pre-activation gradient ([pixels][Cout]).  Returns the number of splits
+// written, or 0 when the shapes do not allow it (nothing launched).
+int umma_wgrad(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int Cin, int ld, int off, const bf16* g,
+               int Cout, float* part, long long part_cap)
+{
+    if (g_engine != UNET_ENGINE_TCGEN05) return 0;
+    if (Cin % 64 || Cout % 64 || W % 16 || H % 4 || ld % 8 || off % 8) return 0;
+    umma::EncodeTiledFn enc = umma::tensor_map_encoder();
+    if (!enc) return 0;
+    const long long Mw = 9LL * Cin;
+    const int bn = Cout >= 256 ? 256 : (Cout >= 128 ? 128 : 64);
+    const long long tiles = ((Mw + 127) / 128) * ((Cout + bn - 1) / bn);
+    const int cpi = (H / 4) * (W / 16);
+    const long long chunks = (long long)Bimg * cpi;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long sp = (2LL * sms + tiles - 1) / tiles;
+    sp = std::min(sp, std::max(1LL, chunks / 8));
+    sp = std::min(sp, (long long)kMaxSplits);
+    sp = std::min(sp, part_cap / (Mw * Cout));
+    if (sp < 1) return 0;
+    const long long cps = (chunks + sp - 1) / sp;
+    sp = (chunks + cps - 1) / cps;
+    CUtensorMap tx, tg;
+    const cuuint32_t box[4] = {64, 16, 4, 1};
+    const cuuint32_t one[4] = {1, 1, 1, 1};
+    const cuuint64_t xdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
+    const cuuint64_t xstr[3] = {(cuuint64_t)ld * 2, (cuuint64_t)W * ld * 2, (cuuint64_t)H * W * ld * 2};
+    const cuuint64_t gdim[4] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
+    const cuuint64_t gstr[3] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2};
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x + off), xdim, xstr, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(g), gdim, gstr, box, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return 0;
+    UmmaWgrad sh{H, W, Cin, Cout, Mw, cpi, chunks, (int)cps};
+    EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
+    const dim3 grid((unsigned)((Mw + 127) / 128), (unsigned)((Cout + bn - 1) / bn), (unsigned)sp);
+    const bool ok = bn == 256 ? launch_wgrad<256>(s, tx, tg, ep, sh, grid)
+                  : bn == 128 ? launch_wgrad<128>(s, tx, tg, ep, sh, grid)
+                              : launch_wgrad<64>(s, tx, tg, ep, sh, grid);
+    return ok ? (int)sp : 0;
+}
+
 // conv3x3 (+bias, ReLU) of x (level geometry H x W, Cin channels at ld/off) into y (contiguous Cout).
 void conv_fwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W, int Cin, int ld, int off, bf16* y,
               int Cout)
@@ -1082,11 +1297,14 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
     float* part = at<float>(C.ws, C.L.part);
     // dW[(tap, ci)][co] = sum_p x[p + tap][ci] g[p][co]
     const long long Mw = 9LL * Cin;
-    const int sp = splits_for(Mw, Cout, P);
-    LdGatherT<BM> la{x, H, W, Cin, ld, off, 9, 0, 0};
-    LdGatherT<BN> lb{g, H, W, Cout, Cout, 0, 1, 0, 0};
-    EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
-    gemm(C.s, la, lb, ep, Mw, Cout, (int)P, sp, 1);
+    int sp = umma_wgrad(C.s, x, C.L.B, H, W, Cin, ld, off, g, Cout, part, C.L.part_floats);
+    if (!sp) {
+        sp = splits_for(Mw, Cout, P);
+        LdGatherT<BM> la{x, H, W, Cin, ld, off, 9, 0, 0};
+        LdGatherT<BN> lb{g, H, W, Cout, Cout, 0, 1, 0, 0};
+        EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
+        gemm(C.s, la, lb, ep, Mw, Cout, (int)P, sp, 1);
+    }
     k_sum_partials<<<ew_grid(Mw * Cout), 256, 0, C.s>>>(part, Mw * Cout, sp, Mw * Cout, grad + C.t[wtensor].off);
     // db[co] = sum_p g[p][co]
     const long long rows = (P + 255) / 256;
