@@ -2,10 +2,10 @@
 // tensor-memory (TMEM) allocation, tcgen05.mma of BF16 operands staged in
 // shared memory with an FP32 accumulator in TMEM, its completion through an
 // mbarrier, and tcgen05.ld of the accumulator into registers.  Operand tiles
-// arrive by TMA (cp.async.bulk.tensor) in the K-major layout with the 128- or
-// 64-byte swizzle, which is also the layout the shared-memory descriptors
-// below describe: rows of KC bf16 (KC = 64: 128 B, KC = 32: 64 B), eight rows
-// per swizzle atom, atoms stacked along M (or N).
+// arrive by TMA (cp.async.bulk.tensor) with the 128- or 64-byte swizzle, in
+// the layouts the shared-memory descriptors below describe: K-major (rows of
+// 64 or 32 K elements, one per M or N index, eight rows per swizzle atom) or
+// MN-major (rows of 64 or 32 M or N elements, one per K index).
 #pragma once
 
 #include <cuda.h>
@@ -131,13 +131,17 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr)
 }
 
 // Shared-memory matrix descriptor of an MN-major tile with the 128-byte
-// swizzle: K rows of 64 M (or N) elements (128 B), eight rows per 1024-byte
-// atom; sbo_bytes from one 8-row group to the next along K, lbo_bytes from
-// one 64-element block to the next along M (or N).
-__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
+// (w = 64) or 64-byte (w = 32) swizzle: K rows of w M (or N) elements, eight
+// rows per atom (8 w 2 bytes, the stride-byte offset along K); lbo_bytes from
+// one w-element block to the next along M (or N).
+template <int WB>
+__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t saddr, uint32_t lbo_bytes)
 {
-    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo_bytes >> 4) << 16) |
-           ((uint64_t)(sbo_bytes >> 4) << 32) | (1ull << 46) | (2ull << 61);
+    static_assert(WB == 64 || WB == 32, "rows of 128 or 64 bytes");
+    constexpr uint64_t sbo = (8 * WB * 2) >> 4;
+    constexpr uint64_t layout = WB == 64 ? 2 : 4;
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo_bytes >> 4) << 16) | (sbo << 32) | (1ull << 46) |
+           (layout << 61);
 }
 
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, M = 128,

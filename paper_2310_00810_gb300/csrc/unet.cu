@@ -603,12 +603,13 @@ __global__ void __launch_bounds__(128, 1) k_umma_conv(const __grid_constant__ CU
 // K = the pixels.  K advances in chunks of 64 pixels (a 16 x 4 patch of one
 // image); a CTA sums a contiguous range of chunks (its split) for a 128-row x
 // BN-column tile and writes FP32 partials (EpPartial) that k_sum_partials adds
-// in a fixed order.  Both operands are MN-major: a TMA box of 64 channels x 16
-// x 4 pixels of the NHWC tensor lands as 64 rows (pixels, the K index) of 128
-// bytes (64 channels) with the 128-byte swizzle, 1024 bytes per 8 rows; the
-// A tile is two such boxes (64 rows (tap, ci) each, one tap per box: C_in is a
-// multiple of 64), the B tile BN / 64 boxes of G.  Pipeline, waits and
-// epilogue as in k_umma_conv.
+// in a fixed order.  Both operands are MN-major: a TMA box of AW channels x
+// 16 x 4 pixels of the NHWC tensor lands as 64 rows (pixels, the K index) of
+// AW channels (AW = 64: 128-byte rows, 128-byte swizzle; AW = 32: 64-byte
+// rows, 64-byte swizzle), eight rows per atom; the A tile is 128 / AW such
+// boxes (AW rows (tap, ci) each, one tap per box: C_in is a multiple of AW),
+// the B tile BN / BW boxes of G.  Pipeline, waits and epilogue as in
+// k_umma_conv.
 struct UmmaWgrad {
     int H, W, Cin, N;
     long long M;                // 9 C_in
@@ -617,14 +618,22 @@ struct UmmaWgrad {
     int chunks_per_split;
 };
 
-constexpr int kWgradBox = 8192;  // 64 pixels x 64 channels x 2 bytes
+template <int AW, int BN, int BW>
+struct WgradSmem {
+    static constexpr int ABOX = 64 * AW * 2, BBOX = 64 * BW * 2;  // 64 pixels x the block's channels
+    static constexpr int ABLK = 128 / AW, BBLK = BN / BW;
+    static constexpr int A_BYTES = ABLK * ABOX, B_BYTES = BBLK * BBOX, STAGE = A_BYTES + B_BYTES;
+    static constexpr int BYTES = 1024 + kUmmaStages * STAGE + (2 * kUmmaStages + 1) * 8 + 16;
+    static_assert(STAGE % 1024 == 0, "stage tiles keep the swizzle atoms aligned");
+};
 
-template <int BN>
+template <int AW, int BN, int BW>
 __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ CUtensorMap tx,
                                                        const __grid_constant__ CUtensorMap tg, EpPartial ep,
                                                        UmmaWgrad sh)
 {
-    constexpr int A_BYTES = 2 * kWgradBox, B_BYTES = (BN / 64) * kWgradBox, STAGE = A_BYTES + B_BYTES;
+    using WS = WgradSmem<AW, BN, BW>;
+    constexpr int A_BYTES = WS::A_BYTES, STAGE = WS::STAGE;
     namespace U = umma;
     if (*reinterpret_cast<volatile unsigned*>(&g_umma_status)) return;
     extern __shared__ unsigned char dyn[];
@@ -655,19 +664,20 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
     ep.split = blockIdx.z;
     const long long c0 = (long long)blockIdx.z * sh.chunks_per_split;
     const int nk = (int)max(0LL, min(sh.chunks, c0 + sh.chunks_per_split) - c0);
-    // the A tile's two 64-row blocks: tap and first channel of each, and whether it holds any row
-    int tap[2], ci[2];
-    bool live[2];
+    // the A tile's AW-row blocks: tap and first channel of each, and whether it holds any row
+    int tap[WS::ABLK], ci[WS::ABLK];
+    bool live[WS::ABLK];
+    uint32_t bytes = WS::B_BYTES;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const long long r0 = m0 + 64 * j;
+    for (int j = 0; j < WS::ABLK; ++j) {
+        const long long r0 = m0 + AW * j;
         live[j] = r0 < sh.M;
         tap[j] = live[j] ? (int)(r0 / sh.Cin) : 0;
         ci[j] = live[j] ? (int)(r0 % sh.Cin) : 0;
+        bytes += live[j] ? WS::ABOX : 0;
     }
     const int tw = sh.W / 16;
     if (warp == 0 && lane == 0) {  // producer
-        const uint32_t bytes = (live[0] ? kWgradBox : 0) + (live[1] ? kWgradBox : 0) + B_BYTES;
         int it = 0;
         for (; it < nk; ++it) {
             const int st = it % kUmmaStages;
@@ -681,12 +691,12 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
             unsigned char* sa = base + st * STAGE;
             U::bar_expect_tx(&full[st], bytes);
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < WS::ABLK; ++j)
                 if (live[j])
-                    U::tma_4d(sa + j * kWgradBox, &tx, &full[st], ci[j], x0 + tap[j] % 3 - 1, y0 + tap[j] / 3 - 1, b);
+                    U::tma_4d(sa + j * WS::ABOX, &tx, &full[st], ci[j], x0 + tap[j] % 3 - 1, y0 + tap[j] / 3 - 1, b);
 #pragma unroll
-            for (int j = 0; j < BN / 64; ++j)
-                U::tma_4d(sa + A_BYTES + j * kWgradBox, &tg, &full[st], n0 + 64 * j, x0, y0, b);
+            for (int j = 0; j < WS::BBLK; ++j)
+                U::tma_4d(sa + A_BYTES + j * WS::BBOX, &tg, &full[st], n0 + BW * j, x0, y0, b);
         }
         for (int j = it > kUmmaStages ? it - kUmmaStages : 0; j < it; ++j) {
             const uint64_t t0 = U::now_ns();
@@ -703,9 +713,9 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
             U::fence_after_sync();
             const uint32_t sa = U::smem_addr(base + st * STAGE), sb = sa + A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk)  // 16 pixels (two 8-row groups, 2048 bytes) per step
-                U::mma_bf16(tmem, U::mnmajor_desc(sa + 2048 * kk, kWgradBox, 1024),
-                            U::mnmajor_desc(sb + 2048 * kk, kWgradBox, 1024), idesc, (it > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < 4; ++kk)  // 16 pixels (two 8-row groups) per step
+                U::mma_bf16(tmem, U::mnmajor_desc<AW>(sa + 16 * AW * 2 * kk, WS::ABOX),
+                            U::mnmajor_desc<BW>(sb + 16 * BW * 2 * kk, WS::BBOX), idesc, (it > 0 || kk > 0) ? 1u : 0u);
             U::mma_commit(&empty[st]);
         }
         U::mma_commit(done);
@@ -1203,16 +1213,28 @@ bool umma_conv(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int C, int
     return KC == 64 ? launch_umma_bn<64>(bn, s, ta, tb, ep, sh, grid) : launch_umma_bn<32>(bn, s, ta, tb, ep, sh, grid);
 }
 
-template <int BN>
+template <int AW, int BN, int BW>
 bool launch_wgrad(cudaStream_t s, const CUtensorMap& tx, const CUtensorMap& tg, const EpPartial& ep,
                   const UmmaWgrad& sh, dim3 grid)
 {
-    constexpr int bytes = 1024 + kUmmaStages * (2 * kWgradBox + (BN / 64) * kWgradBox) + (2 * kUmmaStages + 1) * 8 + 16;
-    static const bool attr =
-        cudaFuncSetAttribute(k_umma_wgrad<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    constexpr int bytes = WgradSmem<AW, BN, BW>::BYTES;
+    static const bool attr = cudaFuncSetAttribute(k_umma_wgrad<AW, BN, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  bytes) == cudaSuccess;
     if (!attr) return false;
-    k_umma_wgrad<BN><<<grid, 128, bytes, s>>>(tx, tg, ep, sh);
+    k_umma_wgrad<AW, BN, BW><<<grid, 128, bytes, s>>>(tx, tg, ep, sh);
     return cudaGetLastError() == cudaSuccess;
+}
+
+template <int AW>
+bool launch_wgrad_bn(int bn, cudaStream_t s, const CUtensorMap& tx, const CUtensorMap& tg, const EpPartial& ep,
+                     const UmmaWgrad& sh, dim3 grid)
+{
+    switch (bn) {
+    case 32: return launch_wgrad<AW, 32, 32>(s, tx, tg, ep, sh, grid);
+    case 64: return launch_wgrad<AW, 64, 64>(s, tx, tg, ep, sh, grid);
+    case 128: return launch_wgrad<AW, 128, 64>(s, tx, tg, ep, sh, grid);
+    default: return launch_wgrad<AW, 256, 64>(s, tx, tg, ep, sh, grid);
+    }
 }
 
 // The weight gradient of a 3x3 convolution (k_umma_wgrad) into FP32 partials
@@ -1224,11 +1246,13 @@ int umma_wgrad(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int Cin, i
                int Cout, float* part, long long part_cap)
 {
     if (g_engine != UNET_ENGINE_TCGEN05) return 0;
-    if (Cin % 64 || Cout % 64 || W % 16 || H % 4 || ld % 8 || off % 8) return 0;
+    if ((Cin % 64 && Cin != 32) || (Cout % 64 && Cout != 32) || W % 16 || H % 4 || ld % 8 || off % 8) return 0;
     umma::EncodeTiledFn enc = umma::tensor_map_encoder();
     if (!enc) return 0;
     const long long Mw = 9LL * Cin;
-    const int bn = Cout >= 256 ? 256 : (Cout >= 128 ? 128 : 64);
+    const int aw = Cin % 64 ? 32 : 64;  // channels per A block (and per box)
+    const int bn = Cout >= 256 ? 256 : (Cout >= 128 ? 128 : Cout);  // 32, 64, 128 or 256
+    const int bw = bn == 32 ? 32 : 64;
     const long long tiles = ((Mw + 127) / 128) * ((Cout + bn - 1) / bn);
     const int cpi = (H / 4) * (W / 16);
     const long long chunks = (long long)Bimg * cpi;
@@ -1243,25 +1267,27 @@ int umma_wgrad(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int Cin, i
     const long long cps = (chunks + sp - 1) / sp;
     sp = (chunks + cps - 1) / cps;
     CUtensorMap tx, tg;
-    const cuuint32_t box[4] = {64, 16, 4, 1};
+    const cuuint32_t abox[4] = {(cuuint32_t)aw, 16, 4, 1};
+    const cuuint32_t bbox[4] = {(cuuint32_t)bw, 16, 4, 1};
     const cuuint32_t one[4] = {1, 1, 1, 1};
+    const CUtensorMapSwizzle asw = aw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const CUtensorMapSwizzle bsw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const cuuint64_t xdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
     const cuuint64_t xstr[3] = {(cuuint64_t)ld * 2, (cuuint64_t)W * ld * 2, (cuuint64_t)H * W * ld * 2};
     const cuuint64_t gdim[4] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
     const cuuint64_t gstr[3] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2};
-    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x + off), xdim, xstr, box, one,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x + off), xdim, xstr, abox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, asw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(g), gdim, gstr, box, one,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(g), gdim, gstr, bbox, one,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, bsw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return 0;
     UmmaWgrad sh{H, W, Cin, Cout, Mw, cpi, chunks, (int)cps};
     EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
     const dim3 grid((unsigned)((Mw + 127) / 128), (unsigned)((Cout + bn - 1) / bn), (unsigned)sp);
-    const bool ok = bn == 256 ? launch_wgrad<256>(s, tx, tg, ep, sh, grid)
-                  : bn == 128 ? launch_wgrad<128>(s, tx, tg, ep, sh, grid)
-                              : launch_wgrad<64>(s, tx, tg, ep, sh, grid);
+    const bool ok = aw == 64 ? launch_wgrad_bn<64>(bn, s, tx, tg, ep, sh, grid)
+                             : launch_wgrad_bn<32>(bn, s, tx, tg, ep, sh, grid);
     return ok ? (int)sp : 0;
 }
 
