@@ -773,25 +773,71 @@ __global__ void k_sum_partials(const float* __restrict__ part, long long count, 
     }
 }
 
+// The same for few outputs over many splits: one warp per output, lane l
+// adding splits l, l + 32, ... in order, then a fixed butterfly.
+__global__ void __launch_bounds__(256) k_sum_partials_warp(const float* __restrict__ part, long long count,
+                                                           int splits, long long stride, float* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= count) return;
+    float s = 0.0f;
+    for (int k = lane; k < splits; k += 32) s += part[k * stride + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[i] = s;
+}
+
+unsigned ew_grid(long long n);
+
+void sum_partials(cudaStream_t st, const float* part, long long count, int splits, long long stride, float* out)
+{
+    if (count <= 16384 && splits >= 16)
+        k_sum_partials_warp<<<(unsigned)((count + 7) / 8), 256, 0, st>>>(part, count, splits, stride, out);
+    else
+        k_sum_partials<<<ew_grid(count), 256, 0, st>>>(part, count, splits, stride, out);
+}
+
+// Eight bf16 (16 bytes) at a time: C, row strides and channel offsets are
+// multiples of 8 throughout the network.
+union V8 {
+    uint4 u;
+    bf16 h[8];
+};
+
+__device__ __forceinline__ V8 ld8(const bf16* p)
+{
+    V8 v;
+    v.u = *reinterpret_cast<const uint4*>(p);
+    return v;
+}
+
+__device__ __forceinline__ void st8(bf16* p, const V8& v) { *reinterpret_cast<uint4*>(p) = v.u; }
+
 // Column sums of g[P][C] (row stride ld, channel offset off) over a range of
-// rows per block: part[block][c].  The block's threads cover 256 / C rows at
-// a time (C <= 256, a power-of-two multiple of 8 or not: threads beyond
-// (256 / C) * C idle), then add their row groups in shared memory.
+// rows per block: part[block][c].  Thread (group rg, vector cv) adds the rows
+// rg, rg + RG, ... of channels 8 cv .. 8 cv + 7 (RG = 256 / (C / 8) groups);
+// the groups are then added in order through shared memory.  C / 8 divides
+// 256 (C = 8 2^k, C <= 2048).
 __global__ void __launch_bounds__(256) k_colsum(const bf16* __restrict__ g, long long P, int C, int ld, int off,
                                                 long long rows, float* __restrict__ part)
 {
-    __shared__ float red[256];
+    __shared__ float red[256 * 8];
+    const int nv = C / 8, RG = 256 / nv, rg = threadIdx.x / nv, cv = threadIdx.x % nv;
     const long long r0 = (long long)blockIdx.x * rows, r1 = min(P, r0 + rows);
-    const int groups = max(1, 256 / C), c = threadIdx.x % C, gi = threadIdx.x / C;
-    float s = 0.0f;
-    if (gi < groups)
-        for (long long r = r0 + gi; r < r1; r += groups) s += __bfloat162float(g[r * ld + off + c]);
-    red[threadIdx.x] = s;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (long long r = r0 + rg; r < r1; r += RG) {
+        const V8 v = ld8(g + r * ld + off + 8 * cv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[j] += __bfloat162float(v.h[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) red[threadIdx.x * 8 + j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < C) {
+    for (int c = threadIdx.x; c < C; c += 256) {
         float t = 0.0f;
-        for (int q = 0; q < groups; ++q) t += red[q * C + threadIdx.x];
-        part[(long long)blockIdx.x * C + threadIdx.x] = t;
+        for (int q = 0; q < RG; ++q) t += red[(q * nv + c / 8) * 8 + c % 8];
+        part[(long long)blockIdx.x * C + c] = t;
     }
 }
 
@@ -799,12 +845,16 @@ __global__ void __launch_bounds__(256) k_colsum(const bf16* __restrict__ g, long
 __global__ void k_relu_grad(const bf16* __restrict__ dy, int ld_dy, int off_dy, const bf16* __restrict__ y,
                             bf16* __restrict__ out, long long P, int C)
 {
-    const long long n = P * C;
+    const int nv = C / 8;
+    const long long n = P * nv;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long p = i / C;
-        const int c = (int)(i - p * C);
-        const float v = __bfloat162float(y[i]) > 0.0f ? __bfloat162float(dy[p * ld_dy + off_dy + c]) : 0.0f;
-        out[i] = __float2bfloat16(v);
+        const long long p = i / nv;
+        const int c = (int)(i - p * nv) * 8;
+        const V8 d = ld8(dy + p * ld_dy + off_dy + c), a = ld8(y + p * C + c);
+        V8 o;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o.h[j] = __bfloat162float(a.h[j]) > 0.0f ? d.h[j] : __float2bfloat16(0.0f);
+        st8(out + p * C + c, o);
     }
 }
 
@@ -812,25 +862,37 @@ __global__ void k_relu_grad(const bf16* __restrict__ dy, int ld_dy, int off_dy, 
 __global__ void k_maxpool(const bf16* __restrict__ x, int B, int H, int W, int C, bf16* __restrict__ y,
                           uint8_t* __restrict__ arg)
 {
-    const int Ho = H / 2, Wo = W / 2;
-    const long long n = (long long)B * Ho * Wo * C;
+    const int Ho = H / 2, Wo = W / 2, nv = C / 8;
+    const long long n = (long long)B * Ho * Wo * nv;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const long long q = i / C;
+        const long long q = i / nv;
+        const int c = (int)(i - q * nv) * 8;
         const int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho);
         const long long b = q / ((long long)Wo * Ho);
-        float best = -INFINITY;
-        int bt = 0;
+        float best[8];
+        uint8_t bt[8];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
-            const float v = __bfloat162float(x[(((b * H) + 2 * yo + t / 2) * W + 2 * xo + t % 2) * C + c]);
-            if (v > best) {
-                best = v;
-                bt = t;
+            const V8 v = ld8(x + (((b * H) + 2 * yo + t / 2) * W + 2 * xo + t % 2) * C + c);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float f = __bfloat162float(v.h[j]);
+                if (t == 0 || f > best[j]) {
+                    best[j] = f;
+                    bt[j] = (uint8_t)t;
+                }
             }
         }
-        y[i] = __float2bfloat16(best);
-        arg[i] = (uint8_t)bt;
+        V8 o;
+        uint2 ar;
+        uint8_t* a8 = reinterpret_cast<uint8_t*>(&ar);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            o.h[j] = __float2bfloat16(best[j]);
+            a8[j] = bt[j];
+        }
+        st8(y + q * C + c, o);
+        *reinterpret_cast<uint2*>(arg + q * C + c) = ar;
     }
 }
 
@@ -838,18 +900,25 @@ __global__ void k_maxpool(const bf16* __restrict__ x, int B, int H, int W, int C
 __global__ void k_maxpool_grad(const bf16* __restrict__ dy, const uint8_t* __restrict__ arg, int B, int H, int W,
                                int C, const bf16* __restrict__ skip, int ld_s, int off_s, bf16* __restrict__ dx)
 {
-    const long long n = (long long)B * H * W * C;
-    const int Ho = H / 2, Wo = W / 2;
+    const int Ho = H / 2, Wo = W / 2, nv = C / 8;
+    const long long n = (long long)B * H * W * nv;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const long long p = i / C;
+        const long long p = i / nv;
+        const int c = (int)(i - p * nv) * 8;
         const int xx = (int)(p % W), yy = (int)((p / W) % H);
         const long long b = p / ((long long)W * H);
         const long long o = (((b * Ho) + yy / 2) * Wo + xx / 2) * C + c;
         const int t = (yy % 2) * 2 + (xx % 2);
-        float v = arg[o] == t ? __bfloat162float(dy[o]) : 0.0f;
-        v += __bfloat162float(skip[p * ld_s + off_s + c]);
-        dx[i] = __float2bfloat16(v);
+        const V8 d = ld8(dy + o), sk = ld8(skip + p * ld_s + off_s + c);
+        const uint2 ar = *reinterpret_cast<const uint2*>(arg + o);
+        const uint8_t* a8 = reinterpret_cast<const uint8_t*>(&ar);
+        V8 r;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float v = (a8[j] == t ? __bfloat162float(d.h[j]) : 0.0f) + __bfloat162float(sk.h[j]);
+            r.h[j] = __float2bfloat16(v);
+        }
+        st8(dx + p * C + c, r);
     }
 }
 
@@ -857,10 +926,12 @@ __global__ void k_maxpool_grad(const bf16* __restrict__ dy, const uint8_t* __res
 __global__ void k_copy_channels(const bf16* __restrict__ src, long long P, int C, bf16* __restrict__ dst, int ld,
                                 int off)
 {
-    const long long n = P * C;
+    const int nv = C / 8;
+    const long long n = P * nv;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long p = i / C;
-        dst[p * ld + off + (i - p * C)] = src[i];
+        const long long p = i / nv;
+        const int c = (int)(i - p * nv) * 8;
+        st8(dst + p * ld + off + c, ld8(src + p * C + c));
     }
 }
 
@@ -907,26 +978,49 @@ __global__ void k_mse(const float* __restrict__ out, const float* __restrict__ t
 
 // Head backward, one block per row (b, h): dx[b][h][w][c] = gout[b][h] / W * w[c];
 // part_w[row][c] = sum_w x[b][h][w][c] gout / W.
-__global__ void k_head_grad(const bf16* __restrict__ x, int W, int C, const float* __restrict__ w,
-                            const float* __restrict__ gout, bf16* __restrict__ dx, float* __restrict__ part_w)
+__global__ void __launch_bounds__(256) k_head_grad(const bf16* __restrict__ x, int W, int C,
+                                                   const float* __restrict__ w, const float* __restrict__ gout,
+                                                   bf16* __restrict__ dx, float* __restrict__ part_w)
 {
+    __shared__ float red[256];
     const long long row = blockIdx.x;
     const float gr = gout[row] / (float)W;
-    for (int i = threadIdx.x; i < W * C; i += blockDim.x) dx[row * W * C + i] = __float2bfloat16(gr * w[i % C]);
-    for (int c = threadIdx.x; c < C; c += blockDim.x) {
-        float s = 0.0f;
-        for (int xw = 0; xw < W; ++xw) s += __bfloat162float(x[(row * W + xw) * C + c]);
-        part_w[row * C + c] = s * gr;
+    const int nv = C / 8;
+    for (int i = threadIdx.x; i < W * nv; i += blockDim.x) {
+        const int c = (i % nv) * 8;
+        V8 o;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o.h[j] = __float2bfloat16(gr * w[c + j]);
+        st8(dx + row * W * C + (long long)i * 8, o);
+    }
+    // part_w[row][c] = gr * sum_w x[row][w][c]: thread (group xg, channel c) adds w = xg, xg + XG, ...; the groups
+    // are added in order (C <= 256)
+    const int XG = 256 / C, xg = threadIdx.x / C, c = threadIdx.x % C;
+    float s = 0.0f;
+    if (xg < XG)
+        for (int xw = xg; xw < W; xw += XG) s += __bfloat162float(x[(row * W + xw) * C + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int q = 0; q < XG; ++q) t += red[q * C + threadIdx.x];
+        part_w[row * C + threadIdx.x] = t * gr;
     }
 }
 
-__global__ void k_sum_vector(const float* __restrict__ v, int n, float* __restrict__ out)
+// *out = sum of v[0 .. n) (one block of 256 threads, fixed order).
+__global__ void __launch_bounds__(256) k_sum_vector(const float* __restrict__ v, int n, float* __restrict__ out)
 {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        float s = 0.0f;
-        for (int i = 0; i < n; ++i) s += v[i];
-        *out = s;
+    __shared__ float red[256];
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < n; i += 256) s += v[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // Input packing: x[b][h][w][c] = (u_x s, u_y s, mask, 0 ...).
@@ -1331,12 +1425,12 @@ void conv_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int H, int W,
         EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
         gemm(C.s, la, lb, ep, Mw, Cout, (int)P, sp, 1);
     }
-    k_sum_partials<<<ew_grid(Mw * Cout), 256, 0, C.s>>>(part, Mw * Cout, sp, Mw * Cout, grad + C.t[wtensor].off);
+    sum_partials(C.s, part, Mw * Cout, sp, Mw * Cout, grad + C.t[wtensor].off);
     // db[co] = sum_p g[p][co]
     const long long rows = (P + 255) / 256;
     const int nb = (int)((P + rows - 1) / rows);
     k_colsum<<<nb, 256, 0, C.s>>>(g, P, Cout, Cout, 0, rows, part);
-    k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
+    sum_partials(C.s, part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
     if (dxo) {
         EpAct ep2{dxo, Cin, 0, nullptr, 0};
         if (umma_conv(C.s, g, C.L.B, H, W, Cout, Cout, 0, 9, C.wb(layer), Cin, 1, Cin, ep2)) return;
@@ -1371,14 +1465,14 @@ void up_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws,
     LdGatherT<BN> lb{gy, Hs, Ws, Cout, ld, 0, 1, 1, 0};
     EpPartial ep{part, Cout, 4LL * Cin * Cout, (long long)Cin * Cout, 0, 0};
     gemm(C.s, la, lb, ep, Cin, Cout, (int)P, sp, 4);
-    k_sum_partials<<<ew_grid(4LL * Cin * Cout), 256, 0, C.s>>>(part, 4LL * Cin * Cout, sp, 4LL * Cin * Cout,
+    sum_partials(C.s, part, 4LL * Cin * Cout, sp, 4LL * Cin * Cout,
                                                                grad + C.t[wtensor].off);
     // db[co] = sum over output pixels of gy[..][co]
     const long long Po = 4 * P;
     const long long rows = (Po + 255) / 256;
     const int nb = (int)((Po + rows - 1) / rows);
     k_colsum<<<nb, 256, 0, C.s>>>(gy, Po, Cout, ld, 0, rows, part);
-    k_sum_partials<<<ew_grid(Cout), 256, 0, C.s>>>(part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
+    sum_partials(C.s, part, Cout, nb, Cout, grad + C.t[wtensor + 1].off);
     // dx[p][ci] = sum_(phase, co) gy[up(p, phase)][co] W[phase][ci][co]
     LdUpGather<BM> la2{gy, Hs, Ws, Cout, ld, 0};
     LdRows<BN> lb2{C.wb(layer), 4 * Cout, 0};
@@ -1479,9 +1573,9 @@ lbm_status unet_forward(const unet_desc* d, const uint16_t* d_x, float* d_out, v
         tensor += 2;
         if (l < 3) {
             bf16* pool = at<bf16>(d_ws, L.pool[l]);
-            k_maxpool<<<ew_grid(L.P[l + 1] * L.c[l]), 256, 0, C.s>>>(eb, L.B, L.Hl[l], L.Wl[l], L.c[l], pool,
+            k_maxpool<<<ew_grid(L.P[l + 1] * L.c[l] / 8), 256, 0, C.s>>>(eb, L.B, L.Hl[l], L.Wl[l], L.c[l], pool,
                                                                        at<uint8_t>(d_ws, L.arg[l]));
-            k_copy_channels<<<ew_grid(L.P[l] * L.c[l]), 256, 0, C.s>>>(eb, L.P[l], L.c[l], at<bf16>(d_ws, L.cat[l]),
+            k_copy_channels<<<ew_grid(L.P[l] * L.c[l] / 8), 256, 0, C.s>>>(eb, L.P[l], L.c[l], at<bf16>(d_ws, L.cat[l]),
                                                                         2 * L.c[l], L.c[l]);
             in = pool;
             cin = L.c[l];
@@ -1524,18 +1618,18 @@ lbm_status unet_backward(const unet_desc* d, const uint16_t* d_x, const float* d
     bf16* gC = at<bf16>(d_ws, L.gC);
     const bf16* db0 = at<bf16>(d_ws, L.db[0]);
     k_head_grad<<<rows, 256, 0, C.s>>>(db0, L.W, L.c[0], C.pw(nt - 2), gout, gA, part);
-    k_sum_partials<<<ew_grid(L.c[0]), 256, 0, C.s>>>(part, L.c[0], rows, L.c[0], d_grad + C.t[nt - 2].off);
-    k_sum_vector<<<1, 32, 0, C.s>>>(gout, rows, d_grad + C.t[nt - 1].off);
+    sum_partials(C.s, part, L.c[0], rows, L.c[0], d_grad + C.t[nt - 2].off);
+    k_sum_vector<<<1, 256, 0, C.s>>>(gout, rows, d_grad + C.t[nt - 1].off);
     // decoder, l = 0, 1, 2 (tensors and layers counted from the end)
     int tensor = nt - 2, layer = 16;  // 17 convolution layers, numbered in forward order
     for (int l = 0; l <= 2; ++l) {
         const int Hl = L.Hl[l], Wl = L.Wl[l], c = L.c[l];
         // gA = dL/d(db_l)
         tensor -= 2;  // dec{l}b
-        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.db[l]), gB, L.P[l], c);
+        k_relu_grad<<<ew_grid(L.P[l] * c / 8), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.db[l]), gB, L.P[l], c);
         conv_bwd(C, layer--, tensor, at<bf16>(d_ws, L.da[l]), Hl, Wl, c, c, 0, gB, c, d_grad, gA);
         tensor -= 2;  // dec{l}a
-        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.da[l]), gB, L.P[l], c);
+        k_relu_grad<<<ew_grid(L.P[l] * c / 8), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.da[l]), gB, L.P[l], c);
         bf16* gcat = at<bf16>(d_ws, L.gcat[l]);
         conv_bwd(C, layer--, tensor, at<bf16>(d_ws, L.cat[l]), Hl, Wl, 2 * c, 2 * c, 0, gB, c, d_grad, gcat);
         tensor -= 2;  // up{l}
@@ -1546,15 +1640,15 @@ lbm_status unet_backward(const unet_desc* d, const uint16_t* d_x, const float* d
     for (int l = 3; l >= 0; --l) {
         const int Hl = L.Hl[l], Wl = L.Wl[l], c = L.c[l];
         if (l < 3) {  // gA = dL/d(pool_l) -> dL/d(eb_l), plus the skip gradient
-            k_maxpool_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, at<uint8_t>(d_ws, L.arg[l]), L.B, Hl, Wl, c,
+            k_maxpool_grad<<<ew_grid(L.P[l] * c / 8), 256, 0, C.s>>>(gA, at<uint8_t>(d_ws, L.arg[l]), L.B, Hl, Wl, c,
                                                                    at<bf16>(d_ws, L.gcat[l]), 2 * c, c, gC);
             std::swap(gA, gC);
         }
         tensor -= 2;  // enc{l}b
-        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.eb[l]), gB, L.P[l], c);
+        k_relu_grad<<<ew_grid(L.P[l] * c / 8), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.eb[l]), gB, L.P[l], c);
         conv_bwd(C, layer--, tensor, at<bf16>(d_ws, L.ea[l]), Hl, Wl, c, c, 0, gB, c, d_grad, gA);
         tensor -= 2;  // enc{l}a
-        k_relu_grad<<<ew_grid(L.P[l] * c), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.ea[l]), gB, L.P[l], c);
+        k_relu_grad<<<ew_grid(L.P[l] * c / 8), 256, 0, C.s>>>(gA, c, 0, at<bf16>(d_ws, L.ea[l]), gB, L.P[l], c);
         const int cin = l == 0 ? UNET_IN_CHANNELS : L.c[l - 1];
         const bf16* in = l == 0 ? reinterpret_cast<const bf16*>(d_x) : at<bf16>(d_ws, L.pool[l - 1]);
         conv_bwd(C, layer--, tensor, in, Hl, Wl, cin, cin, 0, gB, c, d_grad, l == 0 ? nullptr : gA);
