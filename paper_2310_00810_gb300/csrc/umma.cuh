@@ -92,6 +92,16 @@ __device__ __forceinline__ void tma_4d(void* dst, const CUtensorMap* map, uint64
         : "memory");
 }
 
+__device__ __forceinline__ void tma_5d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2, int c3,
+                                       int c4)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // ------------------------------------------------------------------ TMEM
 
 // Allocates ncols columns (a power of two, 32..512) of tensor memory for the

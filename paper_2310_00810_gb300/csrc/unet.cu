@@ -609,13 +609,20 @@ __global__ void __launch_bounds__(128, 1) k_umma_conv(const __grid_constant__ CU
 // rows, 64-byte swizzle), eight rows per atom; the A tile is 128 / AW such
 // boxes (AW rows (tap, ci) each, one tap per box: C_in is a multiple of AW),
 // the B tile BN / BW boxes of G.  Pipeline, waits and epilogue as in
-// k_umma_conv.
+// k_umma_conv.  With up = 1 the same kernel gives the weight gradient of the
+// 2x2 stride-2 transposed convolution, dW[phase][ci][co] = sum_p X[p][ci]
+// G[up(p, phase)][co]: one tap, the phase from blockIdx.z / splits, and G's
+// box holds that phase's samples of the output gradient, read through a 5D
+// map (channel, x parity, x pair, y parity, image row pair) so that a plain
+// box selects them.
 struct UmmaWgrad {
     int H, W, Cin, N;
-    long long M;                // 9 C_in
+    long long M;                // 9 C_in (3x3), C_in (transposed convolution)
     int chunks_per_image;       // (H / 4) (W / 16)
     long long chunks;           // over the batch
     int chunks_per_split;
+    int up;                     // 1: transposed convolution, one product per output phase (blockIdx.z / splits)
+    int splits;
 };
 
 template <int AW, int BN, int BW>
@@ -661,8 +668,11 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
     const uint32_t tmem = *tslot;
     const long long m0 = (long long)blockIdx.x * 128;
     const int n0 = blockIdx.y * BN;
-    ep.split = blockIdx.z;
-    const long long c0 = (long long)blockIdx.z * sh.chunks_per_split;
+    const int split = sh.up ? (int)(blockIdx.z % sh.splits) : (int)blockIdx.z;
+    const int ph = sh.up ? (int)(blockIdx.z / sh.splits) : 0;
+    ep.split = split;
+    ep.set_phase(ph);
+    const long long c0 = (long long)split * sh.chunks_per_split;
     const int nk = (int)max(0LL, min(sh.chunks, c0 + sh.chunks_per_split) - c0);
     // the A tile's AW-row blocks: tap and first channel of each, and whether it holds any row
     int tap[WS::ABLK], ci[WS::ABLK];
@@ -672,7 +682,7 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
     for (int j = 0; j < WS::ABLK; ++j) {
         const long long r0 = m0 + AW * j;
         live[j] = r0 < sh.M;
-        tap[j] = live[j] ? (int)(r0 / sh.Cin) : 0;
+        tap[j] = live[j] && !sh.up ? (int)(r0 / sh.Cin) : 4;  // tap 4: no shift
         ci[j] = live[j] ? (int)(r0 % sh.Cin) : 0;
         bytes += live[j] ? WS::ABOX : 0;
     }
@@ -695,8 +705,13 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
                 if (live[j])
                     U::tma_4d(sa + j * WS::ABOX, &tx, &full[st], ci[j], x0 + tap[j] % 3 - 1, y0 + tap[j] / 3 - 1, b);
 #pragma unroll
-            for (int j = 0; j < WS::BBLK; ++j)
-                U::tma_4d(sa + A_BYTES + j * WS::BBOX, &tg, &full[st], n0 + BW * j, x0, y0, b);
+            for (int j = 0; j < WS::BBLK; ++j) {
+                if (sh.up)
+                    U::tma_5d(sa + A_BYTES + j * WS::BBOX, &tg, &full[st], n0 + BW * j, ph & 1, x0, ph >> 1,
+                              b * sh.H + y0);
+                else
+                    U::tma_4d(sa + A_BYTES + j * WS::BBOX, &tg, &full[st], n0 + BW * j, x0, y0, b);
+            }
         }
         for (int j = it > kUmmaStages ? it - kUmmaStages : 0; j < it; ++j) {
             const uint64_t t0 = U::now_ns();
@@ -1337,13 +1352,17 @@ bool launch_wgrad_bn(int bn, cudaStream_t s, const CUtensorMap& tx, const CUtens
 // pre-activation gradient ([pixels][Cout]).  Returns the number of splits
 // written, or 0 when the shapes do not allow it (nothing launched).
 int umma_wgrad(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int Cin, int ld, int off, const bf16* g,
-               int Cout, float* part, long long part_cap)
+               int Cout, float* part, long long part_cap, int g_ld = 0)
 {
+    // g_ld > 0: the transposed convolution's weight gradient (x the H x W input, g the 2H x 2W output gradient with
+    // row stride g_ld; four phases, partials part[split][phase][Cin][Cout])
+    const bool up = g_ld > 0;
     if (g_engine != UNET_ENGINE_TCGEN05) return 0;
     if ((Cin % 64 && Cin != 32) || (Cout % 64 && Cout != 32) || W % 16 || H % 4 || ld % 8 || off % 8) return 0;
     umma::EncodeTiledFn enc = umma::tensor_map_encoder();
     if (!enc) return 0;
-    const long long Mw = 9LL * Cin;
+    const long long Mw = (up ? 1LL : 9LL) * Cin;
+    const int phases = up ? 4 : 1;
     const int aw = Cin % 64 ? 32 : 64;  // channels per A block (and per box)
     const int bn = Cout >= 256 ? 256 : (Cout >= 128 ? 128 : Cout);  // 32, 64, 128 or 256
     const int bw = bn == 32 ? 32 : 64;
@@ -1353,10 +1372,10 @@ int umma_wgrad(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int Cin, i
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long sp = (2LL * sms + tiles - 1) / tiles;
+    long long sp = (2LL * sms + tiles * phases - 1) / (tiles * phases);
     sp = std::min(sp, std::max(1LL, chunks / 8));
     sp = std::min(sp, (long long)kMaxSplits);
-    sp = std::min(sp, part_cap / (Mw * Cout));
+    sp = std::min(sp, part_cap / (phases * Mw * Cout));
     if (sp < 1) return 0;
     const long long cps = (chunks + sp - 1) / sp;
     sp = (chunks + cps - 1) / cps;
@@ -1364,22 +1383,31 @@ int umma_wgrad(cudaStream_t s, const bf16* x, int Bimg, int H, int W, int Cin, i
     const cuuint32_t abox[4] = {(cuuint32_t)aw, 16, 4, 1};
     const cuuint32_t bbox[4] = {(cuuint32_t)bw, 16, 4, 1};
     const cuuint32_t one[4] = {1, 1, 1, 1};
+    const cuuint32_t one5[5] = {1, 1, 1, 1, 1};
     const CUtensorMapSwizzle asw = aw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const CUtensorMapSwizzle bsw = bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     const cuuint64_t xdim[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
     const cuuint64_t xstr[3] = {(cuuint64_t)ld * 2, (cuuint64_t)W * ld * 2, (cuuint64_t)H * W * ld * 2};
     const cuuint64_t gdim[4] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)Bimg};
     const cuuint64_t gstr[3] = {(cuuint64_t)Cout * 2, (cuuint64_t)W * Cout * 2, (cuuint64_t)H * W * Cout * 2};
+    // the output gradient of a transposed convolution as (channel, x parity, x pair, y parity, image row pair)
+    const cuuint64_t udim[5] = {(cuuint64_t)Cout, 2, (cuuint64_t)W, 2, (cuuint64_t)H * Bimg};
+    const cuuint64_t ustr[4] = {(cuuint64_t)g_ld * 2, (cuuint64_t)g_ld * 4, (cuuint64_t)W * g_ld * 4,
+                                (cuuint64_t)W * g_ld * 8};
+    const cuuint32_t ubox[5] = {(cuuint32_t)bw, 1, 16, 1, 4};
     if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(x + off), xdim, xstr, abox, one,
             CU_TENSOR_MAP_INTERLEAVE_NONE, asw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(g), gdim, gstr, bbox, one,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, bsw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        (up ? enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16*>(g), udim, ustr, ubox, one5,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, bsw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE)
+            : enc(&tg, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(g), gdim, gstr, bbox, one,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, bsw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE)) != CUDA_SUCCESS)
         return 0;
-    UmmaWgrad sh{H, W, Cin, Cout, Mw, cpi, chunks, (int)cps};
-    EpPartial ep{part, Cout, Mw * Cout, 0, 0, 0};
-    const dim3 grid((unsigned)((Mw + 127) / 128), (unsigned)((Cout + bn - 1) / bn), (unsigned)sp);
+    UmmaWgrad sh{H, W, Cin, Cout, Mw, cpi, chunks, (int)cps, up ? 1 : 0, (int)sp};
+    EpPartial ep{part, Cout, phases * Mw * Cout, Mw * Cout, 0, 0};
+    const dim3 grid((unsigned)((Mw + 127) / 128), (unsigned)((Cout + bn - 1) / bn), (unsigned)(sp * phases));
     const bool ok = aw == 64 ? launch_wgrad_bn<64>(bn, s, tx, tg, ep, sh, grid)
                              : launch_wgrad_bn<32>(bn, s, tx, tg, ep, sh, grid);
     return ok ? (int)sp : 0;
@@ -1459,12 +1487,15 @@ void up_bwd(const Ctx& C, int layer, int wtensor, const bf16* x, int Hs, int Ws,
 {
     const long long P = (long long)C.L.B * Hs * Ws;
     float* part = at<float>(C.ws, C.L.part);
-    const int sp = std::max(1, splits_for(Cin, Cout, P) / 4);  // the four phases multiply the CTAs
     // dW[phase][ci][co] = sum_p x[p][ci] gy[up(p, phase)][co]
-    LdGatherT<BM> la{x, Hs, Ws, Cin, Cin, 0, 1, 0, 0};
-    LdGatherT<BN> lb{gy, Hs, Ws, Cout, ld, 0, 1, 1, 0};
-    EpPartial ep{part, Cout, 4LL * Cin * Cout, (long long)Cin * Cout, 0, 0};
-    gemm(C.s, la, lb, ep, Cin, Cout, (int)P, sp, 4);
+    int sp = umma_wgrad(C.s, x, C.L.B, Hs, Ws, Cin, Cin, 0, gy, Cout, part, C.L.part_floats, ld);
+    if (!sp) {
+        sp = std::max(1, splits_for(Cin, Cout, P) / 4);  // the four phases multiply the CTAs
+        LdGatherT<BM> la{x, Hs, Ws, Cin, Cin, 0, 1, 0, 0};
+        LdGatherT<BN> lb{gy, Hs, Ws, Cout, ld, 0, 1, 1, 0};
+        EpPartial ep{part, Cout, 4LL * Cin * Cout, (long long)Cin * Cout, 0, 0};
+        gemm(C.s, la, lb, ep, Cin, Cout, (int)P, sp, 4);
+    }
     sum_partials(C.s, part, 4LL * Cin * Cout, sp, 4LL * Cin * Cout,
                                                                grad + C.t[wtensor].off);
     // db[co] = sum over output pixels of gy[..][co]
