@@ -303,6 +303,28 @@ struct EpAct {
         }
         *reinterpret_cast<__nv_bfloat162*>(y + (size_t)m * ld + off + n) = __floats2bfloat162_rn(v0, v1);
     }
+    // eight consecutive columns n .. n + 7 (n a multiple of 8): one 16-byte store
+    __device__ void store8(long long m, int n, const float (&v)[8]) const
+    {
+        union {
+            uint4 u;
+            __nv_bfloat162 h[4];
+        } o;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float a = v[2 * j], b = v[2 * j + 1];
+            if (bias) {
+                a += bias[n + 2 * j];
+                b += bias[n + 2 * j + 1];
+            }
+            if (relu) {
+                a = fmaxf(a, 0.0f);
+                b = fmaxf(b, 0.0f);
+            }
+            o.h[j] = __floats2bfloat162_rn(a, b);
+        }
+        *reinterpret_cast<uint4*>(y + (size_t)m * ld + off + n) = o.u;
+    }
 };
 
 // Transposed-convolution output: input pixel m of an H x W image -> output
@@ -323,6 +345,19 @@ struct EpUp {
         *reinterpret_cast<__nv_bfloat162*>(y + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + n) =
             __floats2bfloat162_rn(v0, v1);
     }
+    __device__ void store8(long long m, int n, const float (&v)[8]) const
+    {
+        const int mi = (int)m, x = mi % W, t = mi / W;
+        const Pix p{t / H, t % H, x};
+        const int yy = 2 * p.y + ph / 2, xx = 2 * p.x + ph % 2;
+        union {
+            uint4 u;
+            __nv_bfloat162 h[4];
+        } o;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o.h[j] = __floats2bfloat162_rn(v[2 * j] + bias[n + 2 * j], v[2 * j + 1] + bias[n + 2 * j + 1]);
+        *reinterpret_cast<uint4*>(y + ((size_t)((long long)p.b * 2 * H + yy) * (2 * W) + xx) * ld + off + n) = o.u;
+    }
 };
 
 // FP32 partial of a split-K product: p[split][phase][m][n].
@@ -337,6 +372,12 @@ struct EpPartial {
         float* d = p + split * split_stride + ph * phase_stride + m * N + n;
         d[0] = v0;
         d[1] = v1;
+    }
+    __device__ void store8(long long m, int n, const float (&v)[8]) const
+    {
+        float4* d = reinterpret_cast<float4*>(p + split * split_stride + ph * phase_stride + m * N + n);
+        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d[1] = make_float4(v[4], v[5], v[6], v[7]);
     }
 };
 
@@ -584,9 +625,13 @@ __global__ void __launch_bounds__(128, 1) k_umma_conv(const __grid_constant__ CU
             uint32_t v[32];
             U::tmem_load32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-            for (int j = 0; j < 32; j += 2) {
+            for (int j = 0; j < 32; j += 8) {  // N is a multiple of 32: eight columns are all in range or none
                 const int n = n0 + c + j;
-                if (n < sh.N) ep.store(p, n, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+                if (n >= sh.N) continue;
+                float f[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) f[q] = __uint_as_float(v[j + q]);
+                ep.store8(p, n, f);
             }
         }
     }
@@ -761,9 +806,13 @@ __global__ void __launch_bounds__(128, 1) k_umma_wgrad(const __grid_constant__ C
             }
             if (m < sh.M) {
 #pragma unroll
-                for (int j = 0; j < 32; j += 2) {
+                for (int j = 0; j < 32; j += 8) {  // N is a multiple of 32
                     const int n = n0 + c + j;
-                    if (n < sh.N) ep.store(m, n, __uint_as_float(v[j]), __uint_as_float(v[j + 1]));
+                    if (n >= sh.N) continue;
+                    float f[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) f[q] = __uint_as_float(v[j + q]);
+                    ep.store8(m, n, f);
                 }
             }
         }
