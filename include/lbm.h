@@ -123,6 +123,11 @@ typedef struct lbm_kernel_choice {
     int32_t steps_per_launch; /* 1, or 2: two stream-collide steps per launch (temporal blocking: a tile plus a
                                  two-node halo in shared memory) where the dense D2Q9 FP32 TMA kernels apply,
                                  in the forward sweep, the segment recompute and lbm_step; 0 reads as 1 */
+    int32_t recompute_family; /* LBM_FAMILY_* of the reverse sweep's segment recompute (the stream-collide
+                                 launches that run on the second stream beside the adjoint steps when overlap
+                                 is on); LBM_FAMILY_AUTO: as step_family.  A register family here (no shared
+                                 memory) lets its CTAs share the SMs with the adjoint's TMA CTAs.  Every family
+                                 computes the same step; only the speed differs. */
     int32_t aa;              /* 1: in-place (AA-pattern) streaming in the fluid-only layout (the dense layout
                                 ignores it).  The forward sweep and lbm_step advance one state buffer in place
                                 and the reverse sweep updates lambda in place: a step from a state stored in

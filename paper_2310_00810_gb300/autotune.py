@@ -5,8 +5,9 @@ the candidate kernel families of the stream-collide and adjoint steps in the
 dense layout — TMA staging with 8- or 4-row tiles, register kernels with 4 or
 2 nodes per thread, one node per thread — then programmatic dependent launch
 on/off and the one-launch persistent sweeps, the overlapped reverse sweep (recompute on a second stream) on/off,
-two stream-collide steps per launch (D2Q9 FP32), then the fluid-only (compact) layout with two-buffer or
-in-place streaming, and keeps the fastest.  Only the speed differs between candidates;
+the segment recompute on a register family beside the adjoint, two stream-collide steps per launch
+(D2Q9 FP32), then the fluid-only (compact) layout with two-buffer or in-place streaming, and keeps the
+fastest.  Only the speed differs between candidates;
 every family and layout computes the same step.  Results are cached in JSON
 keyed by GPU name, Q, precision, lattice size and inlet kind.
 
@@ -168,6 +169,15 @@ def tune(solver: lbm.Solver, t_tune: int = 64, repeats: int = 3, cache: str | No
         timings[f"sweep:best,overlap={ov}"] = round(t * 1e6, 3)
         if t < best_t:
             best, best_t = c, t
+    if not best.get("persist") and best.get("overlap", 1):
+        # the segment recompute on a register family: its CTAs need no shared memory, so they can share the SMs
+        # with the adjoint's TMA CTAs on the second stream
+        for name, fam in (("vec", lbm.LBM_FAMILY_VEC), ("scalar", lbm.LBM_FAMILY_SCALAR)):
+            c = dict(best, recompute_family=fam)
+            t = time_sweeps(c)
+            timings[f"sweep:best,recompute={name}"] = round(t * 1e6, 3)
+            if t < best_t:
+                best, best_t = c, t
     if tq.q == 9 and tq.precision == 4 and p.nx % 4 == 0 and not best.get("persist"):
         # two stream-collide steps per launch (temporal blocking), with either tile height
         for rows in (8, 4):

@@ -273,11 +273,12 @@ lbm_status final_stream(const lbm_plan* p, const void* cur, void* d_f, const Bc&
 }
 
 // One stream-collide launch of a sweep producing g^t from g^{t-1}: the
-// plan's kernels, or the in-place pair (src and dst may be one buffer).
+// plan's kernels (or those of info, the recompute's choice), or the in-place
+// pair (src and dst may be one buffer).
 lbm_status sweep_step(const lbm_plan* p, const void* src, void* dst, const Bc& bc, int t, const double* tau,
-                      cudaStream_t s)
+                      cudaStream_t s, const PlanInfo* info = nullptr)
 {
-    if (!in_place(p)) return step_launch(p->info, kStreamCollide, src, dst, at_time(bc, t), tau, s);
+    if (!in_place(p)) return step_launch(info ? *info : p->info, kStreamCollide, src, dst, at_time(bc, t), tau, s);
     return step_launch_cmp(p->info, kStreamCollide, src, dst, false, false, at_time(bc, t), tau, s,
                            layout_at(true, t - 1), layout_at(true, t));
 }
@@ -398,6 +399,7 @@ lbm_status lbm_plan_create(const lbm_desc* d, lbm_plan** out)
     I.adj_tma_ty = I.tma_ty;
     I.step_family = LBM_FAMILY_AUTO;
     I.adj_family = LBM_FAMILY_AUTO;
+    I.rec_family = LBM_FAMILY_AUTO;
     const char* sl = std::getenv("LBM_SPIN_LIMIT");
     I.spin_limit = sl ? (unsigned)std::strtoul(sl, nullptr, 10) : (1u << 24);
     // LBM_WAIT_US bounds each mbarrier wait of the TMA kernels in time (default 2 s; tests set it tiny)
@@ -425,11 +427,13 @@ lbm_status lbm_plan_set_kernels(lbm_plan* p, const lbm_kernel_choice* k)
         (k->tma_rows != 4 && k->tma_rows != 8) || (k->pdl != 0 && k->pdl != 1) || (k->persist != 0 && k->persist != 1) ||
         (k->overlap != 0 && k->overlap != 1) ||
         (k->adjoint_tma_rows != 0 && k->adjoint_tma_rows != 4 && k->adjoint_tma_rows != 8) ||
-        k->steps_per_launch < 0 || k->steps_per_launch > 2 || (k->aa != 0 && k->aa != 1))
+        k->steps_per_launch < 0 || k->steps_per_launch > 2 || (k->aa != 0 && k->aa != 1) ||
+        !fam_ok(k->recompute_family))
         return LBM_ERR_INVALID_ARG;
     PlanInfo& I = p->info;
     I.step_family = k->step_family;
     I.adj_family = k->adjoint_family;
+    I.rec_family = k->recompute_family;
     I.max_vec = k->vec;
     I.use_tma = 1;
     I.tma_min_tiles = 1;
@@ -451,6 +455,7 @@ lbm_status lbm_plan_get_kernels(const lbm_plan* p, lbm_kernel_choice* k)
     const PlanInfo& I = p->info;
     k->step_family = I.step_family;
     k->adjoint_family = I.adj_family;
+    k->recompute_family = I.rec_family;
     k->vec = I.max_vec >= 4 ? 4 : 2;
     k->tma_rows = I.tma_ty;
     k->adjoint_tma_rows = I.adj_tma_ty;
@@ -859,7 +864,10 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
     // in place: g^t and lambda^t in the layout of t's parity, lambda updated in place in lam[1]; the
     // recomputed segment states are written out of place, so they read the Eq. 6 velocities from their input
     const bool one = in_place(p);
-    const bool pairs = !one && step2_possible(p->info, bc);
+    // the recompute's kernels: the plan's, or the recompute family when one is chosen
+    PlanInfo rec = p->info;
+    if (rec.rec_family != LBM_FAMILY_AUTO) rec.step_family = rec.rec_family;
+    const bool pairs = !one && step2_possible(rec, bc);
     auto recompute = [&](int sg, cudaStream_t s_) -> lbm_status {
         const int len = std::min(k, T - sg * k);
         const unsigned char* prev = base_of(sg);
@@ -870,12 +878,11 @@ static lbm_status reverse_sweep(lbm_plan* p, const double* d_rho_in, const doubl
                 prev = seg(sg, j);
                 j += 1;
             } else if (pairs && j + 1 < len) {  // every segment state is needed: g^t goes to mid
-                LBM_TRY(step2_launch(p->info, prev, seg(sg, j), seg(sg, j + 1), at_time(bc, sg * k + j - 1), tau,
-                                     s_));
+                LBM_TRY(step2_launch(rec, prev, seg(sg, j), seg(sg, j + 1), at_time(bc, sg * k + j - 1), tau, s_));
                 prev = seg(sg, j + 1);
                 j += 2;
             } else {  // seg(sg, j) holds g^{sg k + j - 1}
-                LBM_TRY(sweep_step(p, prev, seg(sg, j), bc, sg * k + j - 1, tau, s_));
+                LBM_TRY(sweep_step(p, prev, seg(sg, j), bc, sg * k + j - 1, tau, s_, &rec));
                 prev = seg(sg, j);
                 j += 1;
             }

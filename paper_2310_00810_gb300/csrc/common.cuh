@@ -104,6 +104,7 @@ struct PlanInfo {
     int adj_tma_ty;   // the same for the adjoint kernels
     int step_family;  // LBM_FAMILY_* of the stream-collide kernels
     int adj_family;   // LBM_FAMILY_* of the adjoint kernels
+    int rec_family;   // LBM_FAMILY_* of the reverse sweep's segment recompute (AUTO: as step_family)
     int pdl;          // 1: launch the sweep kernels with programmatic dependent launch
     int steps2;       // 1: two stream-collide steps per launch where the two-step kernel applies
     int use_persist;  // 1: one cooperative launch per sweep for lattices of at most persist_max_bytes

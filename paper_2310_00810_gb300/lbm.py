@@ -54,7 +54,8 @@ class lbm_desc(C.Structure):
 class lbm_kernel_choice(C.Structure):
     _fields_ = [("step_family", C.c_int32), ("adjoint_family", C.c_int32), ("vec", C.c_int32),
                 ("tma_rows", C.c_int32), ("pdl", C.c_int32), ("persist", C.c_int32), ("overlap", C.c_int32),
-                ("adjoint_tma_rows", C.c_int32), ("steps_per_launch", C.c_int32), ("aa", C.c_int32)]
+                ("adjoint_tma_rows", C.c_int32), ("steps_per_launch", C.c_int32), ("recompute_family", C.c_int32),
+                ("aa", C.c_int32)]
 
 
 class lbm_geom_desc(C.Structure):
@@ -221,9 +222,9 @@ def lbm_plan_destroy(plan: Plan) -> None:
 
 def lbm_plan_set_kernels(plan: Plan, step_family=LBM_FAMILY_AUTO, adjoint_family=LBM_FAMILY_AUTO, vec=4,
                          tma_rows=8, pdl=1, persist=0, overlap=1, adjoint_tma_rows=0, steps_per_launch=1,
-                         aa=0) -> None:
+                         aa=0, recompute_family=LBM_FAMILY_AUTO) -> None:
     k = lbm_kernel_choice(step_family, adjoint_family, vec, tma_rows, pdl, persist, overlap, adjoint_tma_rows,
-                          steps_per_launch, aa)
+                          steps_per_launch, recompute_family, aa)
     _check(load().lbm_plan_set_kernels(plan.handle, C.byref(k)), "lbm_plan_set_kernels")
 
 
