@@ -1,5 +1,5 @@
-"""Binding of ``include/unet.h`` (argument marshalling only) and the driver of
-the learned inlet-profile initialiser: training data from the library's own
+"""Binding of ``include/unet.h`` (argument marshalling only) and the training
+and inference code of the learned inlet-profile initialiser: training data from the library's own
 forward solves, training with the library's forward/backward/Adam kernels,
 and inference as the starting point of the gradient inversion.
 
