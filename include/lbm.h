@@ -247,15 +247,17 @@ LBM_API lbm_status lbm_bind_geometry(lbm_plan* plan, const uint32_t* d_link);
  * the streaming step (section 2.2: streaming and boundaries are most of the
  * time) is proportional to the nodes stored; a dense layout stores and moves
  * solid nodes too, while the compact layout keeps only the n_fluid fluid
- * nodes, in node order, with a neighbour table: for fluid node k and
+ * nodes (the interior in node order, then the columns x = 0 and nx - 1,
+ * whose boundary rules take a longer code path, in node order), with a
+ * neighbour table: for fluid node k and
  * direction i >= 1 the compact index of x - c_i, or a code for a
  * bounce-back (section 2.2) or Eq. 6 link.  The layout is internal: every
  * call still takes and returns dense Q N arrays (f^T, lambda^T, the lbm_step
  * states); only the plan's workspace and the tables change.
  *
  * lbm_compact_size: bytes of the table buffer for n_fluid fluid nodes
- *   (4 n_fluid dense indices, 4 (Q - 1) n_fluid neighbour codes, 4 N
- *   dense-to-compact map, scan scratch).
+ *   (4 n_fluid dense indices, 4 (Q - 1) n_fluid neighbour codes, one bit per
+ *   fluid node, 4 N dense-to-compact map, scan scratch).
  * lbm_compact_bind: builds the tables from the bound link array into
  *   d_tables (device, caller-owned, 256-byte aligned, lbm_compact_size
  *   bytes, valid while the plan uses it) and switches the plan to the compact

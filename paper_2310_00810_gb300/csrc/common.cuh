@@ -79,7 +79,7 @@ constexpr int32_t kCmpBB = -1;   // neighbour code: halfway bounce-back link
 constexpr int32_t kCmpABB = -2;  // neighbour code: Eq. 6 link through x = -1/2 or nx - 1/2
 struct Cmp {
     long long nf;          // fluid nodes stored
-    const int32_t* idx;    // idx[k]: dense node index of compact node k (increasing)
+    const int32_t* idx;    // idx[k]: dense node index of compact node k (interior nodes, then x = 0 / nx - 1)
     const int32_t* nbr;    // nbr[(i - 1) * nf + k], i = 1..Q-1: compact index of x - c_i, or kCmpBB / kCmpABB
     const uint32_t* eq6;   // bit k & 31 of eq6[k >> 5]: node k has an Eq. 6 / velocity-inlet link
 };

@@ -7,7 +7,8 @@
 // Boolean sphere packing at porosity 0.45 with r = 6 the solid runs along x
 // are short, nearly every 32-byte sector holds some fluid node, and skipping
 // solid nodes saves almost nothing.  Here the state holds only the nf fluid
-// nodes, in node order (compact index k), and a neighbour table gives, per
+// nodes (compact index k: the interior in node order, then the columns
+// x = 0 and nx - 1 in node order), and a neighbour table gives, per
 // direction i >= 1, where node k pulls from:
 //   nbr[(i - 1) nf + k] = compact index of x - c_i    (a fluid node)
 //                       = kCmpBB                     (halfway bounce-back link)
@@ -145,15 +146,26 @@ __device__ __forceinline__ int block_excl_scan(int v, int* total)
     return before + inc - v;
 }
 
-// Fluid nodes per 1024-node block.
-__global__ void __launch_bounds__(256) k_cmp_count(const uint32_t* __restrict__ link, long long N, int* __restrict__ blk)
+// The compact order: the interior fluid nodes first, in node order, then the
+// fluid nodes of the columns x = 0 and x = nx - 1 (the only ones that can
+// have an Eq. 6 or velocity-inlet link), in node order.  The boundary nodes
+// take a longer branch of the step and adjoint kernels; grouped, they do not
+// split the warps of the interior.
+__device__ __forceinline__ bool cmp_member(const uint32_t* __restrict__ link, long long n, long long N, int nx, int cls)
+{
+    if (n >= N || (link[n] & kLinkSolid)) return false;
+    const int x = (int)(n % nx);
+    return ((x == 0 || x == nx - 1) ? 1 : 0) == cls;
+}
+
+// Fluid nodes of class cls (0 interior, 1 boundary columns) per 1024-node block.
+__global__ void __launch_bounds__(256) k_cmp_count(const uint32_t* __restrict__ link, long long N, int nx, int cls,
+                                                   int* __restrict__ blk)
 {
     const long long base = (long long)blockIdx.x * kScanNodes;
     int c = 0;
-    for (int j = threadIdx.x; j < kScanNodes; j += blockDim.x) {
-        const long long n = base + j;
-        if (n < N && !(link[n] & kLinkSolid)) ++c;
-    }
+    for (int j = threadIdx.x; j < kScanNodes; j += blockDim.x)
+        if (cmp_member(link, base + j, N, nx, cls)) ++c;
     c = block_sum_int(c);
     if (threadIdx.x == 0) blk[blockIdx.x] = c;
 }
@@ -173,31 +185,33 @@ __global__ void __launch_bounds__(1024) k_cmp_scan(int* __restrict__ blk, long l
     if (threadIdx.x == 0) *total = carry;
 }
 
-// Dense -> compact map and the compact -> dense index, node order kept.
-__global__ void __launch_bounds__(256) k_cmp_index(const uint32_t* __restrict__ link, long long N,
-                                                   const int* __restrict__ blk, int32_t* __restrict__ cmap,
-                                                   int32_t* __restrict__ idx, long long nf)
+// Dense -> compact map and the compact -> dense index of the class-cls
+// nodes, in node order from compact index *base (0 for the interior, the
+// interior count for the boundary columns).  The interior pass marks every
+// other node -1; the boundary pass then fills its own entries.
+__global__ void __launch_bounds__(256) k_cmp_index(const uint32_t* __restrict__ link, long long N, int nx, int cls,
+                                                   const long long* __restrict__ base, const int* __restrict__ blk,
+                                                   int32_t* __restrict__ cmap, int32_t* __restrict__ idx, long long nf)
 {
     const long long n0 = (long long)blockIdx.x * kScanNodes + 4LL * threadIdx.x;
     bool fl[4];
     int c = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const long long n = n0 + j;
-        fl[j] = n < N && !(link[n] & kLinkSolid);
+        fl[j] = cmp_member(link, n0 + j, N, nx, cls);
         c += fl[j] ? 1 : 0;
     }
     int sum;
-    long long k = (long long)blk[blockIdx.x] + block_excl_scan(c, &sum);
+    long long k = (cls ? *base : 0) + (long long)blk[blockIdx.x] + block_excl_scan(c, &sum);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const long long n = n0 + j;
         if (n >= N) break;
-        if (fl[j] && k < nf) {
+        if (fl[j] && k >= 0 && k < nf) {
             cmap[n] = (int32_t)k;
             idx[k] = (int32_t)n;
             ++k;
-        } else {
+        } else if (!cls) {
             cmap[n] = -1;
         }
     }
@@ -1151,13 +1165,17 @@ lbm_status compact_build(const PlanInfo& p, long long nf, void* tables, Cmp* out
     one.acc_off = 0;
     one.n_in = p.n_in;
     if (cudaMemcpyAsync(inst, &one, sizeof(one), cudaMemcpyHostToDevice, s) != cudaSuccess) return LBM_ERR_CUDA;
-    k_cmp_count<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, blk);
-    k_cmp_scan<<<1, 1024, 0, s>>>(blk, nblk, total);
-    long long got = -1;
-    if (cudaMemcpyAsync(&got, total, sizeof(got), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;
+    // interior nodes, then the boundary columns (index kernels guard against counts above nf)
+    const int nx = p.geo.nx;
+    for (int cls = 0; cls < 2; ++cls) {
+        k_cmp_count<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, nx, cls, blk);
+        k_cmp_scan<<<1, 1024, 0, s>>>(blk, nblk, total + cls);
+        k_cmp_index<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, nx, cls, total, blk, cmap, idx, nf);
+    }
+    long long got[2] = {-1, -1};
+    if (cudaMemcpyAsync(got, total, sizeof(got), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ERR_CUDA;  // also ends the copy of `one`
-    if (got != nf) return LBM_ERR_INVALID_ARG;
-    k_cmp_index<<<(unsigned)nblk, 256, 0, s>>>(p.geo.link, N, blk, cmap, idx, nf);
+    if (got[0] + got[1] != nf) return LBM_ERR_INVALID_ARG;
     if (nf > 0) {
         const unsigned g = cmp_grid(nf);
         if (p.q == 9) k_cmp_nbr<9><<<g, 256, 0, s>>>(p.geo.link, cmap, idx, nbr, nf, p.geo);
