@@ -776,17 +776,10 @@ def run_e2e(P, args, device, barrier, world):
 HBM_TRAFFIC = {
     ("disks8192x4096", "dense"): {"stream-collide": 4 * (343.118080e6 + 201.248512e6),
                                   "adjoint": 4 * (642.651648e6 + 217.033472e6)},
-    ("disks8192x4096", "compact"): {"stream-collide": 20132542 / 5032998 * (343.5e6 + 144.1e6),
-                                    "adjoint": 20132542 / 5032998 * (529.5e6 + 160.6e6)},
-    ("spheres512x256x256", "compact"): {"stream-collide": 15090843 / 1886221 * (295.2e6 + 119.8e6),
-                                        "adjoint": 15090843 / 1886221 * (578.6e6 + 180.1e6)},
-    # in place: the mean of the gather and the local step
-    ("disks8192x4096", "compact", "in place"): {
-        "stream-collide": 20132542 / 5032998 * (343.8e6 + 132.6e6 + 184.6e6 + 125.0e6) / 2,
-        "adjoint": 20132542 / 5032998 * (529.3e6 + 150.0e6 + 369.2e6 + 136.8e6) / 2},
-    ("spheres512x256x256", "compact", "in place"): {
-        "stream-collide": 15090843 / 1886221 * (293.3e6 + 106.6e6 + 195.0e6 + 99.9e6) / 2,
-        "adjoint": 15090843 / 1886221 * (545.2e6 + 167.1e6 + 404.5e6 + 144.6e6) / 2},
+    ("disks8192x4096", "compact"): {"stream-collide": 20132542 / 5032998 * (343.8e6 + 144.4e6),
+                                    "adjoint": 20132542 / 5032998 * (527.8e6 + 158.9e6)},
+    ("spheres512x256x256", "compact"): {"stream-collide": 15090843 / 1886221 * (297.2e6 + 112.1e6),
+                                        "adjoint": 15090843 / 1886221 * (463.7e6 + 130.9e6)},
 }
 
 
