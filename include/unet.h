@@ -18,7 +18,8 @@
  * Weights are FP32 master copies (one flat vector, the order of
  * unet_param_layout) converted to BF16 operand layouts by
  * unet_prepare_weights; activations are BF16; every product accumulates in
- * FP32 (tensor-core mma, m16n8k16 bf16).  Gradients of the weights are FP32.
+ * FP32 on the tensor cores (tcgen05.mma with TMEM accumulators, or mma.sync
+ * m16n8k16: unet_set_engine).  Gradients of the weights are FP32.
  *
  * Conventions as in lbm.h: every call returns an lbm_status, is asynchronous
  * on the given stream (a cudaStream_t as void*), and the caller owns every

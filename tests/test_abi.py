@@ -133,3 +133,44 @@ def test_option_setters_validate_on_the_host(lib):
     assert lib.lbm_spline_grad(p9.handle, 4, 1, None, None, None, None, None) == lbm.LBM_ERR_INVALID_ARG
     assert lib.lbm_probe_loss_grad(p9.handle, None, -1, None, None, 1.0, None, None, None, None) == \
         lbm.LBM_ERR_INVALID_ARG
+
+
+STRUCTS = [("lbm_desc", "lbm.h"), ("lbm_geom_desc", "lbm.h"), ("lbm_kernel_choice", "lbm.h"), ("unet_desc", "unet.h")]
+
+
+def test_ctypes_structures_match_the_c_headers(tmp_path):
+    """The binding's ctypes structures have the C structs' size and every
+    field's offset (a field added to a header but not to the binding, or in
+    another place, would shift the fields after it)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2310_00810_gb300 import lbm as L
+    from paper_2310_00810_gb300 import unet as UN
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    py = {"lbm_desc": L.lbm_desc, "lbm_geom_desc": L.lbm_geom_desc, "lbm_kernel_choice": L.lbm_kernel_choice,
+          "unet_desc": UN.unet_desc}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbm.h"', '#include "unet.h"', "int main(void) {"]
+    for name, _ in STRUCTS:
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in py[name]._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    include = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-std=c11", "-I", include, str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, what, value = line.split()
+        got[(name, what)] = int(value)
+    for name, _ in STRUCTS:
+        s = py[name]
+        assert got[(name, "size")] == ctypes.sizeof(s), name
+        for field, _ in s._fields_:
+            assert got[(name, field)] == getattr(s, field).offset, (name, field)
